@@ -1,0 +1,785 @@
+/*
+ * ppm_oracle.c -- plain, slow FP64 CPU oracle of the per-step bond loop of
+ * updated Lagrangian unsaturated periporomechanics (Menon & Song,
+ * arXiv:2203.05562).
+ *
+ * TEST INFRASTRUCTURE ONLY: it exists so the GPU library can be checked
+ * against something written straight from the paper.  The product library
+ * never includes, links or calls it; only the tests, the package smoke
+ * check and the benchmark's CPU-baseline leg do.
+ *
+ * Every loop follows the paper's statement in the paper's order; nothing is
+ * blocked, fused or reordered for speed.  Compiled with -ffp-contract=off so
+ * that no multiply-add is fused behind our back.  The only parallelism is an
+ * OpenMP loop over points in which every point writes only its own outputs,
+ * so results do not depend on the thread count.
+ *
+ * Readings of passages that are silent, garbled or inconsistent (each is
+ * listed with its reason in the design notes):
+ *   - a point is not a member of its own family; the bond partner j is a
+ *     member of its own sub-horizon (Eq. 1, Eq. 22, Alg. 1 line 4);
+ *   - membership is inclusive, tested on ((dx*dx + dy*dy) + dz*dz) <= delta^2;
+ *   - influence function omega = 1; all point volumes V = dx^3, mass rho V;
+ *   - D = sym(L) (Eq. 26), not the mixed form printed in Eq. 58;
+ *   - objective stress rate: Hughes-Winget incremental rotation with the
+ *     bond spin W = skew(L) (the paper is silent on the spin);
+ *   - every bond starts from its point's state; the point state of step n+1
+ *     is the varpi-weighted mean over its active bonds (internal variables on
+ *     Lagrangian points, Sec. 1);
+ *   - hardening follows Eq. 46 (compaction hardens), not the sign of Eq. 72;
+ *     the viscosity is scaled by pc_n^2 unless visc_form = 1;
+ *   - S_r from van Genuchten at constant suction (Eq. 15 is garbled);
+ *   - Eq. 60 is read with the missing dt: v~ = v + (1-beta1) dt a.
+ */
+#include "ppm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* small dense 3x3 helpers, written out plainly                        */
+/* ------------------------------------------------------------------ */
+
+static void sym_to_mat(const double s[6], double m[3][3]) {
+    m[0][0] = s[0]; m[1][1] = s[1]; m[2][2] = s[2];
+    m[1][2] = s[3]; m[2][1] = s[3];
+    m[0][2] = s[4]; m[2][0] = s[4];
+    m[0][1] = s[5]; m[1][0] = s[5];
+}
+
+static void mat_to_sym(double m[3][3], double s[6]) {
+    s[0] = m[0][0]; s[1] = m[1][1]; s[2] = m[2][2];
+    s[3] = 0.5 * (m[1][2] + m[2][1]);
+    s[4] = 0.5 * (m[0][2] + m[2][0]);
+    s[5] = 0.5 * (m[0][1] + m[1][0]);
+}
+
+static double det3(double m[3][3]) {
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1])
+         - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+         + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+/* inverse through the adjugate; returns 0 if det == 0 */
+static int inv3(double m[3][3], double out[3][3]) {
+    double d = det3(m);
+    if (d == 0.0) return 0;
+    out[0][0] = (m[1][1] * m[2][2] - m[1][2] * m[2][1]) / d;
+    out[0][1] = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) / d;
+    out[0][2] = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) / d;
+    out[1][0] = (m[1][2] * m[2][0] - m[1][0] * m[2][2]) / d;
+    out[1][1] = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) / d;
+    out[1][2] = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) / d;
+    out[2][0] = (m[1][0] * m[2][1] - m[1][1] * m[2][0]) / d;
+    out[2][1] = (m[0][1] * m[2][0] - m[0][0] * m[2][1]) / d;
+    out[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) / d;
+    return 1;
+}
+
+static void matmul3(double A[3][3], double B[3][3], double C[3][3]) {
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double s = 0.0;
+            for (int m = 0; m < 3; m++) s += A[r][m] * B[m][c];
+            C[r][c] = s;
+        }
+}
+
+/* Gaussian elimination with partial pivoting: solves J x = r. */
+static int solve3(double J[9], const double r[3], double x[3]) {
+    double a[3][4];
+    for (int i = 0; i < 3; i++) {
+        for (int j = 0; j < 3; j++) a[i][j] = J[i * 3 + j];
+        a[i][3] = r[i];
+    }
+    for (int c = 0; c < 3; c++) {
+        int piv = c;
+        for (int i = c + 1; i < 3; i++)
+            if (fabs(a[i][c]) > fabs(a[piv][c])) piv = i;
+        if (a[piv][c] == 0.0) return 0;
+        if (piv != c)
+            for (int j = 0; j < 4; j++) { double t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t; }
+        for (int i = c + 1; i < 3; i++) {
+            double m = a[i][c] / a[c][c];
+            for (int j = c; j < 4; j++) a[i][j] -= m * a[c][j];
+        }
+    }
+    for (int i = 2; i >= 0; i--) {
+        double s = a[i][3];
+        for (int j = i + 1; j < 3; j++) s -= a[i][j] * x[j];
+        x[i] = s / a[i][i];
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* material data                                                       */
+/* ------------------------------------------------------------------ */
+
+/* van Genuchten retention curve at constant suction (stands in for the
+ * garbled Eq. 15): S_r = [1 + (alpha s)^n]^-(1 - 1/n). */
+double ppmo_saturation(double suction, double alpha, double n) {
+    if (suction <= 0.0) return 1.0;
+    return pow(1.0 + pow(alpha * suction, n), -(1.0 - 1.0 / n));
+}
+
+double ppmo_time_step(const ppmo_params* p) {
+    if (p->dt > 0.0) return p->dt;
+    double cp = sqrt((p->K + 4.0 * p->mu / 3.0) / p->rho);
+    return 0.3 * p->dx / cp;
+}
+
+static int params_ok(const ppmo_params* p) {
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return 0;
+    if (!(p->dx > 0) || !(p->horizon_factor > 0) || !(p->rho > 0)) return 0;
+    if (!(p->K > 0) || !(p->mu > 0) || !(p->M > 0)) return 0;
+    if (!(p->lambda_t > p->kappa_t) || !(p->eta > 0) || !(p->pc0 > 0)) return 0;
+    if (p->b1 != 0.0 || p->b2 != 1.0) return 0;
+    if (p->model < 0 || p->model > 2) return 0;
+    if (p->newton_max_iter < 1 || !(p->newton_tol > 0)) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* positions and family (Eq. 1; Alg. 1 line 1)                         */
+/* ------------------------------------------------------------------ */
+
+void ppmo_reference_positions(const ppmo_params* p, double* X0) {
+    int64_t n = (int64_t)p->nx * p->ny * p->nz;
+    for (int64_t id = 0; id < n; id++) {
+        int64_t ix = id % p->nx;
+        int64_t iy = (id / p->nx) % p->ny;
+        int64_t iz = id / ((int64_t)p->nx * p->ny);
+        X0[0 * n + id] = (double)ix * p->dx;
+        X0[1 * n + id] = (double)iy * p->dx;
+        X0[2 * n + id] = (double)iz * p->dx;
+    }
+}
+
+/* squared distance between points a and b of a 3n component-major array */
+static double dist2(const double* x, int64_t n, int64_t a, int64_t b) {
+    double d0 = x[0 * n + b] - x[0 * n + a];
+    double d1 = x[1 * n + b] - x[1 * n + a];
+    double d2 = x[2 * n + b] - x[2 * n + a];
+    return (d0 * d0 + d1 * d1) + d2 * d2;
+}
+
+int64_t ppmo_family(int64_t n, const double* x, const int32_t* group, double delta,
+                    int64_t cap, int32_t* row_ptr, int32_t* col, int32_t* rev) {
+    const double d2max = delta * delta;
+    int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cnt) return -2;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            if (group && group[j] != group[i]) continue;
+            if (dist2(x, n, i, j) <= d2max) c++;
+        }
+        cnt[i + 1] = c;
+    }
+    for (int64_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    int64_t total = cnt[n];
+    for (int64_t i = 0; i <= n; i++) row_ptr[i] = (int32_t)cnt[i];
+    free(cnt);
+    if (total > cap) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t pos = row_ptr[i];
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            if (group && group[j] != group[i]) continue;
+            if (dist2(x, n, i, j) <= d2max) col[pos++] = (int32_t)j;
+        }
+    }
+    /* rev[b]: position of bond (j, i) in row j, found by bisection */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
+            int64_t j = col[b];
+            int64_t lo = row_ptr[j], hi = row_ptr[j + 1];
+            int32_t found = -1;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (col[mid] < i) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < row_ptr[j + 1] && col[lo] == i) found = (int32_t)lo;
+            rev[b] = found;
+        }
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* constitutive update (Sec. 2.3, Eq. 40-46; Sec. 3.2.1, Eq. 70-76)     */
+/* ------------------------------------------------------------------ */
+
+/* Residual of Eq. 73-75 with the hardening sign of Eq. 46, and its exact
+ * Jacobian.  c = dt / eta_eff; x = (pbar, q, pbar_c).  Eq. 75 is taken in
+ * logarithmic form, ln(pc / pc_n) + c f f_p / (lambda - kappa) = 0: the
+ * same root, without overflow of the exponential far outside the yield
+ * surface.  r[2] is +inf when pc / pc_n <= 0. */
+void ppmo_return_residual(const ppmo_params* p, double c, double p_tr, double q_tr,
+                          double pc_n, const double x[3], double r[3], double J[9]) {
+    const double M2 = p->M * p->M;
+    const double lk = p->lambda_t - p->kappa_t;
+    double pb = x[0], q = x[1], pc = x[2];
+    double f = q * q / M2 + pb * (pb - pc);          /* Eq. 40 */
+    double fp = 2.0 * pb - pc;                       /* df/dp  */
+    double fq = 2.0 * q / M2;                        /* df/dq  */
+    double fc = -pb;                                 /* df/dpc, Eq. 87 */
+    r[0] = pb - p_tr + p->K * c * f * fp;            /* Eq. 73 */
+    r[1] = q - q_tr + 3.0 * p->mu * c * f * fq;      /* Eq. 74 */
+    double ratio = pc / pc_n;
+    r[2] = (ratio > 0.0) ? log(ratio) + c * f * fp / lk : INFINITY;   /* Eq. 75, 46 */
+    if (J) {
+        J[0] = 1.0 + p->K * c * (fp * fp + 2.0 * f);
+        J[1] = p->K * c * fq * fp;
+        J[2] = p->K * c * (fc * fp - f);
+        J[3] = 3.0 * p->mu * c * fp * fq;
+        J[4] = 1.0 + 3.0 * p->mu * c * (fq * fq + 2.0 * f / M2);
+        J[5] = 3.0 * p->mu * c * fc * fq;
+        J[6] = c / lk * (fp * fp + 2.0 * f);
+        J[7] = c / lk * (fq * fp);
+        J[8] = 1.0 / pc + c / lk * (fc * fp - f);
+    }
+}
+
+/* residual with the two stress rows divided by the stress scale, so that
+ * all three rows are dimensionless */
+static void scaled_residual(const ppmo_params* p, double c, double p_tr, double q_tr,
+                            double pc_n, double inv_scale, const double x[3], double r[3],
+                            double* J) {
+    ppmo_return_residual(p, c, p_tr, q_tr, pc_n, x, r, J);
+    r[0] *= inv_scale;
+    r[1] *= inv_scale;
+    if (J)
+        for (int k = 0; k < 6; k++) J[k] *= inv_scale;
+}
+
+static int finite3(const double r[3]) {
+    return isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]);
+}
+
+static double norm_inf3(const double r[3]) {
+    double m = fabs(r[0]);
+    if (fabs(r[1]) > m) m = fabs(r[1]);
+    if (fabs(r[2]) > m) m = fabs(r[2]);
+    return m;
+}
+
+static double norm2_3(const double r[3]) {
+    return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+}
+
+/* Backward-Euler visco-plastic return (Eq. 70-76) by Newton from the trial
+ * state, with backtracking: a step is halved (at most 20 times) until the
+ * scaled residual is finite and its 2-norm decreases.  Converged when the
+ * scaled residual's max-norm is <= newton_tol, or when the Newton step is
+ * below 1e-14 of the state.  Returns 1 if converged;
+ * otherwise x keeps the last accepted iterate. */
+static int return_map(const ppmo_params* p, double c, double p_tr, double q_tr, double pc_n,
+                      double x[3]) {
+    double scale = fabs(pc_n);
+    if (fabs(p_tr) > scale) scale = fabs(p_tr);
+    if (q_tr > scale) scale = q_tr;
+    if (scale < 1.0) scale = 1.0;
+    const double inv_scale = 1.0 / scale;
+    x[0] = p_tr; x[1] = q_tr; x[2] = pc_n;
+    double r[3], J[9];
+    for (int it = 0; ; it++) {
+        scaled_residual(p, c, p_tr, q_tr, pc_n, inv_scale, x, r, J);
+        if (norm_inf3(r) <= p->newton_tol) return 1;
+        if (it >= p->newton_max_iter) return 0;
+        double dx[3];
+        if (!solve3(J, r, dx)) return 0;
+        /* a Newton step below 1e-14 of the state is the rounding floor of
+         * the residual (f cancels near the yield surface): converged */
+        if (fabs(dx[0]) <= 1e-14 * scale && fabs(dx[1]) <= 1e-14 * scale &&
+            fabs(dx[2]) <= 1e-14 * fabs(x[2]))
+            return 1;
+        double rn = norm2_3(r);
+        double lam = 1.0, xt[3], rt[3];
+        int accepted = 0;
+        for (int ls = 0; ls < 20; ls++) {
+            for (int k = 0; k < 3; k++) xt[k] = x[k] - lam * dx[k];
+            scaled_residual(p, c, p_tr, q_tr, pc_n, inv_scale, xt, rt, NULL);
+            if (finite3(rt) && norm2_3(rt) < rn) { accepted = 1; break; }
+            lam *= 0.5;
+        }
+        if (!accepted) return 0;
+        for (int k = 0; k < 3; k++) x[k] = xt[k];
+    }
+}
+
+int ppmo_material_update(const ppmo_params* p, const double sig_n[6], double pc_n,
+                         const double L[9], double dt, double sig_out[6], double* pc_out,
+                         double* deps_s, int32_t* flags) {
+    double D[3][3], W[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            D[r][c] = 0.5 * (L[r * 3 + c] + L[c * 3 + r]);   /* Eq. 26 */
+            W[r][c] = 0.5 * (L[r * 3 + c] - L[c * 3 + r]);
+        }
+    /* Hughes-Winget: Q = (I - dt/2 W)^-1 (I + dt/2 W), sigma_rot = Q sigma Q^T */
+    double Bm[3][3], Cm[3][3], Bi[3][3], Q[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double I = (r == c) ? 1.0 : 0.0;
+            Bm[r][c] = I - 0.5 * dt * W[r][c];
+            Cm[r][c] = I + 0.5 * dt * W[r][c];
+        }
+    if (!inv3(Bm, Bi)) return -1;
+    matmul3(Bi, Cm, Q);
+    double S[3][3], QS[3][3], QT[3][3], R[3][3];
+    sym_to_mat(sig_n, S);
+    matmul3(Q, S, QS);
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) QT[r][c] = Q[c][r];
+    matmul3(QS, QT, R);
+    /* strain increment (Eq. 59) and linear hypo-elastic trial (Eq. 41) */
+    double de[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) de[r][c] = dt * D[r][c];
+    double trv = de[0][0] + de[1][1] + de[2][2];
+    double Str[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double I = (r == c) ? 1.0 : 0.0;
+            Str[r][c] = R[r][c] + p->K * trv * I + 2.0 * p->mu * (de[r][c] - trv / 3.0 * I);
+        }
+    /* equivalent shear strain of the increment */
+    double ss = 0.0;
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double I = (r == c) ? 1.0 : 0.0;
+            double e = de[r][c] - trv / 3.0 * I;
+            ss += e * e;
+        }
+    *deps_s = sqrt(2.0 / 3.0 * ss);
+    /* invariants and yield function, Eq. 40 */
+    double p_tr = (Str[0][0] + Str[1][1] + Str[2][2]) / 3.0;
+    double s_tr[3][3], sn = 0.0;
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double I = (r == c) ? 1.0 : 0.0;
+            s_tr[r][c] = Str[r][c] - p_tr * I;
+            sn += s_tr[r][c] * s_tr[r][c];
+        }
+    double q_tr = sqrt(1.5 * sn);
+    double f_tr = q_tr * q_tr / (p->M * p->M) + p_tr * (p_tr - pc_n);
+    *flags = 0;
+    if (!(f_tr > 0.0) || dt == 0.0) {          /* elastic, Eq. 44 */
+        mat_to_sym(Str, sig_out);
+        *pc_out = pc_n;
+        return 0;
+    }
+    double eta_eff = (p->visc_form == 0) ? p->eta * pc_n * pc_n : p->eta;
+    double c = dt / eta_eff;
+    double x[3];
+    int ok = return_map(p, c, p_tr, q_tr, pc_n, x);
+    *flags = 1 | (ok ? 0 : 2);
+    double ratio = (q_tr > 0.0) ? x[1] / q_tr : 0.0;
+    double out[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int cc = 0; cc < 3; cc++) {
+            double I = (r == cc) ? 1.0 : 0.0;
+            out[r][cc] = x[0] * I + ratio * s_tr[r][cc];
+        }
+    mat_to_sym(out, sig_out);
+    double pc_new = x[2];
+    if (pc_new > -1.0) pc_new = -1.0;             /* floor at the apex */
+    *pc_out = pc_new;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* bond-associated sub-horizon kinematics (Eq. 22-26, 55, 57)          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double K[3][3], A[3][3];
+    int32_t count;
+} subhorizon_sums;
+
+/* Sums over the sub-horizon of bond (i, j): S = {k in H_i : |x_k - x_j| <= delta}
+ * (Alg. 1 line 4); the standard model takes S = H_i. */
+static void subhorizon(const ppmo_params* p, int64_t n, const double* x, const double* vel,
+                       const int32_t* row_ptr, const int32_t* col, int64_t i, int64_t j,
+                       subhorizon_sums* s) {
+    const double delta = p->horizon_factor * p->dx;
+    const double d2max = delta * delta;
+    const double V = p->dx * p->dx * p->dx;
+    const double omega = 1.0;
+    memset(s, 0, sizeof(*s));
+    for (int64_t b2 = row_ptr[i]; b2 < row_ptr[i + 1]; b2++) {
+        int64_t k = col[b2];
+            int member = (p->model == 1) || (dist2(x, n, j, k) <= d2max);
+        if (!member) continue;
+        double zeta[3], ydot[3];
+        for (int c = 0; c < 3; c++) {
+            zeta[c] = x[c * n + k] - x[c * n + i];
+            ydot[c] = vel[c * n + k] - vel[c * n + i];
+        }
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) {
+                s->K[r][c] += omega * zeta[r] * zeta[c] * V;   /* Eq. 23 */
+                s->A[r][c] += omega * ydot[r] * zeta[c] * V;   /* Eq. 25 / 57 */
+            }
+        s->count++;
+    }
+}
+
+/* Inactive-bond rule: fewer than three sub-horizon members or a shape
+ * tensor whose determinant is below 1e-12 (tr K / 3)^3. */
+static int shape_ok(int32_t count, double K[3][3]) {
+    if (count < 3) return 0;
+    double t = (K[0][0] + K[1][1] + K[2][2]) / 3.0;
+    return det3(K) > 1e-12 * t * t * t;
+}
+
+int ppmo_bond_kinematics(const ppmo_params* p, int64_t n, const double* x, const double* vel,
+                         const int32_t* row_ptr, const int32_t* col,
+                         double* Kb, double* Lb, int32_t* count, int32_t* active) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
+            subhorizon_sums s;
+            subhorizon(p, n, x, vel, row_ptr, col, i, col[b], &s);
+            double ks[6];
+            mat_to_sym(s.K, ks);
+            for (int c = 0; c < 6; c++) Kb[b * 6 + c] = ks[c];
+            count[b] = s.count;
+            double Ki[3][3], L[3][3];
+            int ok = shape_ok(s.count, s.K) && inv3(s.K, Ki);
+            active[b] = ok;
+            if (ok) matmul3(s.A, Ki, L);
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Lb[b * 9 + r * 3 + c] = ok ? L[r][c] : 0.0;
+        }
+    }
+    return 0;
+}
+
+int ppmo_full_horizon_L(const ppmo_params* p, int64_t n, const double* x, const double* vel,
+                        const int32_t* row_ptr, const int32_t* col, double* Lout) {
+    const double V = p->dx * p->dx * p->dx;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double K[3][3] = {{0}}, A[3][3] = {{0}};
+        for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
+            int64_t k = col[b];
+            double zeta[3], ydot[3];
+            for (int c = 0; c < 3; c++) {
+                zeta[c] = x[c * n + k] - x[c * n + i];
+                ydot[c] = vel[c * n + k] - vel[c * n + i];
+            }
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) {
+                    K[r][c] += zeta[r] * zeta[c] * V;          /* Eq. 5 */
+                    A[r][c] += ydot[r] * zeta[c] * V;          /* Eq. 8 */
+                }
+        }
+        double Ki[3][3], L[3][3];
+        int ok = inv3(K, Ki);
+        if (ok) matmul3(A, Ki, L);
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) Lout[i * 9 + r * 3 + c] = ok ? L[r][c] : 0.0;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* the bond pass: Alg. 1 (force states, Eq. 31-32, 51-56)               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t plastic, nonconv, singular;
+} pass_counts;
+
+/* One pass over every bond of every point at positions x and velocities
+ * vel.  T (3 x cap, component-major) receives the total force state of
+ * each bond; fint the internal force per point (Eq. 49-50).  With dt == 0
+ * every bond carries its point's stress unchanged; otherwise the point
+ * state (sig, pc, eps_s) is replaced by the varpi-weighted bond mean. */
+static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const double* vel,
+                      double dt, const int32_t* row_ptr, const int32_t* col,
+                      const int32_t* rev, int64_t cap, double* sig, double* pc,
+                      double* eps_s, int update, double* T, double* fint,
+                      pass_counts* cnt_out) {
+    const double V = p->dx * p->dx * p->dx;
+    const double omega = 1.0;
+    const double Srs = ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
+    const double delta = p->horizon_factor * p->dx;
+    const double d2max = delta * delta;
+    int64_t plastic = 0, nonconv = 0, singular = 0;
+#pragma omp parallel for schedule(static) reduction(+ : plastic, nonconv, singular)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t nb = row_ptr[i + 1] - row_ptr[i];
+        double sig_i[6];
+        for (int c = 0; c < 6; c++) sig_i[c] = sig[c * n + i];
+        double pc_i = pc[i];
+        double w = 0.0, acc_sig[6] = {0}, acc_pc = 0.0, acc_es = 0.0;
+        for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++)
+            for (int c = 0; c < 3; c++) T[c * cap + b] = 0.0;
+        for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
+            int64_t j = col[b];
+            subhorizon_sums s;
+            subhorizon(p, n, x, vel, row_ptr, col, i, j, &s);
+            double Ki[3][3];
+            if (!shape_ok(s.count, s.K) || !inv3(s.K, Ki)) {
+                singular++;
+                continue;
+            }
+            double varpi = (double)s.count / (double)nb;          /* Eq. 55 */
+            double sig_b[6], pc_b = pc_i, des = 0.0;
+            if (dt == 0.0) {
+                for (int c = 0; c < 6; c++) sig_b[c] = sig_i[c];
+            } else {
+                double L[3][3], Lf[9];
+                matmul3(s.A, Ki, L);                                  /* Eq. 57 */
+                for (int r = 0; r < 3; r++)
+                    for (int c = 0; c < 3; c++) Lf[r * 3 + c] = L[r][c];
+                int32_t fl = 0;
+                ppmo_material_update(p, sig_i, pc_i, Lf, dt, sig_b, &pc_b, &des, &fl);
+                if (fl & 1) plastic++;
+                if (fl & 2) nonconv++;
+            }
+            /* total stress sigma_bar - S_r p_w 1 with p_w = -s (Eq. 32) */
+            double St[3][3], SK[3][3];
+            sym_to_mat(sig_b, St);
+            for (int c = 0; c < 3; c++) St[c][c] += Srs;
+            matmul3(St, Ki, SK);
+            if (p->model == 2) {
+                /* power-conjugate form: the force state of this sub-horizon
+                 * acts on every member k of it (Eq. 27, 30-31 read as a state
+                 * over H_s); the row is normalised by sum(varpi) below */
+                for (int64_t b2 = row_ptr[i]; b2 < row_ptr[i + 1]; b2++) {
+                    int64_t k = col[b2];
+                    if (!(dist2(x, n, j, k) <= d2max)) continue;
+                    double zk[3];
+                    for (int c = 0; c < 3; c++) zk[c] = x[c * n + k] - x[c * n + i];
+                    for (int r = 0; r < 3; r++) {
+                        double t = 0.0;
+                        for (int c = 0; c < 3; c++) t += SK[r][c] * zk[c];
+                        T[r * cap + b2] += varpi * omega * t;
+                    }
+                }
+            } else {
+                /* Eq. 31-32, 51: the force state on the bond itself */
+                double zj[3];
+                for (int c = 0; c < 3; c++) zj[c] = x[c * n + j] - x[c * n + i];
+                for (int r = 0; r < 3; r++) {
+                    double t = 0.0;
+                    for (int c = 0; c < 3; c++) t += SK[r][c] * zj[c];
+                    T[r * cap + b] = varpi * omega * t;
+                }
+            }
+            w += varpi;
+            for (int c = 0; c < 6; c++) acc_sig[c] += varpi * sig_b[c];
+            acc_pc += varpi * pc_b;
+            acc_es += varpi * des;
+        }
+        if (p->model == 2 && w > 0.0)
+            for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++)
+                for (int c = 0; c < 3; c++) T[c * cap + b] /= w;
+        if (update && w > 0.0) {
+            for (int c = 0; c < 6; c++) sig[c * n + i] = acc_sig[c] / w;
+            pc[i] = acc_pc / w;
+            eps_s[i] += acc_es / w;
+        }
+    }
+    /* pairwise nodal force, Eq. 49-50: f_i = V^2 sum_j (T_(ij) - T_(ji)) */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        for (int c = 0; c < 3; c++) {
+            double s = 0.0;
+            for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++)
+                s += T[c * cap + b] - T[c * cap + rev[b]];
+            fint[c * n + i] = V * V * s;
+        }
+    }
+    if (cnt_out) {
+        cnt_out->plastic = plastic;
+        cnt_out->nonconv = nonconv;
+        cnt_out->singular = singular;
+    }
+}
+
+int ppmo_internal_force(const ppmo_params* p, int64_t n, const double* x, const double* sig,
+                        const int32_t* row_ptr, const int32_t* col, const int32_t* rev,
+                        double* f) {
+    int64_t B = row_ptr[n];
+    double* T = (double*)malloc(sizeof(double) * 3 * (size_t)(B > 0 ? B : 1));
+    double* sg = (double*)malloc(sizeof(double) * 6 * (size_t)n);
+    double* pcs = (double*)calloc((size_t)n, sizeof(double));
+    double* es = (double*)calloc((size_t)n, sizeof(double));
+    if (!T || !sg || !pcs || !es) { free(T); free(sg); free(pcs); free(es); return -2; }
+    memcpy(sg, sig, sizeof(double) * 6 * (size_t)n);
+    double* vel = (double*)calloc(3 * (size_t)n, sizeof(double));
+    bond_pass(p, n, x, vel, 0.0, row_ptr, col, rev, B, sg, pcs, es, 0, T, f, NULL);
+    free(vel); free(T); free(sg); free(pcs); free(es);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* explicit Newmark / central difference (Eq. 60-64, Alg. 2)           */
+/* ------------------------------------------------------------------ */
+
+static int is_base(const ppmo_params* p, int64_t id) {
+    return (id / ((int64_t)p->nx * p->ny)) == 0;
+}
+
+static void current_positions(const ppmo_params* p, int64_t n, const double* u, double* x) {
+    ppmo_reference_positions(p, x);
+    for (int64_t k = 0; k < 3 * n; k++) x[k] += u[k];
+}
+
+static int rebuild(const ppmo_params* p, ppmo_state* s, const double* x) {
+    int32_t* rp = (int32_t*)malloc(sizeof(int32_t) * ((size_t)s->n + 1));
+    int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->cap > 0 ? s->cap : 1));
+    int32_t* rv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->cap > 0 ? s->cap : 1));
+    if (!rp || !cl || !rv) { free(rp); free(cl); free(rv); return -2; }
+    int64_t B = ppmo_family(s->n, x, NULL, p->horizon_factor * p->dx, s->cap, rp, cl, rv);
+    if (B < 0) {                      /* keep the previous family */
+        s->n_overflow++;
+        free(rp); free(cl); free(rv);
+        return (int)B;
+    }
+    memcpy(s->row_ptr, rp, sizeof(int32_t) * ((size_t)s->n + 1));
+    memcpy(s->col, cl, sizeof(int32_t) * (size_t)B);
+    memcpy(s->rev, rv, sizeof(int32_t) * (size_t)B);
+    s->nbonds = B;
+    free(rp); free(cl); free(rv);
+    return 0;
+}
+
+int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s) {
+    if (!params_ok(p)) return -1;
+    int64_t n = (int64_t)p->nx * p->ny * p->nz;
+    if (s->n != n) return -1;
+    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
+    const double Srs = ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
+    /* K0 = nu / (1 - nu) with nu from K and mu */
+    const double nu = (3.0 * p->K - 2.0 * p->mu) / (2.0 * (3.0 * p->K + p->mu));
+    const double K0 = nu / (1.0 - nu);
+    const double gmag = -p->gravity[2];
+    for (int64_t i = 0; i < n; i++) {
+        int64_t iz = i / ((int64_t)p->nx * p->ny);
+        for (int c = 0; c < 3; c++) {
+            s->u[c * n + i] = 0.0;
+            double vv = v0 ? v0[c * n + i] : 0.0;
+            if (is_base(p, i) || (p->lock_lateral && c < 2)) vv = 0.0;
+            s->v[c * n + i] = vv;
+        }
+        for (int c = 0; c < 6; c++) s->sig[c * n + i] = 0.0;
+        if (p->init_stress == 0) {
+            /* geostatic effective stress with a traction-free top: total
+             * stress sigma_zz = -rho g d, sigma_xx = sigma_yy = K0 sigma_zz,
+             * effective = total - S_r s 1 */
+            double d = (double)(p->nz - 1 - iz) * p->dx;
+            double szz = -p->rho * gmag * d;
+            s->sig[0 * n + i] = K0 * szz - Srs;
+            s->sig[1 * n + i] = K0 * szz - Srs;
+            s->sig[2 * n + i] = szz - Srs;
+        }
+        s->pc[i] = -p->pc0;        /* b1 = 0, b2 = 1: pbar_c = p_c (Eq. 45) */
+        s->eps_s[i] = 0.0;
+    }
+    double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!x) return -2;
+    current_positions(p, n, s->u, x);
+    s->n_overflow = 0;
+    int rc = rebuild(p, s, x);
+    if (rc < 0) { free(x); return rc; }
+    bond_pass(p, n, x, s->v, 0.0, s->row_ptr, s->col, s->rev, s->cap, s->sig, s->pc,
+              s->eps_s, 0, s->tforce, s->fint, NULL);
+    double wk = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        for (int c = 0; c < 3; c++) {
+            double a = s->fint[c * n + i] / m + p->gravity[c];      /* Eq. 62 */
+            if (is_base(p, i) || (p->lock_lateral && c < 2)) a = 0.0;
+            s->a[c * n + i] = a;
+            wk += 0.5 * m * s->v[c * n + i] * s->v[c * n + i];
+        }
+    free(x);
+    s->step = 0;
+    s->W_int = 0.0; s->W_ext = 0.0; s->W_kin = wk; s->W_kin0 = wk;
+    s->n_plastic = s->n_nonconv = s->n_singular = 0;
+    return 0;
+}
+
+int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
+    if (!params_ok(p)) return -1;
+    const int64_t n = s->n;
+    const double dt = ppmo_time_step(p);
+    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
+    double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* vh = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* f_old = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!x || !vh || !f_old) { free(x); free(vh); free(f_old); return -2; }
+    for (int st = 0; st < n_steps; st++) {
+        memcpy(f_old, s->fint, sizeof(double) * 3 * (size_t)n);
+        /* predictor, Eq. 60-61 with beta1 = 1/2, beta2 = 0; boundary
+         * conditions; displacement, Eq. 64 (Alg. 2 lines 6-8) */
+        for (int64_t i = 0; i < n; i++)
+            for (int c = 0; c < 3; c++) {
+                double v = s->v[c * n + i] + 0.5 * dt * s->a[c * n + i];
+                if (is_base(p, i) || (p->lock_lateral && c < 2)) v = 0.0;
+                vh[c * n + i] = v;
+                s->u[c * n + i] += dt * v;
+            }
+        current_positions(p, n, s->u, x);
+        if (p->rebuild_every > 0 && (s->step + 1) % p->rebuild_every == 0) rebuild(p, s, x);
+        /* internal force, Alg. 1 (Alg. 2 line 9) */
+        pass_counts pcnt;
+        bond_pass(p, n, x, vh, dt, s->row_ptr, s->col, s->rev, s->cap, s->sig, s->pc,
+                  s->eps_s, 1, s->tforce, s->fint, &pcnt);
+        s->n_plastic += pcnt.plastic;
+        s->n_nonconv += pcnt.nonconv;
+        s->n_singular += pcnt.singular;
+        /* acceleration and velocity corrector, Eq. 62-63 */
+        double dWi = 0.0, dWe = 0.0, wk = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            for (int c = 0; c < 3; c++) {
+                double a = s->fint[c * n + i] / m + p->gravity[c];
+                if (is_base(p, i) || (p->lock_lateral && c < 2)) a = 0.0;
+                s->a[c * n + i] = a;
+                double v = vh[c * n + i] + 0.5 * dt * a;
+                s->v[c * n + i] = v;
+                /* energies, Eq. 66-68: stored energy = minus the work of the
+                 * internal force; external work of gravity */
+                dWi += -0.5 * dt * vh[c * n + i] * (f_old[c * n + i] + s->fint[c * n + i]);
+                dWe += 0.5 * dt * vh[c * n + i] * (2.0 * m * p->gravity[c]);
+                wk += 0.5 * m * v * v;
+            }
+        s->W_int += dWi;
+        s->W_ext += dWe;
+        s->W_kin = wk;
+        s->step++;
+    }
+    free(x); free(vh); free(f_old);
+    return 0;
+}
+
+int ppmo_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void ppmo_set_num_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
