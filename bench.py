@@ -1,0 +1,297 @@
+"""Throughput of the per-step bond loop on one GB300 (bond-steps/s).
+
+Workload (default): the 40x40x80 mixed-precision column collapse
+(128,000 points, dx = 2.5 mm, delta = 3.015 dx, suction 20 kPa; family
+rebuilt every 50 steps), inputs seeded and synthetic.  A "step" is one
+explicit Newmark step of the whole path: predictor, family search when due,
+the fused bond kernel, the force gather with the corrector, and the energy
+terms.  The FP64 path is timed on the same column for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.  Under torchrun each rank runs an
+independent replica (the column does not shard); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ppm_inputs as pi  # noqa: E402
+
+WORKLOAD = "collapse_40x40x80_mixed"
+METRIC = "bond-steps/s (mixed path, 40x40x80 column collapse)"
+UNIT = "bond-steps/s"
+# FP32 lanes per SM and SM count of GB300; the ALU roof is lanes x 2 flop x clock
+SMS, LANES = 152, 128
+# algorithmic FP32 flops of the sub-horizon loop: per (bond, family member)
+# membership test 8 flops (3 sub, 3 mul, 2 add); per (bond, sub-horizon
+# member) 30 flops (15 multiply-adds into K~ and A~)
+FLOPS_TEST, FLOPS_PAIR = 8, 30
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(steps: int = 3):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the
+    workload: a 20x20x40 sub-column (same material, dx, suction) for a few
+    steps.  Returns (bond-steps/s, threads, description)."""
+    import oracle
+    cfg = pi.config(WORKLOAD, nx=20, ny=20, nz=40)
+    v0 = pi.initial_velocity(cfg)
+    run = oracle.Run(cfg, v0)
+    run.step(1)                                   # warm-up step
+    t0 = time.perf_counter()
+    run.step(steps)
+    t = time.perf_counter() - t0
+    rate = run.nbonds * steps / t
+    desc = (f"20x20x40 sub-column (16,000 points, {run.nbonds} bonds) of the workload, "
+            f"{steps} steps after 1 warm-up step, FP64 oracle")
+    return rate, oracle.num_threads(), desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    rate, threads, desc = oracle_sample(max(1, min(args.steps, 5)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_path(cfg, precision, steps, warmup, stream_sync):
+    """Device-timed steps of one precision; returns a dict of figures."""
+    import torch
+    from paper_2203_05562_gb300 import Simulation
+    sim = Simulation(cfg, precision=precision)
+    sim.write("v", pi.initial_velocity(cfg))
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    st0 = sim.status()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream_sync()
+    ev0.record(sim.stream)
+    sim.step(steps)
+    ev1.record(sim.stream)
+    torch.cuda.synchronize()
+    stream_sync()
+    ms = ev0.elapsed_time(ev1)
+    st1 = sim.status()
+    return sim, dict(ms=ms, bond_steps=st1["bond_steps"] - st0["bond_steps"],
+                     pairs=st1["pairs"] - st0["pairs"], launches=st1["launches"] - st0["launches"],
+                     nbonds=st1["nbonds"], status=st1)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cfg = pi.config(WORKLOAD)
+    n = pi.num_points(cfg)
+    sampler = ClockSampler(local)
+
+    # ---- device-timed mixed path (the headline) ----
+    barrier()
+    sampler.start()
+    sim, fig = time_path(cfg, "mixed", args.steps, args.warmup, barrier)
+    clocks = sampler.stop()
+    ms = fig["ms"]
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        b = torch.tensor([float(fig["bond_steps"])], device="cuda")
+        dist.all_reduce(b)
+        total_bond_steps = float(b.item())
+    else:
+        total_bond_steps = float(fig["bond_steps"])
+    value = total_bond_steps / (ms * 1e-3)
+
+    # ---- dominant kernel: per-phase CUDA-event times on the launching stream ----
+    phase = sim.step_timed(max(5, min(20, args.steps)))
+    nph = max(5, min(20, args.steps))
+    st = sim.status()
+    bond_ms = phase[1] / nph
+    pairs_per_step = fig["pairs"] / args.steps
+    nb = fig["nbonds"]
+    rp = sim.read("row_ptr")
+    fam_sq = float(np.sum(np.diff(rp).astype(np.float64) ** 2))
+    flops = FLOPS_TEST * fam_sq + FLOPS_PAIR * pairs_per_step
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (bond_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "k_bond<float,0> (fused sub-horizon / constitutive / force state)",
+                "peak_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
+                "bond_kernel_ms": bond_ms, "gather_ms": phase[2] / nph,
+                "predictor_family_ms": phase[0] / nph}
+
+    # ---- FP64 path on the same column (fewer steps: FP64 is ~1/64 rate) ----
+    sim64, fig64 = time_path(cfg, "fp64", args.fp64_steps, 1, barrier)
+    fp64_rate = fig64["bond_steps"] / (fig64["ms"] * 1e-3)
+    del sim64
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    from paper_2203_05562_gb300 import Simulation
+    host_v0 = torch.from_numpy(pi.initial_velocity(cfg).astype(np.float32)).pin_memory()
+    host_u = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    esim = Simulation(cfg, precision="mixed")
+    esim.write("v", host_v0.numpy())
+    esim.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    s0 = esim.status()["bond_steps"]
+    t0 = time.perf_counter()
+    host_u_np = host_u.numpy()
+    esim.write("v", host_v0.numpy())    # this run's input, from pinned host memory
+    for _ in range(args.steps):
+        esim.step(1)
+        esim.read("u", out=host_u_np)   # the step's result back to pinned host memory
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s1 = esim.status()["bond_steps"]
+    e2e = {"value": (s1 - s0) / e2e_s * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_v0.numel() * 4 / args.steps),
+           "d2h_bytes_per_step": int(host_u.numel() * 4)}
+
+    # ---- CPU baseline (oracle, host cores, bounded sample) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, desc = oracle_sample(3)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": n, "bonds": nb, "dx": cfg["dx"],
+                       "horizon": "3.015 dx", "rebuild_every": cfg["rebuild_every"],
+                       "l2": "inputs larger than L2 (force states + family > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
+            "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": fig["launches"],
+            "status": {k: st[k] for k in ("plastic", "nonconv", "singular", "flags")},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * ppm.h -- C ABI of the GB300 (sm_103a) library for the per-time-step bond
+ * loop of updated Lagrangian unsaturated periporomechanics (Menon & Song,
+ * arXiv:2203.05562).
+ *
+ * One explicit step (Alg. 2) is: Newmark predictor and boundary conditions
+ * (Eq. 60-61, 64) -> family search in the current configuration when due
+ * (Eq. 1, Alg. 1 line 1) -> for every bond the sub-horizon shape tensor and
+ * velocity gradient (Eq. 22-26, 55, 57), the critical-state visco-plastic
+ * update at constant suction (Sec. 2.3, Eq. 40-46, 70-76) and the force
+ * state (Eq. 31-32, 51) -> pairwise nodal forces (Eq. 49-50) -> acceleration
+ * and velocity corrector (Eq. 62-63) and the energy terms (Eq. 66-68).
+ *
+ * Conventions: SI units; tension positive; suction s > 0 (p_w = -s).
+ * Per-point vector fields are component-major (f[c*N + i]); the symmetric
+ * stress has 6 components in the order xx, yy, zz, yz, xz, xy.  Point id
+ * of lattice site (ix, iy, iz) of column c is offset[c] + ix + nx*(iy +
+ * ny*iz); columns are stored one after another.  The base layer (iz = 0)
+ * of every column is fixed.
+ *
+ * Ownership: the caller allocates one device workspace of the size
+ * ppm_workspace_size() reports and keeps it alive until ppm_destroy();
+ * the library never calls cudaMalloc.  Host buffers passed to read/write
+ * calls belong to the caller.  All device work is issued on the stream
+ * given to ppm_init() and is asynchronous unless stated otherwise.
+ *
+ * Errors: every function returns PPM_OK (0) or a negative PPM_E* code
+ * synchronously; nothing aborts or traps.  Conditions found on the device
+ * (Newton non-convergence, degenerate shape tensors, non-finite values,
+ * family capacity exceeded) set bits of a status word that ppm_status()
+ * returns.
+ */
+#ifndef PPM_H
+#define PPM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define PPM_OK        0
+#define PPM_EINVAL   -1   /* invalid argument or parameter                  */
+#define PPM_ENOSPACE -2   /* workspace smaller than ppm_workspace_size()    */
+#define PPM_ECUDA    -3   /* a CUDA runtime call failed                     */
+#define PPM_ESTATE   -4   /* call not valid in the context's current state  */
+
+/* device status bits (ppm_counters.status) */
+#define PPM_STATUS_NONCONV        1u  /* a return-map Newton solve did not converge */
+#define PPM_STATUS_SINGULAR       2u  /* a bond had a degenerate shape tensor       */
+#define PPM_STATUS_NONFINITE      4u  /* a non-finite acceleration appeared         */
+#define PPM_STATUS_FAMILY_FULL    8u  /* bonds exceeded the workspace capacity      */
+#define PPM_STATUS_ROW_FULL      16u  /* a point had more than max_family bonds     */
+#define PPM_STATUS_UNSTABLE      32u  /* energy balance of Eq. 69 above 1e-2        */
+
+/* precision of the path */
+#define PPM_FP64  0   /* everything in FP64                                     */
+#define PPM_MIXED 1   /* FP32 kinematics, stress and forces; FP64 shape-tensor
+                         inverse and visco-plastic return solve               */
+
+/* force-state model */
+#define PPM_SUBHORIZON           0  /* Eq. 51: force state on the bond itself      */
+#define PPM_STANDARD             1  /* Sec. 2.1: full-horizon correspondence       */
+#define PPM_SUBHORIZON_CONJUGATE 2  /* Eq. 27-31 as a state over each sub-horizon  */
+
+/* state fields for ppm_read_state / ppm_write_state; element type is
+ * double for PPM_FP64 and float for PPM_MIXED unless noted */
+#define PPM_FIELD_U        0   /* displacement, 3N                           */
+#define PPM_FIELD_V        1   /* velocity, 3N                               */
+#define PPM_FIELD_A        2   /* acceleration, 3N                           */
+#define PPM_FIELD_SIGMA    3   /* effective stress, 6N                       */
+#define PPM_FIELD_PC       4   /* preconsolidation pressure (negative), N   */
+#define PPM_FIELD_EPS_S    5   /* accumulated equivalent shear strain, N     */
+#define PPM_FIELD_FINT     6   /* internal force of the last pass, 3N        */
+#define PPM_FIELD_ROW_PTR  7   /* int32, N+1                                 */
+#define PPM_FIELD_COL      8   /* int32, bonds (ascending within a row)      */
+#define PPM_FIELD_REV      9   /* int32, bonds: index of bond (j,i), -1 none */
+#define PPM_FIELD_TFORCE  10   /* force state per bond, 3 x bonds            */
+
+typedef struct {
+    int32_t nx, ny, nz;          /* lattice of the column (single-column runs)  */
+    int32_t model;               /* PPM_SUBHORIZON / _STANDARD / _CONJUGATE     */
+    double dx, horizon_factor;   /* spacing; horizon delta = factor * dx        */
+    double rho, K, mu;           /* mixture density, bulk and shear modulus     */
+    double M, lambda_t, kappa_t; /* critical-state slope; compression indices   */
+    double pc0, eta;             /* initial preconsolidation (> 0); viscosity   */
+    double suction;              /* constant matric suction (>= 0)              */
+    double vg_alpha, vg_n;       /* van Genuchten S_r(s) parameters             */
+    double b1, b2;               /* Eq. 45; only b1 = 0, b2 = 1 are accepted    */
+    double gravity[3];
+    double dt;                   /* <= 0: 0.3 dx / sqrt((K + 4mu/3) / rho)      */
+    int32_t rebuild_every;       /* family rebuilt before step n+1 when
+                                    (n+1) % R == 0; 0 = never                   */
+    int32_t init_stress;         /* 0: K0 geostatic, 1: zero                    */
+    int32_t visc_form;           /* 0: eta scaled by pc_n^2 (Pa s), 1: literal  */
+    int32_t newton_max_iter;
+    double newton_tol;
+    int32_t lock_lateral;        /* 1: x and y motion suppressed               */
+    int32_t precision;           /* PPM_FP64 or PPM_MIXED                       */
+    int32_t max_family;          /* bond capacity per point (0: 192; max 256)  */
+    int32_t use_graph;           /* 1: replay steps through CUDA graphs         */
+} ppm_params;
+
+/* one column of a batched ensemble; other parameters come from ppm_params */
+typedef struct {
+    int32_t nx, ny, nz, pad_;
+    double suction, M;
+} ppm_column;
+
+typedef struct {
+    int64_t steps;               /* steps taken                                 */
+    int64_t nbonds;              /* bonds of the current family                 */
+    int64_t bond_steps;          /* sum over steps of the bond count            */
+    int64_t plastic;             /* bond updates that took the plastic branch   */
+    int64_t nonconv;             /* Newton solves that did not converge         */
+    int64_t singular;            /* bond updates with a degenerate shape tensor */
+    int64_t rebuilds;            /* family searches done                        */
+    int64_t pairs;               /* sum over updated bonds of the sub-horizon
+                                    size |S_b| (member pairs visited)          */
+    int64_t launches;            /* CUDA kernels this context has issued        */
+    uint32_t status;             /* PPM_STATUS_* bits                           */
+    uint32_t pad_;
+    double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */
+} ppm_counters;
+
+typedef struct ppm_ctx ppm_ctx;
+
+/* Bytes of device workspace needed for these parameters.  n_columns = 0
+ * (cols = NULL) means one column described by p->nx, ny, nz, suction, M. */
+int ppm_workspace_size(const ppm_params* p, int n_columns, const ppm_column* cols,
+                       size_t* bytes);
+
+/* Creates a context on the current CUDA device.  d_workspace: device
+ * pointer to at least ppm_workspace_size() bytes, 256-byte aligned.
+ * cuda_stream: the cudaStream_t to issue all work on (NULL: default
+ * stream).  Initial state (Alg. 2 line 1): u = v = a = 0, effective stress
+ * per init_stress, pc = -pc0.  The family is not built yet. */
+int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d_workspace,
+             size_t bytes, void* cuda_stream, ppm_ctx** out);
+
+/* Family search in the current configuration (Eq. 1): uniform-grid cell
+ * list, then the bond-major CSR family with rows ascending and the reverse
+ * index.  Asynchronous. */
+int ppm_build_families(ppm_ctx* c);
+
+/* Advances n_steps explicit steps (Alg. 2 lines 5-13).  The first call
+ * applies the boundary conditions to the velocities, builds the family if
+ * needed and computes the initial acceleration (Alg. 2 lines 2-3).
+ * Asynchronous; no host synchronisation. */
+int ppm_step(ppm_ctx* c, int n_steps);
+
+/* Like ppm_step but without graph replay, recording CUDA events on the
+ * context's stream around each phase and adding the elapsed milliseconds
+ * to ms[0] (predictor and, when due, the family search), ms[1] (the fused
+ * bond kernel) and ms[2] (gather, corrector and energy terms).
+ * Synchronises the stream after every step. */
+int ppm_step_timed(ppm_ctx* c, int n_steps, double ms[3]);
+
+/* Copies a state field (PPM_FIELD_*) to dst (device pointer if
+ * dst_is_device, else host).  bytes must be at least the field's size.
+ * Synchronises the stream when dst is a host pointer. */
+int ppm_read_state(ppm_ctx* c, int field, void* dst, size_t bytes, int dst_is_device);
+
+/* Overwrites a state field from src (same layout and type as read).
+ * Writing PPM_FIELD_U marks the family as stale (rebuilt before the next
+ * step).  Family fields are read-only. */
+int ppm_write_state(ppm_ctx* c, int field, const void* src, size_t bytes, int src_is_device);
+
+/* Number of bonds of the current family (synchronises the stream). */
+int ppm_num_bonds(ppm_ctx* c, int64_t* nbonds);
+
+/* Synchronises the stream and returns the counters and status word. */
+int ppm_status(ppm_ctx* c, ppm_counters* out);
+
+/* Time step in use and total number of points. */
+int ppm_info(const ppm_ctx* c, double* dt, int64_t* npoints);
+
+const char* ppm_error_string(int code);
+
+/* sizeof of the ABI structs as compiled into the library, so that a
+ * binding can check its own layout: which = 0 ppm_params, 1 ppm_column,
+ * 2 ppm_counters; 0 for anything else.  Needs no GPU. */
+size_t ppm_struct_size(int which);
+
+/* Frees host-side resources (graphs, events).  The workspace stays the
+ * caller's. */
+void ppm_destroy(ppm_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,118 @@
+// Internal declarations of the sm_103a library (kernels + host runtime).
+// Not part of the public ABI; see include/ppm.h for that.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ppm.h"
+
+namespace ppm {
+
+constexpr int kMaxRow = 256;          // hard cap of bonds per point (smem staging)
+constexpr int kDefaultMaxFamily = 192;
+constexpr int kBondThreads = 128;     // threads per point in the fused bond kernel
+constexpr int kWarpPointsPerBlock = 8;  // family / gather kernels: one warp per point
+constexpr int kLatBits = 10;          // packed lattice index: ix | iy << 10 | iz << 20
+constexpr int kLatMask = (1 << kLatBits) - 1;
+
+__host__ __device__ __forceinline__ int lat_x(int l) { return l & kLatMask; }
+__host__ __device__ __forceinline__ int lat_y(int l) { return (l >> kLatBits) & kLatMask; }
+__host__ __device__ __forceinline__ int lat_z(int l) { return l >> (2 * kLatBits); }
+
+// per-column constants (ensembles have one entry per column)
+struct ColumnConst {
+    double M;       // critical-state slope
+    double Srs;     // S_r * suction: total stress = effective + Srs * 1
+    int32_t nx, ny, nz, pad;
+    int64_t offset; // first point id of the column
+};
+
+// device-resident counters and status word
+struct DevCounters {
+    unsigned long long plastic, nonconv, singular, rebuilds, bond_steps, pairs;
+    unsigned int status, pad;
+    int family_ok, pad2;
+    double W_int, W_ext, W_kin, W_kin0;
+};
+
+// uniform cell grid of the family search (device-computed)
+struct CellGrid {
+    double lo[3];
+    double h, inv_h;
+    int dims[3];
+    int ncell;      // cells per column
+};
+
+// constants of the time step shared by all kernels
+struct StepConst {
+    double dx, inv_dx, delta2;   // delta2 = delta * delta in m^2 (FP64 tests)
+    float hf2f;                   // (delta / dx)^2 for FP32 lattice-unit tests
+    double dt, rho, K, mu, lk, eta, tol;
+    double g[3];
+    int visc_form, max_iter, model, lock_lateral;
+    int npoints, ncols, max_family, pad;
+    long long cap;               // bond capacity
+};
+
+// device pointers of one context (Real = double for FP64, float for mixed)
+template <typename Real>
+struct DevState {
+    int32_t* lat;        // packed lattice index, N
+    int32_t* colid;      // column of each point, N
+    const ColumnConst* cols;
+    Real* u;             // 3N
+    float* ulo;          // 3N compensation of u (mixed only; else null)
+    Real* v;             // 3N
+    Real* vh;            // 3N half-step velocity
+    Real* a;             // 3N
+    Real* sig;           // 6N
+    Real* pc;            // N
+    Real* eps;           // N
+    Real* fint;          // 3N
+    Real* tsum;          // 3N sum of own force states (scaled)
+    int32_t* row_ptr;    // N+1
+    int32_t* col;        // cap
+    int32_t* rev;        // cap
+    Real* T;             // 3 x cap scaled force state
+    double* epart;       // energy partials, 3 x gather blocks
+    DevCounters* ctr;
+    // family scratch
+    CellGrid* grid;
+    long long* bbox;     // 6 ordered-int encodings (min xyz, max xyz)
+    int32_t* cellkey;    // N
+    int32_t* cellcnt;    // ncell_cap + 1
+    int32_t* cellstart;  // ncell_cap + 1
+    int32_t* cellfill;   // ncell_cap
+    int32_t* sorted;     // N
+    int32_t* rowlen;     // N + 1
+    int32_t* scanbuf;    // block sums of the scans
+    int ncell_cap;
+};
+
+// ---- launchers (family.cu) ----
+// *nlaunch (if not null) is incremented by the number of kernels launched
+template <typename Real>
+cudaError_t launch_family_build(const DevState<Real>& s, const StepConst& k, cudaStream_t st,
+                                long long* nlaunch);
+// exclusive scan of n int32 values in place (n <= 16M); scanbuf >= 8192 ints
+cudaError_t launch_exclusive_scan(int32_t* data, int n, int32_t* scanbuf, cudaStream_t st,
+                                  long long* nlaunch);
+
+// ---- launchers (bond.cu) ----
+template <typename Real>
+cudaError_t launch_init_state(const DevState<Real>& s, const StepConst& k, int init_stress,
+                              double pc0, cudaStream_t st);
+template <typename Real>
+cudaError_t launch_apply_velocity_bc(const DevState<Real>& s, const StepConst& k, cudaStream_t st);
+template <typename Real>
+cudaError_t launch_predictor(const DevState<Real>& s, const StepConst& k, cudaStream_t st);
+template <typename Real>
+cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, int update,
+                        cudaStream_t st);
+template <typename Real>
+cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt, int initial,
+                          int gather_blocks, cudaStream_t st);
+cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
+                                 const int32_t* row_ptr, int npoints, cudaStream_t st);
+
+}  // namespace ppm

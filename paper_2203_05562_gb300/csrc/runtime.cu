@@ -1,0 +1,570 @@
+// Host runtime behind the C ABI of include/ppm.h: parameter checks,
+// workspace carving (the library never allocates device memory), the step
+// sequence of Alg. 2, CUDA-graph replay of whole steps, state transfer and
+// the status word.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ppm_internal.cuh"
+
+using namespace ppm;
+
+struct ppm_ctx {
+    ppm_params p;
+    int ncols;
+    std::vector<ColumnConst> cols;
+    int64_t N;
+    long long cap;
+    int ncell_cap;
+    int gather_blocks;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    StepConst k;
+    DevState<double> sd;
+    DevState<float> sf;
+    ColumnConst* d_cols;
+    bool started;
+    bool family_built;
+    int64_t step;
+    cudaGraphExec_t g_plain, g_rebuild;
+    cudaEvent_t ev[8];
+    bool events_ok;
+    long long launches;          // kernels issued (graph replays count their kernels)
+    long long launches_plain, launches_rebuild;   // kernels per captured step graph
+};
+
+namespace {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Offsets of every buffer in the caller's workspace.
+struct Layout {
+    size_t total = 0;
+    template <typename T>
+    T* take(char* base, size_t count) {
+        size_t off = total;
+        total = align_up(total + sizeof(T) * (count > 0 ? count : 1), 256);
+        return base ? reinterpret_cast<T*>(base + off) : nullptr;
+    }
+};
+
+double saturation(double s, double alpha, double n) {
+    if (s <= 0.0) return 1.0;
+    return pow(1.0 + pow(alpha * s, n), -(1.0 - 1.0 / n));
+}
+
+int check_params(const ppm_params* p) {
+    if (!p) return PPM_EINVAL;
+    if (!(p->dx > 0) || !(p->horizon_factor > 0) || !(p->rho > 0)) return PPM_EINVAL;
+    if (!(p->K > 0) || !(p->mu > 0) || !(p->M > 0)) return PPM_EINVAL;
+    if (!(p->lambda_t > p->kappa_t) || !(p->eta > 0) || !(p->pc0 > 0)) return PPM_EINVAL;
+    if (p->b1 != 0.0 || p->b2 != 1.0) return PPM_EINVAL;
+    if (p->model < 0 || p->model > 2) return PPM_EINVAL;
+    if (p->precision != PPM_FP64 && p->precision != PPM_MIXED) return PPM_EINVAL;
+    if (p->newton_max_iter < 1 || !(p->newton_tol > 0)) return PPM_EINVAL;
+    if (p->max_family < 0 || p->max_family > kMaxRow) return PPM_EINVAL;
+    if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
+        return PPM_EINVAL;
+    return PPM_OK;
+}
+
+int collect_columns(const ppm_params* p, int n_columns, const ppm_column* cols,
+                    std::vector<ColumnConst>& out, int64_t* N) {
+    out.clear();
+    int64_t off = 0;
+    const int nc = n_columns > 0 ? n_columns : 1;
+    if (n_columns > 0 && !cols) return PPM_EINVAL;
+    for (int c = 0; c < nc; c++) {
+        int nx = n_columns > 0 ? cols[c].nx : p->nx;
+        int ny = n_columns > 0 ? cols[c].ny : p->ny;
+        int nz = n_columns > 0 ? cols[c].nz : p->nz;
+        double s = n_columns > 0 ? cols[c].suction : p->suction;
+        double M = n_columns > 0 ? cols[c].M : p->M;
+        if (nx < 1 || ny < 1 || nz < 1 || nx > kLatMask + 1 || ny > kLatMask + 1 ||
+            nz > kLatMask + 1 || s < 0 || !(M > 0))
+            return PPM_EINVAL;
+        ColumnConst cc;
+        cc.M = M;
+        cc.Srs = saturation(s, p->vg_alpha, p->vg_n) * s;
+        cc.nx = nx; cc.ny = ny; cc.nz = nz; cc.pad = 0;
+        cc.offset = off;
+        out.push_back(cc);
+        off += (int64_t)nx * ny * nz;
+    }
+    *N = off;
+    if (off < 1 || off > (1LL << 27)) return PPM_EINVAL;
+    return PPM_OK;
+}
+
+// shared by ppm_workspace_size and ppm_init
+template <typename Real>
+void carve(Layout& L, char* base, int64_t N, long long cap, int ncell_cap, int gather_blocks,
+           int ncols, bool mixed, DevState<Real>& s, ColumnConst** d_cols) {
+    const size_t n = (size_t)N;
+    s.lat = L.take<int32_t>(base, n);
+    s.colid = L.take<int32_t>(base, n);
+    *d_cols = L.take<ColumnConst>(base, (size_t)ncols);
+    s.cols = *d_cols;
+    s.u = L.take<Real>(base, 3 * n);
+    s.ulo = mixed ? L.take<float>(base, 3 * n) : nullptr;
+    s.v = L.take<Real>(base, 3 * n);
+    s.vh = L.take<Real>(base, 3 * n);
+    s.a = L.take<Real>(base, 3 * n);
+    s.sig = L.take<Real>(base, 6 * n);
+    s.pc = L.take<Real>(base, n);
+    s.eps = L.take<Real>(base, n);
+    s.fint = L.take<Real>(base, 3 * n);
+    s.tsum = L.take<Real>(base, 3 * n);
+    s.row_ptr = L.take<int32_t>(base, n + 1);
+    s.col = L.take<int32_t>(base, (size_t)cap);
+    s.rev = L.take<int32_t>(base, (size_t)cap);
+    s.T = L.take<Real>(base, 3 * (size_t)cap);
+    s.epart = L.take<double>(base, 3 * (size_t)gather_blocks);
+    s.ctr = L.take<DevCounters>(base, 1);
+    s.grid = L.take<CellGrid>(base, 1);
+    s.bbox = L.take<long long>(base, 6);
+    s.cellkey = L.take<int32_t>(base, n);
+    s.cellcnt = L.take<int32_t>(base, (size_t)ncell_cap + 1);
+    s.cellstart = L.take<int32_t>(base, (size_t)ncell_cap + 1);
+    s.cellfill = L.take<int32_t>(base, (size_t)ncell_cap);
+    s.sorted = L.take<int32_t>(base, n);
+    s.rowlen = L.take<int32_t>(base, n + 1);
+    s.scanbuf = L.take<int32_t>(base, 8192);
+    s.ncell_cap = ncell_cap;
+}
+
+struct Sizes {
+    int64_t N;
+    long long cap;
+    int ncell_cap, gather_blocks, max_family;
+};
+
+Sizes sizes_for(const ppm_params* p, int64_t N) {
+    Sizes z;
+    z.N = N;
+    z.max_family = p->max_family > 0 ? p->max_family : kDefaultMaxFamily;
+    z.cap = (long long)N * z.max_family;
+    if (z.cap > 0x7fffffffLL) z.cap = 0x7fffffffLL;
+    z.ncell_cap = (int)((2 * N > 4096) ? 2 * N : 4096);
+    long long gb = (N + kWarpPointsPerBlock - 1) / kWarpPointsPerBlock;
+    z.gather_blocks = (int)(gb < 4096 ? gb : 4096);
+    return z;
+}
+
+size_t workspace_bytes(const ppm_params* p, int ncols, const Sizes& z) {
+    Layout L;
+    ColumnConst* dc;
+    if (p->precision == PPM_FP64) {
+        DevState<double> s;
+        carve<double>(L, nullptr, z.N, z.cap, z.ncell_cap, z.gather_blocks, ncols, false, s, &dc);
+    } else {
+        DevState<float> s;
+        carve<float>(L, nullptr, z.N, z.cap, z.ncell_cap, z.gather_blocks, ncols, true, s, &dc);
+    }
+    return L.total;
+}
+
+#define CU(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return PPM_ECUDA; \
+    } while (0)
+
+template <typename Real>
+int run_family(ppm_ctx* c, const DevState<Real>& s) {
+    CU(launch_family_build<Real>(s, c->k, c->stream, &c->launches));
+    c->family_built = true;
+    return PPM_OK;
+}
+
+template <typename Real>
+int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
+    CU(launch_apply_velocity_bc<Real>(s, c->k, c->stream));
+    if (!c->family_built) {
+        int rc = run_family<Real>(c, s);
+        if (rc) return rc;
+    }
+    CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
+    CU(launch_gather<Real>(s, c->k, 0.0, 1, c->gather_blocks, c->stream));
+    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 1, s.row_ptr, c->k.npoints, c->stream));
+    c->launches += 4;
+    return PPM_OK;
+}
+
+// one explicit step (Alg. 2 lines 5-13) issued on stream st; ev (optional)
+// records phase boundaries: 0 start, 1 after predictor+family, 2 after
+// bond, 3 after gather
+template <typename Real>
+int issue_step(ppm_ctx* c, const DevState<Real>& s, bool rebuild, cudaStream_t st,
+               cudaEvent_t* ev, long long* nlaunch) {
+    if (ev) CU(cudaEventRecord(ev[0], st));
+    CU(launch_predictor<Real>(s, c->k, st));
+    if (rebuild) CU(launch_family_build<Real>(s, c->k, st, nlaunch));
+    *nlaunch += 4;   // predictor, bond, gather, energy reduction
+    if (ev) CU(cudaEventRecord(ev[1], st));
+    CU(launch_bond<Real>(s, c->k, c->k.dt, 1, st));
+    if (ev) CU(cudaEventRecord(ev[2], st));
+    CU(launch_gather<Real>(s, c->k, c->k.dt, 0, c->gather_blocks, st));
+    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 0, s.row_ptr, c->k.npoints, st));
+    if (ev) CU(cudaEventRecord(ev[3], st));
+    return PPM_OK;
+}
+
+template <typename Real>
+int capture_step(ppm_ctx* c, const DevState<Real>& s, bool rebuild, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    long long nl = 0;
+    int rc = issue_step<Real>(c, s, rebuild, c->cap_stream, nullptr, &nl);
+    (rebuild ? c->launches_rebuild : c->launches_plain) = nl;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc != PPM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return PPM_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? PPM_OK : PPM_ECUDA;
+}
+
+bool rebuild_due(const ppm_ctx* c) {
+    return c->p.rebuild_every > 0 && (c->step + 1) % c->p.rebuild_every == 0;
+}
+
+template <typename Real>
+int do_steps(ppm_ctx* c, const DevState<Real>& s, int n_steps, double* phase_ms) {
+    if (!c->started) {
+        int rc = issue_initial<Real>(c, s);
+        if (rc) return rc;
+        c->started = true;
+    }
+    for (int t = 0; t < n_steps; t++) {
+        const bool rebuild = rebuild_due(c);
+        if (phase_ms) {
+            int rc = issue_step<Real>(c, s, rebuild, c->stream, c->ev, &c->launches);
+            if (rc) return rc;
+            CU(cudaEventSynchronize(c->ev[3]));
+            float ms;
+            CU(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1])); phase_ms[0] += ms;
+            CU(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2])); phase_ms[1] += ms;
+            CU(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3])); phase_ms[2] += ms;
+        } else if (c->p.use_graph) {
+            cudaGraphExec_t* g = rebuild ? &c->g_rebuild : &c->g_plain;
+            if (!*g) {
+                int rc = capture_step<Real>(c, s, rebuild, g);
+                if (rc) return rc;
+            }
+            CU(cudaGraphLaunch(*g, c->stream));
+            c->launches += rebuild ? c->launches_rebuild : c->launches_plain;
+        } else {
+            int rc = issue_step<Real>(c, s, rebuild, c->stream, nullptr, &c->launches);
+            if (rc) return rc;
+        }
+        c->step++;
+    }
+    CU(cudaGetLastError());
+    return PPM_OK;
+}
+
+struct FieldView {
+    void* ptr;
+    size_t bytes;
+    size_t stride_bytes;   // for TFORCE: bytes between components on device
+    int ncomp;
+};
+
+int field_view(ppm_ctx* c, int field, int64_t nbonds, FieldView* v) {
+    const size_t n = (size_t)c->N;
+    const bool f64 = c->p.precision == PPM_FP64;
+    const size_t rs = f64 ? sizeof(double) : sizeof(float);
+    void* base = nullptr;
+    size_t count = 0;
+    v->ncomp = 1;
+    v->stride_bytes = 0;
+#define PICK(member) (f64 ? (void*)c->sd.member : (void*)c->sf.member)
+    switch (field) {
+        case PPM_FIELD_U: base = PICK(u); count = 3 * n; break;
+        case PPM_FIELD_V: base = PICK(v); count = 3 * n; break;
+        case PPM_FIELD_A: base = PICK(a); count = 3 * n; break;
+        case PPM_FIELD_SIGMA: base = PICK(sig); count = 6 * n; break;
+        case PPM_FIELD_PC: base = PICK(pc); count = n; break;
+        case PPM_FIELD_EPS_S: base = PICK(eps); count = n; break;
+        case PPM_FIELD_FINT: base = PICK(fint); count = 3 * n; break;
+        case PPM_FIELD_ROW_PTR:
+            v->ptr = f64 ? (void*)c->sd.row_ptr : (void*)c->sf.row_ptr;
+            v->bytes = sizeof(int32_t) * (n + 1);
+            return PPM_OK;
+        case PPM_FIELD_COL:
+            v->ptr = f64 ? (void*)c->sd.col : (void*)c->sf.col;
+            v->bytes = sizeof(int32_t) * (size_t)nbonds;
+            return PPM_OK;
+        case PPM_FIELD_REV:
+            v->ptr = f64 ? (void*)c->sd.rev : (void*)c->sf.rev;
+            v->bytes = sizeof(int32_t) * (size_t)nbonds;
+            return PPM_OK;
+        case PPM_FIELD_TFORCE:
+            v->ptr = PICK(T);
+            v->bytes = rs * (size_t)nbonds;
+            v->stride_bytes = rs * (size_t)c->cap;
+            v->ncomp = 3;
+            return PPM_OK;
+        default: return PPM_EINVAL;
+    }
+#undef PICK
+    v->ptr = base;
+    v->bytes = rs * count;
+    return PPM_OK;
+}
+
+int read_nbonds(ppm_ctx* c, int64_t* nb) {
+    int32_t* rp = c->p.precision == PPM_FP64 ? c->sd.row_ptr : c->sf.row_ptr;
+    int32_t h = 0;
+    CU(cudaMemcpyAsync(&h, rp + c->N, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    *nb = h;
+    return PPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppm_workspace_size(const ppm_params* p, int n_columns, const ppm_column* cols, size_t* bytes) {
+    if (!bytes) return PPM_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    std::vector<ColumnConst> cc;
+    int64_t N = 0;
+    rc = collect_columns(p, n_columns, cols, cc, &N);
+    if (rc) return rc;
+    Sizes z = sizes_for(p, N);
+    *bytes = workspace_bytes(p, (int)cc.size(), z);
+    return PPM_OK;
+}
+
+int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d_workspace,
+             size_t bytes, void* cuda_stream, ppm_ctx** out) {
+    if (!out) return PPM_EINVAL;
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!d_workspace || ((uintptr_t)d_workspace & 255u)) return PPM_EINVAL;
+    ppm_ctx* c = new (std::nothrow) ppm_ctx();
+    if (!c) return PPM_EINVAL;
+    c->p = *p;
+    rc = collect_columns(p, n_columns, cols, c->cols, &c->N);
+    if (rc) { delete c; return rc; }
+    c->ncols = (int)c->cols.size();
+    Sizes z = sizes_for(p, c->N);
+    if (bytes < workspace_bytes(p, c->ncols, z)) { delete c; return PPM_ENOSPACE; }
+    c->cap = z.cap;
+    c->ncell_cap = z.ncell_cap;
+    c->gather_blocks = z.gather_blocks;
+    c->stream = (cudaStream_t)cuda_stream;
+    Layout L;
+    char* base = (char*)d_workspace;
+    const bool mixed = p->precision == PPM_MIXED;
+    if (mixed) carve<float>(L, base, c->N, c->cap, c->ncell_cap, c->gather_blocks, c->ncols, true, c->sf, &c->d_cols);
+    else carve<double>(L, base, c->N, c->cap, c->ncell_cap, c->gather_blocks, c->ncols, false, c->sd, &c->d_cols);
+
+    // step constants
+    StepConst& k = c->k;
+    memset(&k, 0, sizeof(k));
+    const double delta = p->horizon_factor * p->dx;
+    k.dx = p->dx;
+    k.inv_dx = 1.0 / p->dx;
+    k.delta2 = delta * delta;
+    k.hf2f = (float)(p->horizon_factor * p->horizon_factor);
+    k.dt = p->dt > 0 ? p->dt : 0.3 * p->dx / sqrt((p->K + 4.0 * p->mu / 3.0) / p->rho);
+    k.rho = p->rho; k.K = p->K; k.mu = p->mu;
+    k.lk = p->lambda_t - p->kappa_t;
+    k.eta = p->eta;
+    k.tol = p->newton_tol;
+    for (int d = 0; d < 3; d++) k.g[d] = p->gravity[d];
+    k.visc_form = p->visc_form;
+    k.max_iter = p->newton_max_iter;
+    k.model = p->model;
+    k.lock_lateral = p->lock_lateral;
+    k.npoints = (int)c->N;
+    k.ncols = c->ncols;
+    k.max_family = z.max_family;
+    k.cap = c->cap;
+
+    // lattice indices and column ids (host-built, copied once)
+    std::vector<int32_t> lat((size_t)c->N), colid((size_t)c->N);
+    for (int ci = 0; ci < c->ncols; ci++) {
+        const ColumnConst& cc = c->cols[ci];
+        int64_t id = cc.offset;
+        for (int iz = 0; iz < cc.nz; iz++)
+            for (int iy = 0; iy < cc.ny; iy++)
+                for (int ix = 0; ix < cc.nx; ix++, id++) {
+                    lat[(size_t)id] = ix | (iy << kLatBits) | (iz << (2 * kLatBits));
+                    colid[(size_t)id] = ci;
+                }
+    }
+    int32_t* d_lat = mixed ? c->sf.lat : c->sd.lat;
+    int32_t* d_colid = mixed ? c->sf.colid : c->sd.colid;
+    DevCounters* d_ctr = mixed ? c->sf.ctr : c->sd.ctr;
+    cudaError_t e = cudaSuccess;
+    e = cudaMemcpyAsync(d_lat, lat.data(), sizeof(int32_t) * lat.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_colid, colid.data(), sizeof(int32_t) * colid.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_cols, c->cols.data(), sizeof(ColumnConst) * c->cols.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(DevCounters), c->stream);
+    int32_t* rp = mixed ? c->sf.row_ptr : c->sd.row_ptr;
+    if (e == cudaSuccess) e = cudaMemsetAsync(rp, 0, sizeof(int32_t) * ((size_t)c->N + 1), c->stream);
+    if (e == cudaSuccess) {
+        e = mixed ? launch_init_state<float>(c->sf, k, p->init_stress, p->pc0, c->stream)
+                  : launch_init_state<double>(c->sd, k, p->init_stress, p->pc0, c->stream);
+    }
+    // host copies of lat/colid must outlive the async copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    c->events_ok = true;
+    for (int q = 0; q < 8 && e == cudaSuccess; q++) e = cudaEventCreate(&c->ev[q]);
+    if (e != cudaSuccess) {
+        delete c;
+        return PPM_ECUDA;
+    }
+    c->started = false;
+    c->family_built = false;
+    c->step = 0;
+    c->g_plain = nullptr;
+    c->g_rebuild = nullptr;
+    c->launches = 1;   // initial-state kernel
+    *out = c;
+    return PPM_OK;
+}
+
+int ppm_build_families(ppm_ctx* c) {
+    if (!c) return PPM_EINVAL;
+    return c->p.precision == PPM_FP64 ? run_family<double>(c, c->sd) : run_family<float>(c, c->sf);
+}
+
+int ppm_step(ppm_ctx* c, int n_steps) {
+    if (!c || n_steps < 0) return PPM_EINVAL;
+    return c->p.precision == PPM_FP64 ? do_steps<double>(c, c->sd, n_steps, nullptr)
+                                      : do_steps<float>(c, c->sf, n_steps, nullptr);
+}
+
+/* Like ppm_step, without graphs, timing each phase with CUDA events on the
+ * context's stream: ms[0] predictor (+ family search when due), ms[1] the
+ * fused bond kernel, ms[2] gather + corrector + energies (accumulated). */
+int ppm_step_timed(ppm_ctx* c, int n_steps, double* ms) {
+    if (!c || n_steps < 0 || !ms) return PPM_EINVAL;
+    return c->p.precision == PPM_FP64 ? do_steps<double>(c, c->sd, n_steps, ms)
+                                      : do_steps<float>(c, c->sf, n_steps, ms);
+}
+
+int ppm_num_bonds(ppm_ctx* c, int64_t* nbonds) {
+    if (!c || !nbonds) return PPM_EINVAL;
+    return read_nbonds(c, nbonds);
+}
+
+int ppm_read_state(ppm_ctx* c, int field, void* dst, size_t bytes, int dst_is_device) {
+    if (!c || !dst) return PPM_EINVAL;
+    int64_t nb = 0;
+    if (field == PPM_FIELD_COL || field == PPM_FIELD_REV || field == PPM_FIELD_TFORCE) {
+        int rc = read_nbonds(c, &nb);
+        if (rc) return rc;
+    }
+    FieldView v;
+    int rc = field_view(c, field, nb, &v);
+    if (rc) return rc;
+    if (bytes < v.bytes * (size_t)v.ncomp) return PPM_EINVAL;
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int q = 0; q < v.ncomp; q++)
+        CU(cudaMemcpyAsync((char*)dst + q * v.bytes, (char*)v.ptr + q * v.stride_bytes, v.bytes,
+                           kind, c->stream));
+    if (!dst_is_device) CU(cudaStreamSynchronize(c->stream));
+    return PPM_OK;
+}
+
+int ppm_write_state(ppm_ctx* c, int field, const void* src, size_t bytes, int src_is_device) {
+    if (!c || !src) return PPM_EINVAL;
+    if (field == PPM_FIELD_ROW_PTR || field == PPM_FIELD_COL || field == PPM_FIELD_REV ||
+        field == PPM_FIELD_TFORCE)
+        return PPM_EINVAL;
+    FieldView v;
+    int rc = field_view(c, field, 0, &v);
+    if (rc) return rc;
+    if (bytes < v.bytes) return PPM_EINVAL;
+    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CU(cudaMemcpyAsync(v.ptr, src, v.bytes, kind, c->stream));
+    if (field == PPM_FIELD_U && c->p.precision == PPM_MIXED)
+        CU(cudaMemsetAsync(c->sf.ulo, 0, sizeof(float) * 3 * (size_t)c->N, c->stream));
+    if (!src_is_device) CU(cudaStreamSynchronize(c->stream));
+    return PPM_OK;
+}
+
+int ppm_status(ppm_ctx* c, ppm_counters* out) {
+    if (!c || !out) return PPM_EINVAL;
+    DevCounters h;
+    DevCounters* d = c->p.precision == PPM_FP64 ? c->sd.ctr : c->sf.ctr;
+    CU(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    int64_t nb = 0;
+    int rc = read_nbonds(c, &nb);
+    if (rc) return rc;
+    memset(out, 0, sizeof(*out));
+    out->steps = c->step;
+    out->nbonds = nb;
+    out->bond_steps = (int64_t)h.bond_steps;
+    out->plastic = (int64_t)h.plastic;
+    out->nonconv = (int64_t)h.nonconv;
+    out->singular = (int64_t)h.singular;
+    out->rebuilds = (int64_t)h.rebuilds;
+    out->pairs = (int64_t)h.pairs;
+    out->launches = c->launches;
+    out->status = h.status;
+    out->W_int = h.W_int;
+    out->W_ext = h.W_ext;
+    out->W_kin = h.W_kin;
+    out->W_kin0 = h.W_kin0;
+    return PPM_OK;
+}
+
+int ppm_info(const ppm_ctx* c, double* dt, int64_t* npoints) {
+    if (!c) return PPM_EINVAL;
+    if (dt) *dt = c->k.dt;
+    if (npoints) *npoints = c->N;
+    return PPM_OK;
+}
+
+const char* ppm_error_string(int code) {
+    switch (code) {
+        case PPM_OK: return "ok";
+        case PPM_EINVAL: return "invalid argument or parameter";
+        case PPM_ENOSPACE: return "workspace smaller than ppm_workspace_size()";
+        case PPM_ECUDA: return "a CUDA runtime call failed";
+        case PPM_ESTATE: return "call not valid in the context's current state";
+        default: return "unknown error";
+    }
+}
+
+size_t ppm_struct_size(int which) {
+    switch (which) {
+        case 0: return sizeof(ppm_params);
+        case 1: return sizeof(ppm_column);
+        case 2: return sizeof(ppm_counters);
+        default: return 0;
+    }
+}
+
+void ppm_destroy(ppm_ctx* c) {
+    if (!c) return;
+    if (c->g_plain) cudaGraphExecDestroy(c->g_plain);
+    if (c->g_rebuild) cudaGraphExecDestroy(c->g_rebuild);
+    for (int q = 0; q < 8; q++)
+        if (c->ev[q]) cudaEventDestroy(c->ev[q]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every declared symbol, and
+rejects invalid parameters -- all without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import ppm_inputs as pi
+from paper_2203_05562_gb300 import ppm as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ppm_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.library()
+    names = declared_functions()
+    assert "ppm_step" in names and "ppm_init" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_struct_layout_matches_binding():
+    L = P.library()
+    assert L.ppm_struct_size(0) == C.sizeof(P.Params)
+    assert L.ppm_struct_size(1) == C.sizeof(P.Column)
+    assert L.ppm_struct_size(2) == C.sizeof(P.Counters)
+
+
+def _ws(cfg, **kw):
+    p = P.make_params(cfg, **kw)
+    n = C.c_size_t(0)
+    rc = P.library().ppm_workspace_size(C.byref(p), 0, None, C.byref(n))
+    return rc, n.value
+
+
+def test_workspace_size_and_invalid_parameters():
+    cfg = pi.config(0)
+    rc, nbytes = _ws(cfg, precision=P.FP64)
+    assert rc == 0 and nbytes > 0
+    rc2, nbytes_mixed = _ws(cfg, precision=P.MIXED)
+    assert rc2 == 0 and nbytes_mixed < nbytes
+    for bad in (dict(dx=0.0), dict(K=-1.0), dict(b1=0.5), dict(lambda_t=0.01),
+                dict(nz=0), dict(nx=2000), dict(newton_max_iter=0), dict(max_family=300)):
+        rc, _ = _ws(dict(cfg, **bad))
+        assert rc == -1, bad
+    rc, _ = _ws(cfg, model=5)
+    assert rc == -1
+
+
+def test_error_strings():
+    L = P.library()
+    assert L.ppm_error_string(0) == b"ok"
+    assert b"workspace" in L.ppm_error_string(-2)
+
+
+def test_init_rejects_null_and_misaligned_workspace():
+    L = P.library()
+    p = P.make_params(pi.config(0))
+    ctx = C.c_void_p()
+    assert L.ppm_init(C.byref(p), 0, None, None, 0, None, C.byref(ctx)) == -1
+    assert L.ppm_init(C.byref(p), 0, None, C.c_void_p(0x1001), 1 << 30, None, C.byref(ctx)) == -1
+    assert not ctx.value

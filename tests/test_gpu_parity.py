@@ -1,0 +1,164 @@
+"""GPU library against the FP64 CPU oracle on identical seeded inputs.
+
+Tolerances: family CSR and reverse index bit-exact; FP64 path <= 1e-10
+relative (max-norm over a field, relative to the field's max) on every
+state field; mixed path <= 1e-3 relative L2 on displacement.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import ppm_inputs as pi
+from gpu_helpers import gpu_run, oracle_run, rel_inf, rel_l2, state_errors
+
+pytestmark = pytest.mark.gpu
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-3
+
+
+def _family_gpu(cfg, u, columns=None):
+    from paper_2203_05562_gb300 import Simulation
+    sim = Simulation(cfg, columns=columns, precision="fp64")
+    sim.write("u", u)
+    sim.build_families()
+    return sim.read("row_ptr"), sim.read("col"), sim.read("rev")
+
+
+@pytest.mark.parametrize("amp", [0.0, 0.3])
+def test_family_bit_exact_fp64(amp):
+    cfg = pi.small_config(9, 8, 11)
+    u = pi.perturbation(cfg, amp * cfg["dx"], seed=5)
+    rp, col, rev = _family_gpu(cfg, u)
+    X = oracle.reference_positions(cfg) + u
+    orp, ocol, orev = oracle.family(X, cfg["horizon_factor"] * cfg["dx"])
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(col, ocol)
+    assert np.array_equal(rev, orev)
+
+
+def test_family_config0_counts():
+    cfg = pi.config(0)
+    rp, col, rev = _family_gpu(cfg, np.zeros((3, pi.num_points(cfg))))
+    assert len(col) == 179768 and rp[-1] == 179768
+    assert np.all(col[rev] == np.repeat(np.arange(len(rp) - 1), np.diff(rp)))
+
+
+def test_family_ensemble_columns_never_bond():
+    cols = [dict(nx=4, ny=5, nz=6, suction=5e3, M=1.1), dict(nx=3, ny=3, nz=9, suction=0.0, M=1.3),
+            dict(nx=5, ny=4, nz=4, suction=40e3, M=1.0)]
+    cfg = pi.small_config(1, 1, 1)
+    n = sum(c["nx"] * c["ny"] * c["nz"] for c in cols)
+    rp, col, rev = _family_gpu(cfg, np.zeros((3, n)), columns=cols)
+    off = 0
+    for c in cols:
+        cc = dict(cfg, nx=c["nx"], ny=c["ny"], nz=c["nz"])
+        m = pi.num_points(cc)
+        orp, ocol, orev = oracle.family(oracle.reference_positions(cc), cfg["horizon_factor"] * cfg["dx"])
+        assert np.array_equal(rp[off:off + m + 1] - rp[off], orp)
+        assert np.array_equal(col[rp[off]:rp[off + m]] - off, ocol)
+        assert np.array_equal(rev[rp[off]:rp[off + m]] - rp[off], orev)
+        off += m
+
+
+def test_fp64_config0_50_steps_matches_oracle():
+    cfg = pi.config(0)
+    v0 = pi.initial_velocity(cfg)
+    run = oracle_run(cfg, 50, v0)
+    sim = gpu_run(cfg, 50, "fp64", v0=v0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    st = sim.status()
+    ce = run.energies()
+    for key in ("W_int", "W_ext", "W_kin"):
+        assert abs(st[key] - ce[key]) <= FP64_TOL * max(abs(ce[key]), ce["W_kin"]), key
+    assert st["plastic"] == run.counters()["plastic"]
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_fp64_plastic_column_all_models(model):
+    # suction 50 kPa: S_r s = 21.7 kPa exceeds pc0, every bond starts plastic
+    cfg = pi.small_config(6, 5, 7, suction=50e3, model=model, rebuild_every=2)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=3)
+    run = oracle_run(cfg, 8, v0)
+    assert run.counters()["plastic"] > 0
+    sim = gpu_run(cfg, 8, "fp64", v0=v0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    assert sim.status()["plastic"] == run.counters()["plastic"]
+
+
+def test_fp64_switches_zero_stress_locked_no_rebuild():
+    cfg = pi.small_config(5, 6, 8, init_stress=1, lock_lateral=1, rebuild_every=0,
+                          visc_form=1, eta=5e12)
+    v0 = pi.initial_velocity(cfg, std=1e-2, seed=9)
+    run = oracle_run(cfg, 6, v0)
+    sim = gpu_run(cfg, 6, "fp64", v0=v0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+
+
+def test_fp64_ensemble_matches_per_column_oracle():
+    cols = [dict(nx=4, ny=4, nz=6, suction=5e3, M=1.1), dict(nx=3, ny=5, nz=5, suction=45e3, M=1.35)]
+    cfg = pi.small_config(1, 1, 1, rebuild_every=2)
+    n = sum(c["nx"] * c["ny"] * c["nz"] for c in cols)
+    v0 = np.random.default_rng(4).normal(0, 1e-4, size=(3, n))
+    sim = gpu_run(cfg, 5, "fp64", v0=v0, columns=cols)
+    u, sig = sim.read("u"), sim.read("sigma")
+    off = 0
+    for c in cols:
+        cc = dict(cfg, **c)
+        m = pi.num_points(cc)
+        run = oracle_run(cc, 5, v0[:, off:off + m])
+        assert rel_inf(u[:, off:off + m], run.u) <= FP64_TOL
+        assert rel_inf(sig[:, off:off + m], run.sig) <= FP64_TOL
+        off += m
+
+
+def test_mixed_config0_50_steps_within_1e3():
+    cfg = pi.config(0)
+    v0 = pi.initial_velocity(cfg)
+    run = oracle_run(cfg, 50, v0)
+    sim = gpu_run(cfg, 50, "mixed", v0=v0)
+    assert rel_l2(sim.read("u"), run.u) <= MIXED_TOL
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["sigma"] <= MIXED_TOL and err["v"] <= 1e-2, err
+
+
+@pytest.mark.slow
+def test_mixed_config1_first_50_steps_within_1e3():
+    cfg = pi.config(1)
+    v0 = pi.initial_velocity(cfg)
+    run = oracle_run(cfg, 50, v0)
+    sim = gpu_run(cfg, 50, "mixed", v0=v0)
+    assert rel_l2(sim.read("u"), run.u) <= MIXED_TOL
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["sigma"] <= MIXED_TOL, err
+
+
+def test_graph_replay_matches_direct_launches_bitwise():
+    cfg = pi.small_config(7, 6, 9, suction=30e3, rebuild_every=3)
+    v0 = pi.initial_velocity(cfg, std=1e-3)
+    a = gpu_run(cfg, 7, "mixed", v0=v0, use_graph=True)
+    b = gpu_run(cfg, 7, "mixed", v0=v0, use_graph=False)
+    for f in ("u", "v", "a", "sigma", "pc"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+def test_runs_are_deterministic():
+    cfg = pi.config(0)
+    v0 = pi.initial_velocity(cfg)
+    a = gpu_run(cfg, 20, "mixed", v0=v0)
+    b = gpu_run(cfg, 20, "mixed", v0=v0)
+    for f in ("u", "v", "sigma", "pc", "tforce"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (1, 1, 5), (3, 1, 4)])
+def test_degenerate_columns(dims):
+    cfg = pi.small_config(*dims, suction=20e3, model=0)
+    v0 = pi.initial_velocity(cfg, std=1e-3)
+    run = oracle_run(cfg, 4, v0)
+    sim = gpu_run(cfg, 4, "fp64", v0=v0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    assert sim.status()["singular"] == run.counters()["singular"]
