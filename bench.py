@@ -171,11 +171,13 @@ def time_path(cfg, precision, steps, warmup, stream_sync):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warm-up + steps of the mixed path only (for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -196,6 +198,14 @@ def main():
     cfg = pi.config(WORKLOAD)
     n = pi.num_points(cfg)
     sampler = ClockSampler(local)
+    if args.profile_only:
+        from paper_2203_05562_gb300 import Simulation
+        sim = Simulation(cfg, precision="mixed", use_graph=False)
+        sim.write("v", pi.initial_velocity(cfg))
+        sim.step(args.warmup + args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_only": True, "status": sim.status()["flags"]}))
+        return 0
 
     # ---- device-timed mixed path (the headline) ----
     barrier()

@@ -119,6 +119,9 @@ typedef struct {
     int64_t pairs;               /* sum over updated bonds of the sub-horizon
                                     size |S_b| (member pairs visited)          */
     int64_t launches;            /* CUDA kernels this context has issued        */
+    int64_t returns_fp64;        /* plastic returns solved in FP64 (all of them
+                                    in PPM_FP64; in PPM_MIXED those near the
+                                    apex or whose FP32 solve failed)           */
     uint32_t status;             /* PPM_STATUS_* bits                           */
     uint32_t pad_;
     double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */

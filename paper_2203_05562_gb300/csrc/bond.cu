@@ -81,6 +81,28 @@ __device__ __forceinline__ bool inverse_sym_fp64(const double k[6], double inv[6
     return true;
 }
 
+// Mixed path: the cancellation-prone steps -- cofactors and determinant --
+// in FP64 from the FP32 sums; the degeneracy test, the reciprocal of the
+// determinant and the final scaling in FP32 (the result is FP32 either
+// way, so a full FP64 division would change it by at most an ulp).
+__device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K22, float K12,
+                                                  float K02, float K01, float inv[6]) {
+    const double k00 = K00, k11 = K11, k22 = K22, k12 = K12, k02 = K02, k01 = K01;
+    const double c00 = k11 * k22 - k12 * k12;
+    const double c11 = k00 * k22 - k02 * k02;
+    const double c22 = k00 * k11 - k01 * k01;
+    const double c12 = k01 * k02 - k00 * k12;
+    const double c02 = k01 * k12 - k02 * k11;
+    const double c01 = k02 * k12 - k01 * k22;
+    const float det = (float)(k00 * c00 + k01 * c01 + k02 * c02);
+    const float t = (K00 + K11 + K22) * (1.0f / 3.0f);
+    if (!(det > 1e-12f * t * t * t) || det == 0.0f) return false;
+    const float r = 1.0f / det;
+    inv[0] = (float)c00 * r; inv[1] = (float)c11 * r; inv[2] = (float)c22 * r;
+    inv[3] = (float)c12 * r; inv[4] = (float)c02 * r; inv[5] = (float)c01 * r;
+    return true;
+}
+
 struct ReturnConst {
     double K, mu, M2, lk, c, inv_scale;
     double p_tr, q_tr, pc_n;
@@ -159,6 +181,81 @@ __device__ __noinline__ int return_map(const ReturnConst& R, double tol, int max
     }
 }
 
+// Mixed path: the same return solved in FP32, in increments from the trial
+// state, x = (dp, dq, dpc) with p = p_tr + dp, q = q_tr + dq, pc = pc_n + dpc,
+// so that the small corrections keep their precision; Eq. 75 in the form
+// log1p(dpc / pc_n) + c f f_p / (lambda - kappa) = 0.  Stopping rules as in
+// the FP64 solve with an FP32 tolerance.  Returns 1 if converged.
+struct ReturnConstF {
+    float K, mu, M2, lk, c, inv_scale, scale;
+    float p_tr, q_tr, pc_n, tol;
+    int max_iter;
+};
+
+template <bool WANT_J>
+__device__ __forceinline__ void return_residual_f(const ReturnConstF& R, const float x[3],
+                                                  float r[3], float J[9]) {
+    const float pb = R.p_tr + x[0], q = R.q_tr + x[1], pc = R.pc_n + x[2];
+    const float f = q * q / R.M2 + pb * (pb - pc);
+    const float fp = 2.0f * pb - pc;
+    const float fq = 2.0f * q / R.M2;
+    const float fc = -pb;
+    r[0] = (x[0] + R.K * R.c * f * fp) * R.inv_scale;
+    r[1] = (x[1] + 3.0f * R.mu * R.c * f * fq) * R.inv_scale;
+    const float rel = x[2] / R.pc_n;
+    r[2] = (rel > -1.0f) ? log1pf(rel) + R.c * f * fp / R.lk : INFINITY;
+    if (WANT_J) {
+        const float a = R.K * R.c * R.inv_scale, b = 3.0f * R.mu * R.c * R.inv_scale;
+        const float g = R.c / R.lk;
+        J[0] = R.inv_scale + a * (fp * fp + 2.0f * f);
+        J[1] = a * fq * fp;
+        J[2] = a * (fc * fp - f);
+        J[3] = b * fp * fq;
+        J[4] = R.inv_scale + b * (fq * fq + 2.0f * f / R.M2);
+        J[5] = b * fc * fq;
+        J[6] = g * (fp * fp + 2.0f * f);
+        J[7] = g * (fq * fp);
+        J[8] = 1.0f / pc + g * (fc * fp - f);
+    }
+}
+
+__device__ __noinline__ int return_map_f32(const ReturnConstF& R, float x[3]) {
+    x[0] = 0.0f; x[1] = 0.0f; x[2] = 0.0f;
+    float r[3], J[9];
+    for (int it = 0;; it++) {
+        return_residual_f<true>(R, x, r, J);
+        if (fmaxf(fabsf(r[0]), fmaxf(fabsf(r[1]), fabsf(r[2]))) <= R.tol) return 1;
+        if (it >= R.max_iter) return 0;
+        const float m0 = J[4] * J[8] - J[5] * J[7];
+        const float m1 = J[3] * J[8] - J[5] * J[6];
+        const float m2 = J[3] * J[7] - J[4] * J[6];
+        const float det = J[0] * m0 - J[1] * m1 + J[2] * m2;
+        if (det == 0.0f || !isfinite(det)) return 0;
+        const float id = 1.0f / det;
+        float dx[3];
+        dx[0] = (r[0] * m0 - J[1] * (r[1] * J[8] - J[5] * r[2]) + J[2] * (r[1] * J[7] - J[4] * r[2])) * id;
+        dx[1] = (J[0] * (r[1] * J[8] - J[5] * r[2]) - r[0] * m1 + J[2] * (J[3] * r[2] - r[1] * J[6])) * id;
+        dx[2] = (J[0] * (J[4] * r[2] - r[1] * J[7]) - J[1] * (J[3] * r[2] - r[1] * J[6]) + r[0] * m2) * id;
+        const float small = 2e-7f * R.scale;
+        if (fabsf(dx[0]) <= small && fabsf(dx[1]) <= small && fabsf(dx[2]) <= small) return 1;
+        const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        float lam = 1.0f, xt[3], rt[3];
+        bool accepted = false;
+        for (int ls = 0; ls < 20; ls++) {
+            for (int q = 0; q < 3; q++) xt[q] = x[q] - lam * dx[q];
+            return_residual_f<false>(R, xt, rt, nullptr);
+            if (isfinite(rt[0]) && isfinite(rt[1]) && isfinite(rt[2]) &&
+                sqrtf(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]) < rn) {
+                accepted = true;
+                break;
+            }
+            lam *= 0.5f;
+        }
+        if (!accepted) return 0;
+        x[0] = xt[0]; x[1] = xt[1]; x[2] = xt[2];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // constitutive update of one bond (Sec. 2.3; Sec. 3.2.1)
 // ---------------------------------------------------------------------------
@@ -166,15 +263,17 @@ template <typename Real>
 struct BondStress {
     Real sig[6];
     Real pc, des;
-    int plastic, nonconv;
+    int plastic, nonconv, ret64;
 };
 
 template <typename Real>
 __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6], Real pc_n,
-                                                const StepConst& k, double M,
+                                                const StepConst& k, double M, float Mf,
                                                 BondStress<Real>& o) {
-    const Real dt = (Real)k.dt;
-    const Real Kb = (Real)k.K, mu = (Real)k.mu;
+    constexpr bool F64 = sizeof(Real) == 8;
+    const Real dt = F64 ? (Real)k.dt : (Real)k.dtf;
+    const Real Kb = F64 ? (Real)k.K : (Real)k.Kf;
+    const Real mu = F64 ? (Real)k.mu : (Real)k.muf;
     // rate of deformation and spin (Eq. 26)
     const Real D00 = L[0], D11 = L[4], D22 = L[8];
     const Real D12 = (Real)0.5 * (L[5] + L[7]);
@@ -222,42 +321,79 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
     const Real s0 = st[0] - p_tr, s1 = st[1] - p_tr, s2 = st[2] - p_tr;
     const Real q_tr = sqrt((Real)1.5 * (s0 * s0 + s1 * s1 + s2 * s2 +
                                         (Real)2 * (st[3] * st[3] + st[4] * st[4] + st[5] * st[5])));
-    const Real Mr = (Real)M;
+    const Real Mr = F64 ? (Real)M : (Real)Mf;
     const Real f_tr = q_tr * q_tr / (Mr * Mr) + p_tr * (p_tr - pc_n);
     o.plastic = 0;
     o.nonconv = 0;
+    o.ret64 = 0;
     if (!(f_tr > (Real)0)) {
 #pragma unroll
         for (int c = 0; c < 6; c++) o.sig[c] = st[c];
         o.pc = pc_n;
         return;
     }
-    // visco-plastic return in FP64 (both precisions)
-    ReturnConst R;
-    R.K = k.K; R.mu = k.mu; R.M2 = M * M; R.lk = k.lk;
-    R.p_tr = (double)p_tr; R.q_tr = (double)q_tr; R.pc_n = (double)pc_n;
-    const double eta_eff = (k.visc_form == 0) ? k.eta * R.pc_n * R.pc_n : k.eta;
-    R.c = k.dt / eta_eff;
-    double scale = fabs(R.pc_n);
-    if (fabs(R.p_tr) > scale) scale = fabs(R.p_tr);
-    if (R.q_tr > scale) scale = R.q_tr;
-    if (scale < 1.0) scale = 1.0;
-    R.inv_scale = 1.0 / scale;
-    double x[3];
-    const int ok = return_map(R, k.tol, k.max_iter, x);
     o.plastic = 1;
-    o.nonconv = !ok;
-    const Real ratio = (q_tr > (Real)0) ? (Real)(x[1] / R.q_tr) : (Real)0;
-    const Real pn = (Real)x[0];
+    o.ret64 = 0;
+    Real p_new = p_tr, q_new = q_tr, pc_new = pc_n;
+    bool need64 = F64;
+    if constexpr (!F64) {
+        // FP32 return unless the state is near the critical-state apex
+        // (mean stress within 5% of the preconsolidation pressure from
+        // zero, or tensile) or the preconsolidation pressure has nearly
+        // vanished; any FP32 solve that fails is redone in FP64
+        need64 = (p_tr > 0.05f * pc_n) || (pc_n > -100.0f);
+        if (!need64) {
+            ReturnConstF R;
+            R.K = k.Kf; R.mu = k.muf; R.M2 = Mf * Mf; R.lk = (float)k.lk;
+            R.p_tr = p_tr; R.q_tr = q_tr; R.pc_n = pc_n;
+            const float eta_eff = (k.visc_form == 0) ? k.etaf * pc_n * pc_n : k.etaf;
+            R.c = k.dtf / eta_eff;
+            float scale = fmaxf(fmaxf(fabsf(pc_n), fabsf(p_tr)), fmaxf(q_tr, 1.0f));
+            R.scale = scale;
+            R.inv_scale = 1.0f / scale;
+            R.tol = fmaxf((float)k.tol, 2e-6f);
+            R.max_iter = k.max_iter;
+            float x[3];
+            if (return_map_f32(R, x)) {
+                p_new = p_tr + x[0];
+                q_new = q_tr + x[1];
+                pc_new = pc_n + x[2];
+                o.nonconv = 0;
+            } else {
+                need64 = true;
+            }
+        }
+    }
+    if (need64) {
+        // visco-plastic return in FP64
+        ReturnConst R;
+        R.K = k.K; R.mu = k.mu; R.M2 = M * M; R.lk = k.lk;
+        R.p_tr = (double)p_tr; R.q_tr = (double)q_tr; R.pc_n = (double)pc_n;
+        const double eta_eff = (k.visc_form == 0) ? k.eta * R.pc_n * R.pc_n : k.eta;
+        R.c = k.dt / eta_eff;
+        double scale = fabs(R.pc_n);
+        if (fabs(R.p_tr) > scale) scale = fabs(R.p_tr);
+        if (R.q_tr > scale) scale = R.q_tr;
+        if (scale < 1.0) scale = 1.0;
+        R.inv_scale = 1.0 / scale;
+        double x[3];
+        const int ok = return_map(R, k.tol, k.max_iter, x);
+        o.nonconv = !ok;
+        o.ret64 = 1;
+        p_new = (Real)x[0];
+        q_new = (Real)x[1];
+        pc_new = (Real)(x[2] > -1.0 ? -1.0 : x[2]);
+    }
+    const Real ratio = (q_tr > (Real)0) ? q_new / q_tr : (Real)0;
+    const Real pn = p_new;
     o.sig[0] = pn + ratio * s0;
     o.sig[1] = pn + ratio * s1;
     o.sig[2] = pn + ratio * s2;
     o.sig[3] = ratio * st[3];
     o.sig[4] = ratio * st[4];
     o.sig[5] = ratio * st[5];
-    double pcn = x[2];
-    if (pcn > -1.0) pcn = -1.0;   // floor at the apex
-    o.pc = (Real)pcn;
+    if (pc_new > (Real)-1) pc_new = (Real)-1;   // floor at the apex
+    o.pc = pc_new;
 }
 
 // deterministic block sum: butterfly within warps, then warps in order
@@ -285,7 +421,7 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sm)[NV]) {
 // fused bond kernel: one CTA per point, one thread per bond
 // ---------------------------------------------------------------------------
 template <typename Real, int MODEL>
-__global__ void __launch_bounds__(kBondThreads)
+__global__ void __launch_bounds__(kBondThreads, sizeof(Real) == 4 ? 4 : 2)
 k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     constexpr bool F64 = sizeof(Real) == 8;
     constexpr int NW = kBondThreads / 32;
@@ -294,7 +430,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     __shared__ double s_p[F64 ? 3 : 1][F64 ? kMaxRow : 1];    // FP64: absolute x_k
     __shared__ Real s_M[MODEL == 2 ? 9 : 1][MODEL == 2 ? kMaxRow : 1];
     __shared__ Real s_red[NW][12];
-    __shared__ unsigned s_cnt[NW][4];
+    __shared__ unsigned s_cnt[NW][5];
 
     const int i = blockIdx.x;
     const size_t n = (size_t)k.npoints;
@@ -303,7 +439,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     if (nb > kMaxRow) nb = 0;
     const int li = s.lat[i];
     const int ix = lat_x(li), iy = lat_y(li), iz = lat_z(li);
-    const Real inv_dx = (Real)k.inv_dx;
+    const Real inv_dx = F64 ? (Real)k.inv_dx : (Real)k.inv_dxf;
 
     // stage the family of i: bond vectors and relative velocities
     double pxi = 0, pyi = 0, pzi = 0;
@@ -331,7 +467,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             z.y = (Real)(lat_y(lj) - iy) + (s.u[n + j] - uyi) * inv_dx;
             z.z = (Real)(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
         }
-        z.w = (Real)0;
+        z.w = z.x * z.x + z.y * z.y + z.z * z.z;
         y.x = s.vh[j] - vxi;
         y.y = s.vh[n + j] - vyi;
         y.z = s.vh[2 * n + j] - vzi;
@@ -346,7 +482,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     for (int c = 0; c < 6; c++) sig_i[c] = s.sig[c * n + i];
     const Real pc_i = s.pc[i];
     const ColumnConst cc = s.cols[s.colid[i]];
-    const Real Srs = (Real)cc.Srs;
+    const Real Srs = F64 ? (Real)cc.Srs : (Real)cc.Srsf;
     const Real hf2 = (Real)k.hf2f;
     const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
 
@@ -354,10 +490,13 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     Real red[12];
 #pragma unroll
     for (int e = 0; e < 12; e++) red[e] = (Real)0;
-    unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0;
+    unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
 
     for (int t = threadIdx.x; t < nb; t += kBondThreads) {
         const R4<Real> zj = s_z[t];
+        // mixed-path test |z_k - z_j|^2 - hf^2 = |z_k|^2 + (|z_j|^2 - hf^2) - 2 z_k.z_j
+        const Real mjx = (Real)-2 * zj.x, mjy = (Real)-2 * zj.y, mjz = (Real)-2 * zj.z;
+        const Real cj = zj.w - hf2;
         double pjx = 0, pjy = 0, pjz = 0;
         if constexpr (F64) { pjx = s_p[0][t]; pjy = s_p[F64 ? 1 : 0][t]; pjz = s_p[F64 ? 2 : 0][t]; }
         Real K00 = 0, K11 = 0, K22 = 0, K12 = 0, K02 = 0, K01 = 0;
@@ -365,43 +504,70 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         int cnt = 0;
         // sub-horizon of bond (i, j): k in H_i with |x_k - x_j| <= delta
         // (Alg. 1 line 4); the standard model takes all of H_i
+        if constexpr (F64 || MODEL == 1) {
 #pragma unroll 2
-        for (int q = 0; q < nb; q++) {
-            const R4<Real> zk = s_z[q];
-            bool member;
-            if constexpr (MODEL == 1) {
-                member = true;
-            } else if constexpr (F64) {
-                const double d0 = __dsub_rn(s_p[0][q], pjx);
-                const double d1 = __dsub_rn(s_p[F64 ? 1 : 0][q], pjy);
-                const double d2 = __dsub_rn(s_p[F64 ? 2 : 0][q], pjz);
-                member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
-                                   __dmul_rn(d2, d2)) <= k.delta2;
-            } else {
-                const Real d0 = zk.x - zj.x, d1 = zk.y - zj.y, d2 = zk.z - zj.z;
-                member = d0 * d0 + d1 * d1 + d2 * d2 <= hf2;
+            for (int q = 0; q < nb; q++) {
+                const R4<Real> zk = s_z[q];
+                bool member = true;
+                if constexpr (MODEL != 1) {
+                    const double d0 = __dsub_rn(s_p[0][q], pjx);
+                    const double d1 = __dsub_rn(s_p[F64 ? 1 : 0][q], pjy);
+                    const double d2 = __dsub_rn(s_p[F64 ? 2 : 0][q], pjz);
+                    member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
+                                       __dmul_rn(d2, d2)) <= k.delta2;
+                }
+                if (member) {
+                    const R4<Real> yk = s_y[q];
+                    K00 += zk.x * zk.x; K11 += zk.y * zk.y; K22 += zk.z * zk.z;
+                    K12 += zk.y * zk.z; K02 += zk.x * zk.z; K01 += zk.x * zk.y;
+                    A00 += yk.x * zk.x; A01 += yk.x * zk.y; A02 += yk.x * zk.z;
+                    A10 += yk.y * zk.x; A11 += yk.y * zk.y; A12 += yk.y * zk.z;
+                    A20 += yk.z * zk.x; A21 += yk.z * zk.y; A22 += yk.z * zk.z;
+                    cnt++;
+                }
             }
-            if (member) {
+        } else {
+            // FP32 sub-horizon sums without branches: the membership mask
+            // multiplies the bond vector, so every lane runs the same stream
+            Real cntf = (Real)0;
+#pragma unroll 4
+            for (int q = 0; q < nb; q++) {
+                const R4<Real> zk = s_z[q];
                 const R4<Real> yk = s_y[q];
-                K00 += zk.x * zk.x; K11 += zk.y * zk.y; K22 += zk.z * zk.z;
-                K12 += zk.y * zk.z; K02 += zk.x * zk.z; K01 += zk.x * zk.y;
-                A00 += yk.x * zk.x; A01 += yk.x * zk.y; A02 += yk.x * zk.z;
-                A10 += yk.y * zk.x; A11 += yk.y * zk.y; A12 += yk.y * zk.z;
-                A20 += yk.z * zk.x; A21 += yk.z * zk.y; A22 += yk.z * zk.z;
-                cnt++;
+                const Real tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + (zk.w + cj)));
+                const Real m = tst <= (Real)0 ? (Real)1 : (Real)0;
+                const Real zx = zk.x * m, zy = zk.y * m, zz = zk.z * m;
+                K00 += zx * zk.x; K11 += zy * zk.y; K22 += zz * zk.z;
+                K12 += zy * zk.z; K02 += zx * zk.z; K01 += zx * zk.y;
+                A00 += yk.x * zx; A01 += yk.x * zy; A02 += yk.x * zz;
+                A10 += yk.y * zx; A11 += yk.y * zy; A12 += yk.y * zz;
+                A20 += yk.z * zx; A21 += yk.z * zy; A22 += yk.z * zz;
+                cntf += m;
             }
+            cnt = (int)cntf;
         }
         n_pairs += cnt;
-        // FP64 shape-tensor inverse (Eq. 23, 25)
-        double Kd[6] = {(double)K00, (double)K11, (double)K22, (double)K12, (double)K02, (double)K01};
-        double Kid[6];
-        const bool active = cnt >= 3 && inverse_sym_fp64(Kd, Kid);
+        // shape-tensor inverse with FP64 cofactors and determinant (Eq. 23, 25)
+        Real Kid[6];
+        bool active = cnt >= 3;
+        if constexpr (F64) {
+            const double Kd[6] = {K00, K11, K22, K12, K02, K01};
+            active = active && inverse_sym_fp64(Kd, Kid);
+        } else {
+            active = active && inverse_sym_mixed(K00, K11, K22, K12, K02, K01, Kid);
+        }
         if (!active) {
             n_singular++;
             if constexpr (MODEL != 2) {
                 s.T[r0 + t] = (Real)0;
                 s.T[k.cap + r0 + t] = (Real)0;
                 s.T[2 * k.cap + r0 + t] = (Real)0;
+                const int rb = s.rev[r0 + t];
+                if (rb >= 0) {
+                    s.Trev[rb] = (Real)0;
+                    s.Trev[k.cap + rb] = (Real)0;
+                    s.Trev[2 * k.cap + rb] = (Real)0;
+                }
             } else {
 #pragma unroll
                 for (int e = 0; e < 9; e++) s_M[e][t] = (Real)0;
@@ -423,9 +589,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 for (int c = 0; c < 3; c++)
                     L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
                                     A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
-            material_update<Real>(L, sig_i, pc_i, k, cc.M, bs);
+            material_update<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, bs);
             n_plastic += bs.plastic;
             n_nonconv += bs.nonconv;
+            n_ret64 += bs.ret64;
         } else {
 #pragma unroll
             for (int c = 0; c < 6; c++) bs.sig[c] = sig_i[c];
@@ -451,6 +618,12 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;
+            const int rb = s.rev[r0 + t];
+            if (rb >= 0) {
+                s.Trev[rb] = T0;
+                s.Trev[k.cap + rb] = T1;
+                s.Trev[2 * k.cap + rb] = T2;
+            }
             red[9] += T0; red[10] += T1; red[11] += T2;
         } else {
 #pragma unroll
@@ -500,14 +673,20 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;
+            const int rb = s.rev[r0 + t];
+            if (rb >= 0) {
+                s.Trev[rb] = T0;
+                s.Trev[k.cap + rb] = T1;
+                s.Trev[2 * k.cap + rb] = T2;
+            }
             ts[0] += T0; ts[1] += T1; ts[2] += T2;
         }
         block_sum<3, Real>(ts, reinterpret_cast<Real(*)[3]>(&s_red[0][0]));
         red[9] = ts[0]; red[10] = ts[1]; red[11] = ts[2];
     }
 
-    unsigned cnts[4] = {n_plastic, n_nonconv, n_singular, n_pairs};
-    block_sum<4, unsigned>(cnts, s_cnt);
+    unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
+    block_sum<5, unsigned>(cnts, s_cnt);
     if (threadIdx.x == 0) {
         if (update && w > (Real)0) {
             const Real iw = (Real)1 / w;
@@ -521,6 +700,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         s.tsum[2 * n + i] = red[11];
         if (with_dt && cnts[3]) atomicAdd(&s.ctr->pairs, (unsigned long long)cnts[3]);
         if (cnts[0]) atomicAdd(&s.ctr->plastic, (unsigned long long)cnts[0]);
+        if (cnts[4]) atomicAdd(&s.ctr->ret64, (unsigned long long)cnts[4]);
         if (cnts[1]) {
             atomicAdd(&s.ctr->nonconv, (unsigned long long)cnts[1]);
             atomicOr(&s.ctr->status, PPM_STATUS_NONCONV);
@@ -545,99 +725,101 @@ template <typename Real>
 __global__ void __launch_bounds__(kWarpPointsPerBlock * 32)
 k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     constexpr bool F64 = sizeof(Real) == 8;
-    __shared__ double s_e[kWarpPointsPerBlock][3];
+    constexpr int kIt = kMaxRow / 32;
+    __shared__ Real s_e[kWarpPointsPerBlock][3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int i = blockIdx.x * kWarpPointsPerBlock + wib;       // one warp per point
     const size_t n = (size_t)k.npoints;
-    const double m = k.rho * k.dx * k.dx * k.dx;
-    const double dx2 = k.dx * k.dx;
-    const double inv_rho_dx = 1.0 / (k.rho * k.dx);
-    double e_int = 0.0, e_ext = 0.0, e_kin = 0.0;
-    for (int i = warp; i < k.npoints; i += nwarps) {
+    const Real m = F64 ? (Real)(k.rho * k.dx * k.dx * k.dx) : (Real)k.massf;
+    const Real dx2 = F64 ? (Real)(k.dx * k.dx) : (Real)k.dx2f;
+    const Real inv_rho_dx = F64 ? (Real)(1.0 / (k.rho * k.dx)) : (Real)k.inv_rho_dxf;
+    const Real dtr = F64 ? (Real)dt : (Real)(float)dt;
+    const Real hdt = (Real)0.5 * dtr;
+    Real dwi = 0, dwe = 0, wk = 0;
+    if (i < k.npoints) {
         const int r0 = s.row_ptr[i], r1 = s.row_ptr[i + 1];
-        Real sum[3] = {(Real)0, (Real)0, (Real)0};
-        Real cmp[3] = {(Real)0, (Real)0, (Real)0};
-        for (int b = r0 + lane; b < r1; b += 32) {
-            const int rb = s.rev[b];
-            if (rb < 0) continue;
+        // lanes 0..2 fetch the per-point data of component c = lane early
+        const int c = lane < 3 ? lane : 0;
+        const size_t t = (size_t)c * n + i;
+        const Real ts = s.tsum[t], fo = s.fint[t], vh = s.vh[t], v0 = s.v[t];
+        const bool base = lat_z(s.lat[i]) == 0;
+        // every load of the row T_(ji) (stored contiguously in Trev) first
+        Real x[3][kIt];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const Real x = s.T[(size_t)c * k.cap + rb];
+        for (int it = 0; it < kIt; it++) {
+            const int b = r0 + lane + 32 * it;
+#pragma unroll
+            for (int q = 0; q < 3; q++) x[q][it] = b < r1 ? s.Trev[(size_t)q * k.cap + b] : (Real)0;
+        }
+        Real sum[3], cmp[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            sum[q] = (Real)0;
+            cmp[q] = (Real)0;
+#pragma unroll
+            for (int it = 0; it < kIt; it++) {
                 if constexpr (F64) {
-                    sum[c] += x;
+                    sum[q] += x[q][it];
                 } else {
-                    // Kahan-compensated running sum
-                    const float y = (float)x - (float)cmp[c];
-                    const float t = (float)sum[c] + y;
-                    cmp[c] = (Real)((t - (float)sum[c]) - y);
-                    sum[c] = (Real)t;
+                    float ss, ee;          // compensated running sum
+                    two_sum(sum[q], x[q][it], ss, ee);
+                    sum[q] = ss;
+                    cmp[q] += ee;
                 }
             }
         }
-        if (!F64)
-#pragma unroll
-            for (int c = 0; c < 3; c++) cmp[c] = -cmp[c];   // carried low part
-        // fixed-order tree over lanes; compensated in FP32
+        // fixed-order butterfly over lanes (every lane ends with the total)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const Real so = __shfl_down_sync(0xffffffffu, sum[c], off);
-                const Real co = __shfl_down_sync(0xffffffffu, cmp[c], off);
+            for (int q = 0; q < 3; q++) {
+                const Real so = __shfl_xor_sync(0xffffffffu, sum[q], off);
+                const Real co = __shfl_xor_sync(0xffffffffu, cmp[q], off);
                 if constexpr (F64) {
-                    sum[c] += so;
+                    sum[q] += so;
                 } else {
                     float ss, ee;
-                    two_sum((float)sum[c], (float)so, ss, ee);
-                    sum[c] = (Real)ss;
-                    cmp[c] = (Real)((float)cmp[c] + (float)co + ee);
+                    two_sum(sum[q], so, ss, ee);
+                    sum[q] = ss;
+                    cmp[q] = cmp[q] + co + ee;
                 }
             }
         }
-        if (lane == 0) {
-            const int li = s.lat[i];
-            const bool base = lat_z(li) == 0;
-            double dwi = 0.0, dwe = 0.0, wk = 0.0;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const size_t t = (size_t)c * n + i;
-                const double gathered = F64 ? (double)sum[c] : (double)sum[c] + (double)cmp[c];
-                const double fhat = (double)s.tsum[t] - gathered;
-                const double f = fhat * dx2;                        // Eq. 49-50
-                double a = fhat * inv_rho_dx + k.g[c];               // Eq. 62
-                if (base || (k.lock_lateral && c < 2)) a = 0.0;
-                if (!isfinite(a)) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
-                const double f_old = (double)s.fint[t];
-                s.fint[t] = (Real)f;
-                s.a[t] = (Real)a;
-                if (initial) {
-                    const double v = (double)s.v[t];
-                    wk += 0.5 * m * v * v;
-                } else {
-                    const double vh = (double)s.vh[t];
-                    const double v = (double)(s.vh[t] + (Real)(0.5 * dt) * (Real)a);  // Eq. 63
-                    s.v[t] = (Real)v;
-                    dwi += -0.5 * dt * vh * (f_old + f);              // Eq. 66
-                    dwe += dt * m * vh * k.g[c];                      // Eq. 67
-                    wk += 0.5 * m * v * v;                            // Eq. 68
-                }
+        if (lane < 3) {
+            const Real g = F64 ? (Real)k.g[c] : (Real)k.gf[c];
+            const Real gathered = c == 0 ? sum[0] + cmp[0] : (c == 1 ? sum[1] + cmp[1] : sum[2] + cmp[2]);
+            const Real fhat = ts - gathered;
+            const Real f = fhat * dx2;                               // Eq. 49-50
+            Real a = fhat * inv_rho_dx + g;                          // Eq. 62
+            if (base || (k.lock_lateral && c < 2)) a = (Real)0;
+            if (!isfinite(a)) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
+            s.fint[t] = f;
+            s.a[t] = a;
+            if (initial) {
+                wk = (Real)0.5 * m * v0 * v0;
+            } else {
+                const Real v = vh + hdt * a;                         // Eq. 63
+                s.v[t] = v;
+                dwi = -hdt * vh * (fo + f);                          // Eq. 66
+                dwe = dtr * m * vh * g;                              // Eq. 67
+                wk = (Real)0.5 * m * v * v;                          // Eq. 68
             }
-            e_int += dwi;
-            e_ext += dwe;
-            e_kin += wk;
         }
     }
+    // energies of the point: lanes 0..2 hold the three components
+    dwi += __shfl_down_sync(0xffffffffu, dwi, 1) + __shfl_down_sync(0xffffffffu, dwi, 2);
+    dwe += __shfl_down_sync(0xffffffffu, dwe, 1) + __shfl_down_sync(0xffffffffu, dwe, 2);
+    wk += __shfl_down_sync(0xffffffffu, wk, 1) + __shfl_down_sync(0xffffffffu, wk, 2);
     if (lane == 0) {
-        s_e[wib][0] = e_int;
-        s_e[wib][1] = e_ext;
-        s_e[wib][2] = e_kin;
+        s_e[wib][0] = dwi;
+        s_e[wib][1] = dwe;
+        s_e[wib][2] = wk;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int q = 0; q < kWarpPointsPerBlock; q++) t += s_e[q][threadIdx.x];
-        s.epart[(size_t)blockIdx.x * 3 + threadIdx.x] = t;
+        double tot = 0.0;
+        for (int q = 0; q < kWarpPointsPerBlock; q++) tot += (double)s_e[q][threadIdx.x];
+        s.epart[(size_t)blockIdx.x * 3 + threadIdx.x] = tot;
     }
 }
 

@@ -284,7 +284,14 @@ __global__ void k_family_rev(DevState<Real> s, StepConst k) {
                 if (s.col[mid] < i) lo = mid + 1;
                 else hi = mid;
             }
-            s.rev[b] = (lo < end && s.col[lo] == i) ? lo : -1;
+            const int rb = (lo < end && s.col[lo] == i) ? lo : -1;
+            s.rev[b] = rb;
+            // a bond without a reverse partner receives no force state
+            if (rb < 0) {
+                s.Trev[b] = (Real)0;
+                s.Trev[k.cap + b] = (Real)0;
+                s.Trev[2 * k.cap + b] = (Real)0;
+            }
         }
     }
 }

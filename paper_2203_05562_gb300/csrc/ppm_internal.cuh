@@ -23,13 +23,14 @@ __host__ __device__ __forceinline__ int lat_z(int l) { return l >> (2 * kLatBits
 struct ColumnConst {
     double M;       // critical-state slope
     double Srs;     // S_r * suction: total stress = effective + Srs * 1
+    float Mf, Srsf; // the same in FP32
     int32_t nx, ny, nz, pad;
     int64_t offset; // first point id of the column
 };
 
 // device-resident counters and status word
 struct DevCounters {
-    unsigned long long plastic, nonconv, singular, rebuilds, bond_steps, pairs;
+    unsigned long long plastic, nonconv, singular, rebuilds, bond_steps, pairs, ret64;
     unsigned int status, pad;
     int family_ok, pad2;
     double W_int, W_ext, W_kin, W_kin0;
@@ -52,6 +53,9 @@ struct StepConst {
     int visc_form, max_iter, model, lock_lateral;
     int npoints, ncols, max_family, pad;
     long long cap;               // bond capacity
+    // FP32 copies used by the mixed path (no FP64 conversions in its loops)
+    float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;
+    float gf[3];
 };
 
 // device pointers of one context (Real = double for FP64, float for mixed)
@@ -73,7 +77,8 @@ struct DevState {
     int32_t* row_ptr;    // N+1
     int32_t* col;        // cap
     int32_t* rev;        // cap
-    Real* T;             // 3 x cap scaled force state
+    Real* T;             // 3 x cap scaled force state, bond order
+    Real* Trev;          // 3 x cap: Trev[rev[b]] = T[b], so row j holds T_(ij)
     double* epart;       // energy partials, 3 x gather blocks
     DevCounters* ctr;
     // family scratch

@@ -91,6 +91,8 @@ int collect_columns(const ppm_params* p, int n_columns, const ppm_column* cols,
         ColumnConst cc;
         cc.M = M;
         cc.Srs = saturation(s, p->vg_alpha, p->vg_n) * s;
+        cc.Mf = (float)cc.M;
+        cc.Srsf = (float)cc.Srs;
         cc.nx = nx; cc.ny = ny; cc.nz = nz; cc.pad = 0;
         cc.offset = off;
         out.push_back(cc);
@@ -124,6 +126,7 @@ void carve(Layout& L, char* base, int64_t N, long long cap, int ncell_cap, int g
     s.col = L.take<int32_t>(base, (size_t)cap);
     s.rev = L.take<int32_t>(base, (size_t)cap);
     s.T = L.take<Real>(base, 3 * (size_t)cap);
+    s.Trev = L.take<Real>(base, 3 * (size_t)cap);
     s.epart = L.take<double>(base, 3 * (size_t)gather_blocks);
     s.ctr = L.take<DevCounters>(base, 1);
     s.grid = L.take<CellGrid>(base, 1);
@@ -151,8 +154,8 @@ Sizes sizes_for(const ppm_params* p, int64_t N) {
     z.cap = (long long)N * z.max_family;
     if (z.cap > 0x7fffffffLL) z.cap = 0x7fffffffLL;
     z.ncell_cap = (int)((2 * N > 4096) ? 2 * N : 4096);
-    long long gb = (N + kWarpPointsPerBlock - 1) / kWarpPointsPerBlock;
-    z.gather_blocks = (int)(gb < 4096 ? gb : 4096);
+    // the gather runs one warp per point
+    z.gather_blocks = (int)((N + kWarpPointsPerBlock - 1) / kWarpPointsPerBlock);
     return z;
 }
 
@@ -394,6 +397,18 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.ncols = c->ncols;
     k.max_family = z.max_family;
     k.cap = c->cap;
+    k.dxf = (float)k.dx;
+    k.inv_dxf = (float)k.inv_dx;
+    k.dtf = (float)k.dt;
+    k.hdtf = (float)(0.5 * k.dt);
+    k.Kf = (float)k.K;
+    k.muf = (float)k.mu;
+    k.rhof = (float)k.rho;
+    k.inv_rho_dxf = (float)(1.0 / (k.rho * k.dx));
+    k.dx2f = (float)(k.dx * k.dx);
+    k.massf = (float)(k.rho * k.dx * k.dx * k.dx);
+    k.etaf = (float)k.eta;
+    for (int d = 0; d < 3; d++) k.gf[d] = (float)k.g[d];
 
     // lattice indices and column ids (host-built, copied once)
     std::vector<int32_t> lat((size_t)c->N), colid((size_t)c->N);
@@ -521,6 +536,7 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     out->singular = (int64_t)h.singular;
     out->rebuilds = (int64_t)h.rebuilds;
     out->pairs = (int64_t)h.pairs;
+    out->returns_fp64 = (int64_t)h.ret64;
     out->launches = c->launches;
     out->status = h.status;
     out->W_int = h.W_int;

@@ -51,6 +51,7 @@ class Counters(C.Structure):
     _fields_ = [("steps", C.c_int64), ("nbonds", C.c_int64), ("bond_steps", C.c_int64),
                 ("plastic", C.c_int64), ("nonconv", C.c_int64), ("singular", C.c_int64),
                 ("rebuilds", C.c_int64), ("pairs", C.c_int64), ("launches", C.c_int64),
+                ("returns_fp64", C.c_int64),
                 ("status", C.c_uint32), ("pad_", C.c_uint32),
                 ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double),
                 ("W_kin0", C.c_double)]

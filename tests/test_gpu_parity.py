@@ -162,3 +162,26 @@ def test_degenerate_columns(dims):
     err = state_errors(sim, run)
     assert max(err.values()) <= FP64_TOL, err
     assert sim.status()["singular"] == run.counters()["singular"]
+
+
+def test_mixed_plastic_column_fp32_returns_within_1e3():
+    # every bond yields from the first step; most returns are solved in FP32
+    cfg = pi.small_config(8, 8, 10, suction=50e3, rebuild_every=5)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=12)
+    run = oracle_run(cfg, 20, v0)
+    sim = gpu_run(cfg, 20, "mixed", v0=v0)
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["u"] <= MIXED_TOL and err["sigma"] <= MIXED_TOL and err["pc"] <= MIXED_TOL, err
+    st = sim.status()
+    assert st["plastic"] > 0 and st["returns_fp64"] < st["plastic"]
+
+
+def test_mixed_near_apex_returns_use_fp64():
+    # zero initial stress and no suction: every state sits at the apex
+    cfg = pi.small_config(6, 6, 8, suction=0.0, init_stress=1, rebuild_every=0)
+    v0 = pi.initial_velocity(cfg, std=1e-2, seed=21)
+    run = oracle_run(cfg, 10, v0)
+    sim = gpu_run(cfg, 10, "mixed", v0=v0)
+    st = sim.status()
+    assert st["returns_fp64"] > 0
+    assert rel_l2(sim.read("u"), run.u) <= MIXED_TOL
