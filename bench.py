@@ -149,7 +149,7 @@ def time_path(cfg, precision, steps, warmup, stream_sync):
     """Device-timed steps of one precision; returns a dict of figures."""
     import torch
     from paper_2203_05562_gb300 import Simulation
-    sim = Simulation(cfg, precision=precision)
+    sim = Simulation(cfg, precision=precision, bond_tile=0)
     sim.write("v", pi.initial_velocity(cfg))
     sim.step(warmup)
     torch.cuda.synchronize()
@@ -176,6 +176,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--tile", type=int, default=128, help="bond-kernel tile for --profile-only")
+    ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + steps of the mixed path only (for ncu captures)")
     args = ap.parse_args()
@@ -200,7 +203,7 @@ def main():
     sampler = ClockSampler(local)
     if args.profile_only:
         from paper_2203_05562_gb300 import Simulation
-        sim = Simulation(cfg, precision="mixed", use_graph=False)
+        sim = Simulation(cfg, precision="mixed", use_graph=False, bond_tile=args.tile)
         sim.write("v", pi.initial_velocity(cfg))
         sim.step(args.warmup + args.steps)
         torch.cuda.synchronize()
@@ -224,15 +227,24 @@ def main():
         total_bond_steps = float(fig["bond_steps"])
     value = total_bond_steps / (ms * 1e-3)
 
-    # ---- dominant kernel: per-phase CUDA-event times on the launching stream ----
-    phase = sim.step_timed(max(5, min(20, args.steps)))
-    nph = max(5, min(20, args.steps))
+    # ---- dominant kernel: per-phase CUDA-event times on the launching stream,
+    # over the same warm-up and steps as the headline, on a fresh column ----
     st = sim.status()
+    del sim
+    from paper_2203_05562_gb300 import Simulation
+    tsim = Simulation(cfg, precision="mixed", bond_tile=fig["status"]["bond_tile"])
+    tsim.write("v", pi.initial_velocity(cfg))
+    tsim.step(args.warmup)
+    t0 = tsim.status()
+    phase = tsim.step_timed(args.steps)
+    t1 = tsim.status()
+    nph = args.steps
     bond_ms = phase[1] / nph
-    pairs_per_step = fig["pairs"] / args.steps
+    pairs_per_step = (t1["pairs"] - t0["pairs"]) / nph
     nb = fig["nbonds"]
-    rp = sim.read("row_ptr")
+    rp = tsim.read("row_ptr")
     fam_sq = float(np.sum(np.diff(rp).astype(np.float64) ** 2))
+    del tsim
     flops = FLOPS_TEST * fam_sq + FLOPS_PAIR * pairs_per_step
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -244,6 +256,31 @@ def main():
                 "peak_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
                 "bond_kernel_ms": bond_ms, "gather_ms": phase[2] / nph,
                 "predictor_family_ms": phase[0] / nph}
+
+    # ---- batched ensemble: 64 columns in one context, whole rebuild periods as graphs ----
+    ens = None
+    if not args.no_ensemble:
+        ecfg = pi.config("ensemble_64_columns_mixed")
+        cols = pi.ensemble_columns(64, seed=ecfg["seed"])
+        esim0 = Simulation(ecfg, columns=cols, precision="mixed", bond_tile=0)
+        ne = esim0.n
+        esim0.write("v", np.random.default_rng(ecfg["seed"]).normal(0, 1e-6, size=(3, ne)))
+        esim0.step(args.warmup)
+        torch.cuda.synchronize()
+        e0 = esim0.status()
+        eva, evb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eva.record(esim0.stream)
+        esim0.step(args.ensemble_steps)
+        evb.record(esim0.stream)
+        torch.cuda.synchronize()
+        e1 = esim0.status()
+        ems = eva.elapsed_time(evb)
+        ens = {"workload": "ensemble_64_columns_mixed", "columns": 64, "points": ne,
+               "bonds": e1["nbonds"], "steps": args.ensemble_steps,
+               "value": (e1["bond_steps"] - e0["bond_steps"]) / (ems * 1e-3), "unit": UNIT,
+               "ms_per_step": ems / args.ensemble_steps, "bond_tile": e1["bond_tile"],
+               "graph": "one CUDA graph per 50-step rebuild period"}
+        del esim0
 
     # ---- FP64 path on the same column (fewer steps: FP64 is ~1/64 rate) ----
     sim64, fig64 = time_path(cfg, "fp64", args.fp64_steps, 1, barrier)
@@ -292,7 +329,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "clocks": clocks, "gpu_launches": fig["launches"],
             "status": {k: st[k] for k in ("plastic", "nonconv", "singular", "flags")},
         }

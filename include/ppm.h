@@ -99,7 +99,13 @@ typedef struct {
     int32_t lock_lateral;        /* 1: x and y motion suppressed               */
     int32_t precision;           /* PPM_FP64 or PPM_MIXED                       */
     int32_t max_family;          /* bond capacity per point (0: 192; max 256)  */
-    int32_t use_graph;           /* 1: replay steps through CUDA graphs         */
+    int32_t use_graph;           /* 1: replay steps through CUDA graphs; a whole
+                                    rebuild period (R <= 64) is one graph      */
+    int32_t bond_tile;           /* bond-kernel threads per point: 64, 128, 256,
+                                    or 0 to time all three on the first pass
+                                    and keep the fastest (results are bitwise
+                                    reproducible for a fixed tile)             */
+    int32_t pad_;
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */
@@ -122,6 +128,8 @@ typedef struct {
     int64_t returns_fp64;        /* plastic returns solved in FP64 (all of them
                                     in PPM_FP64; in PPM_MIXED those near the
                                     apex or whose FP32 solve failed)           */
+    int32_t bond_tile;           /* tile in use                                 */
+    int32_t pad2_;
     uint32_t status;             /* PPM_STATUS_* bits                           */
     uint32_t pad_;
     double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */

@@ -396,6 +396,59 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
     o.pc = pc_new;
 }
 
+// Predicated sub-horizon accumulation: when tst <= 0 (member), add the
+// outer products zeta~ zeta~^T (6), Ydot zeta~^T (9) and 1 to the count; the
+// predicate guards each FMA, so non-members cost no extra multiplies and the
+// warp never branches.
+__device__ __forceinline__ void masked_accumulate(float tst, float zx, float zy, float zz,
+                                                  float yx, float yy, float yz, float (&K)[6],
+                                                  float (&A)[9], float& cnt) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.f32 p, %16, 0f00000000;\n\t"
+        "@p fma.rn.f32 %0, %17, %17, %0;\n\t"
+        "@p fma.rn.f32 %1, %18, %18, %1;\n\t"
+        "@p fma.rn.f32 %2, %19, %19, %2;\n\t"
+        "@p fma.rn.f32 %3, %18, %19, %3;\n\t"
+        "@p fma.rn.f32 %4, %17, %19, %4;\n\t"
+        "@p fma.rn.f32 %5, %17, %18, %5;\n\t"
+        "@p fma.rn.f32 %6, %20, %17, %6;\n\t"
+        "@p fma.rn.f32 %7, %20, %18, %7;\n\t"
+        "@p fma.rn.f32 %8, %20, %19, %8;\n\t"
+        "@p fma.rn.f32 %9, %21, %17, %9;\n\t"
+        "@p fma.rn.f32 %10, %21, %18, %10;\n\t"
+        "@p fma.rn.f32 %11, %21, %19, %11;\n\t"
+        "@p fma.rn.f32 %12, %22, %17, %12;\n\t"
+        "@p fma.rn.f32 %13, %22, %18, %13;\n\t"
+        "@p fma.rn.f32 %14, %22, %19, %14;\n\t"
+        "@p add.f32 %15, %15, 0f3F800000;\n\t"
+        "}"
+        : "+f"(K[0]), "+f"(K[1]), "+f"(K[2]), "+f"(K[3]), "+f"(K[4]), "+f"(K[5]),
+          "+f"(A[0]), "+f"(A[1]), "+f"(A[2]), "+f"(A[3]), "+f"(A[4]), "+f"(A[5]),
+          "+f"(A[6]), "+f"(A[7]), "+f"(A[8]), "+f"(cnt)
+        : "f"(tst), "f"(zx), "f"(zy), "f"(zz), "f"(yx), "f"(yy), "f"(yz));
+}
+
+// Predicated sum of a sender's 3x3 matrix (M) into N when tst <= 0.
+__device__ __forceinline__ void masked_add9(float tst, const float4& m0, const float4& m1,
+                                            float m8, float (&N)[9]) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.f32 p, %9, 0f00000000;\n\t"
+        "@p add.f32 %0, %0, %10;\n\t"
+        "@p add.f32 %1, %1, %11;\n\t"
+        "@p add.f32 %2, %2, %12;\n\t"
+        "@p add.f32 %3, %3, %13;\n\t"
+        "@p add.f32 %4, %4, %14;\n\t"
+        "@p add.f32 %5, %5, %15;\n\t"
+        "@p add.f32 %6, %6, %16;\n\t"
+        "@p add.f32 %7, %7, %17;\n\t"
+        "@p add.f32 %8, %8, %18;\n\t"
+        "}"
+        : "+f"(N[0]), "+f"(N[1]), "+f"(N[2]), "+f"(N[3]), "+f"(N[4]), "+f"(N[5]), "+f"(N[6]),
+          "+f"(N[7]), "+f"(N[8])
+        : "f"(tst), "f"(m0.x), "f"(m0.y), "f"(m0.z), "f"(m0.w), "f"(m1.x), "f"(m1.y), "f"(m1.z),
+          "f"(m1.w), "f"(m8));
+}
+
 // deterministic block sum: butterfly within warps, then warps in order
 template <int NV, typename T>
 __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sm)[NV]) {
@@ -420,15 +473,19 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sm)[NV]) {
 // ---------------------------------------------------------------------------
 // fused bond kernel: one CTA per point, one thread per bond
 // ---------------------------------------------------------------------------
-template <typename Real, int MODEL>
-__global__ void __launch_bounds__(kBondThreads, sizeof(Real) == 4 ? 4 : 2)
+// TPP threads per point (a tile the autotuner picks among 64, 128, 256); the
+// register budget targets 640 resident threads per SM for FP32
+template <typename Real, int MODEL, int TPP>
+__global__ void __launch_bounds__(TPP, sizeof(Real) == 4 ? (640 / TPP) : (256 / TPP > 0 ? 256 / TPP : 1))
 k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     constexpr bool F64 = sizeof(Real) == 8;
-    constexpr int NW = kBondThreads / 32;
+    constexpr int NW = TPP / 32;
     __shared__ R4<Real> s_z[kMaxRow];                         // zeta~_k, lattice units
     __shared__ R4<Real> s_y[kMaxRow];                         // Ydot_k, m/s
     __shared__ double s_p[F64 ? 3 : 1][F64 ? kMaxRow : 1];    // FP64: absolute x_k
-    __shared__ Real s_M[MODEL == 2 ? 9 : 1][MODEL == 2 ? kMaxRow : 1];
+    // model 2: per sender bond, its matrix M = varpi sigma K^-1 (9), and (FP32) the
+    // terms of its membership test, -2 zeta~ (3) and |zeta~|^2 - hf^2 (1)
+    __shared__ alignas(16) Real s_M[MODEL == 2 ? kMaxRow : 1][F64 ? 9 : 16];
     __shared__ Real s_red[NW][12];
     __shared__ unsigned s_cnt[NW][5];
 
@@ -450,7 +507,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     }
     const Real uxi = s.u[i], uyi = s.u[n + i], uzi = s.u[2 * n + i];
     const Real vxi = s.vh[i], vyi = s.vh[n + i], vzi = s.vh[2 * n + i];
-    for (int t = threadIdx.x; t < nb; t += kBondThreads) {
+    for (int t = threadIdx.x; t < nb; t += TPP) {
         const int j = s.col[r0 + t];
         const int lj = s.lat[j];
         R4<Real> z, y;
@@ -492,7 +549,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     for (int e = 0; e < 12; e++) red[e] = (Real)0;
     unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
 
-    for (int t = threadIdx.x; t < nb; t += kBondThreads) {
+    for (int t = threadIdx.x; t < nb; t += TPP) {
         const R4<Real> zj = s_z[t];
         // mixed-path test |z_k - z_j|^2 - hf^2 = |z_k|^2 + (|z_j|^2 - hf^2) - 2 z_k.z_j
         const Real mjx = (Real)-2 * zj.x, mjy = (Real)-2 * zj.y, mjz = (Real)-2 * zj.z;
@@ -527,23 +584,19 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 }
             }
         } else {
-            // FP32 sub-horizon sums without branches: the membership mask
-            // multiplies the bond vector, so every lane runs the same stream
-            Real cntf = (Real)0;
+            // FP32 sub-horizon sums, predicated (no branches, no mask multiplies)
+            float Kf[6] = {0, 0, 0, 0, 0, 0}, Af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            float cntf = 0.0f;
 #pragma unroll 4
             for (int q = 0; q < nb; q++) {
                 const R4<Real> zk = s_z[q];
                 const R4<Real> yk = s_y[q];
-                const Real tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + (zk.w + cj)));
-                const Real m = tst <= (Real)0 ? (Real)1 : (Real)0;
-                const Real zx = zk.x * m, zy = zk.y * m, zz = zk.z * m;
-                K00 += zx * zk.x; K11 += zy * zk.y; K22 += zz * zk.z;
-                K12 += zy * zk.z; K02 += zx * zk.z; K01 += zx * zk.y;
-                A00 += yk.x * zx; A01 += yk.x * zy; A02 += yk.x * zz;
-                A10 += yk.y * zx; A11 += yk.y * zy; A12 += yk.y * zz;
-                A20 += yk.z * zx; A21 += yk.z * zy; A22 += yk.z * zz;
-                cntf += m;
+                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + (zk.w + cj)));
+                masked_accumulate(tst, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
             }
+            K00 = Kf[0]; K11 = Kf[1]; K22 = Kf[2]; K12 = Kf[3]; K02 = Kf[4]; K01 = Kf[5];
+            A00 = Af[0]; A01 = Af[1]; A02 = Af[2]; A10 = Af[3]; A11 = Af[4]; A12 = Af[5];
+            A20 = Af[6]; A21 = Af[7]; A22 = Af[8];
             cnt = (int)cntf;
         }
         n_pairs += cnt;
@@ -570,7 +623,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 9; e++) s_M[e][t] = (Real)0;
+                for (int e = 0; e < 9; e++) s_M[t][e] = (Real)0;
+                if constexpr (!F64) {
+                    s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = cj;
+                }
             }
             continue;
         }
@@ -627,7 +683,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             red[9] += T0; red[10] += T1; red[11] += T2;
         } else {
 #pragma unroll
-            for (int e = 0; e < 9; e++) s_M[e][t] = SK[e];
+            for (int e = 0; e < 9; e++) s_M[t][e] = SK[e];
+            if constexpr (!F64) {
+                s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = cj;
+            }
         }
         red[0] += varpi;
 #pragma unroll
@@ -643,29 +702,39 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         // members; the row is normalised by sum(varpi)
         Real ts[3] = {(Real)0, (Real)0, (Real)0};
         const Real inv_w = w > (Real)0 ? (Real)1 / w : (Real)0;
-        for (int t = threadIdx.x; t < nb; t += kBondThreads) {
+        for (int t = threadIdx.x; t < nb; t += TPP) {
             const R4<Real> zt = s_z[t];
             double ptx = 0, pty = 0, ptz = 0;
             if constexpr (F64) { ptx = s_p[0][t]; pty = s_p[F64 ? 1 : 0][t]; ptz = s_p[F64 ? 2 : 0][t]; }
             Real N[9];
 #pragma unroll
             for (int e = 0; e < 9; e++) N[e] = (Real)0;
-            for (int q = 0; q < nb; q++) {
-                bool member;
-                if constexpr (F64) {
-                    const double d0 = __dsub_rn(ptx, s_p[0][q]);
-                    const double d1 = __dsub_rn(pty, s_p[F64 ? 1 : 0][q]);
-                    const double d2 = __dsub_rn(ptz, s_p[F64 ? 2 : 0][q]);
-                    member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
-                                       __dmul_rn(d2, d2)) <= k.delta2;
-                } else {
-                    const R4<Real> zq = s_z[q];
-                    const Real d0 = zt.x - zq.x, d1 = zt.y - zq.y, d2 = zt.z - zq.z;
-                    member = d0 * d0 + d1 * d1 + d2 * d2 <= hf2;
-                }
-                if (member)
+            if constexpr (F64) {
+                for (int q = 0; q < nb; q++) {
+                    const double d0 = __dsub_rn(s_p[0][q], ptx);
+                    const double d1 = __dsub_rn(s_p[F64 ? 1 : 0][q], pty);
+                    const double d2 = __dsub_rn(s_p[F64 ? 2 : 0][q], ptz);
+                    const bool member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
+                                                  __dmul_rn(d2, d2)) <= k.delta2;
+                    if (member)
 #pragma unroll
-                    for (int e = 0; e < 9; e++) N[e] += s_M[e][q];
+                        for (int e = 0; e < 9; e++) N[e] += s_M[q][e];
+                }
+            } else {
+                // receiver t is a member of sender q's sub-horizon: the same
+                // expression (and rounding) as the sender's own test
+                float Nf[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 2
+                for (int q = 0; q < nb; q++) {
+                    const float4 m0 = *reinterpret_cast<const float4*>(&s_M[q][0]);
+                    const float4 m1 = *reinterpret_cast<const float4*>(&s_M[q][4]);
+                    const float4 m2 = *reinterpret_cast<const float4*>(&s_M[q][8]);
+                    const float4 m3 = *reinterpret_cast<const float4*>(&s_M[q][12]);
+                    const float tst = zt.x * m2.y + (zt.y * m2.z + (zt.z * m2.w + (zt.w + m3.x)));
+                    masked_add9(tst, m0, m1, m2.x, Nf);
+                }
+#pragma unroll
+                for (int e = 0; e < 9; e++) N[e] = Nf[e];
             }
             const Real T0 = (N[0] * zt.x + N[1] * zt.y + N[2] * zt.z) * inv_w;
             const Real T1 = (N[3] * zt.x + N[4] * zt.y + N[5] * zt.z) * inv_w;
@@ -931,11 +1000,19 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
                         cudaStream_t st) {
     if (k.npoints <= 0) return cudaSuccess;
     const int with_dt = dt != 0.0;
+    const int tpp = (k.tile == 64 || k.tile == 256) ? k.tile : 128;
+#define PPM_BOND(M, T) k_bond<Real, M, T><<<k.npoints, T, 0, st>>>(s, k, with_dt, update)
+#define PPM_BOND_TILES(M)                           \
+    if (tpp == 64) PPM_BOND(M, 64);                 \
+    else if (tpp == 256) PPM_BOND(M, 256);          \
+    else PPM_BOND(M, 128);
     switch (k.model) {
-        case 0: k_bond<Real, 0><<<k.npoints, kBondThreads, 0, st>>>(s, k, with_dt, update); break;
-        case 1: k_bond<Real, 1><<<k.npoints, kBondThreads, 0, st>>>(s, k, with_dt, update); break;
-        default: k_bond<Real, 2><<<k.npoints, kBondThreads, 0, st>>>(s, k, with_dt, update); break;
+        case 0: PPM_BOND_TILES(0); break;
+        case 1: PPM_BOND_TILES(1); break;
+        default: PPM_BOND_TILES(2); break;
     }
+#undef PPM_BOND_TILES
+#undef PPM_BOND
     return cudaGetLastError();
 }
 

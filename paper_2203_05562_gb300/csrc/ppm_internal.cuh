@@ -10,7 +10,6 @@ namespace ppm {
 
 constexpr int kMaxRow = 256;          // hard cap of bonds per point (smem staging)
 constexpr int kDefaultMaxFamily = 192;
-constexpr int kBondThreads = 128;     // threads per point in the fused bond kernel
 constexpr int kWarpPointsPerBlock = 8;  // family / gather kernels: one warp per point
 constexpr int kLatBits = 10;          // packed lattice index: ix | iy << 10 | iz << 20
 constexpr int kLatMask = (1 << kLatBits) - 1;
@@ -51,7 +50,7 @@ struct StepConst {
     double dt, rho, K, mu, lk, eta, tol;
     double g[3];
     int visc_form, max_iter, model, lock_lateral;
-    int npoints, ncols, max_family, pad;
+    int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;

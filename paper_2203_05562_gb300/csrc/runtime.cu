@@ -31,11 +31,12 @@ struct ppm_ctx {
     bool started;
     bool family_built;
     int64_t step;
-    cudaGraphExec_t g_plain, g_rebuild;
+    cudaGraphExec_t g_plain, g_rebuild, g_segment;   // one step; one rebuild period
     cudaEvent_t ev[8];
     bool events_ok;
     long long launches;          // kernels issued (graph replays count their kernels)
-    long long launches_plain, launches_rebuild;   // kernels per captured step graph
+    long long launches_plain, launches_rebuild, launches_segment;   // kernels per graph
+    int segment_len;             // steps in g_segment (the rebuild period)
 };
 
 namespace {
@@ -68,6 +69,8 @@ int check_params(const ppm_params* p) {
     if (p->precision != PPM_FP64 && p->precision != PPM_MIXED) return PPM_EINVAL;
     if (p->newton_max_iter < 1 || !(p->newton_tol > 0)) return PPM_EINVAL;
     if (p->max_family < 0 || p->max_family > kMaxRow) return PPM_EINVAL;
+    if (p->bond_tile != 0 && p->bond_tile != 64 && p->bond_tile != 128 && p->bond_tile != 256)
+        return PPM_EINVAL;
     if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
         return PPM_EINVAL;
     return PPM_OK;
@@ -186,10 +189,17 @@ int run_family(ppm_ctx* c, const DevState<Real>& s) {
 }
 
 template <typename Real>
+int autotune_tile(ppm_ctx* c, const DevState<Real>& s);
+
+template <typename Real>
 int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
     CU(launch_apply_velocity_bc<Real>(s, c->k, c->stream));
     if (!c->family_built) {
         int rc = run_family<Real>(c, s);
+        if (rc) return rc;
+    }
+    if (c->p.bond_tile == 0) {
+        int rc = autotune_tile<Real>(c, s);
         if (rc) return rc;
     }
     CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
@@ -235,6 +245,49 @@ int capture_step(ppm_ctx* c, const DevState<Real>& s, bool rebuild, cudaGraphExe
     return e == cudaSuccess ? PPM_OK : PPM_ECUDA;
 }
 
+// a whole rebuild period (a family search, then R - 1 plain steps) as one graph
+template <typename Real>
+int capture_segment(ppm_ctx* c, const DevState<Real>& s, int len, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    long long nl = 0;
+    int rc = PPM_OK;
+    for (int q = 0; q < len && rc == PPM_OK; q++)
+        rc = issue_step<Real>(c, s, q == 0, c->cap_stream, nullptr, &nl);
+    c->launches_segment = nl;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc != PPM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return PPM_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? PPM_OK : PPM_ECUDA;
+}
+
+// bond-kernel tile: time the initial (dt = 0, state-preserving) bond pass
+// with 64, 128 and 256 threads per point and keep the fastest
+template <typename Real>
+int autotune_tile(ppm_ctx* c, const DevState<Real>& s) {
+    const int tiles[3] = {64, 128, 256};
+    float best = 1e30f;
+    int pick = 128;
+    for (int q = 0; q < 3; q++) {
+        c->k.tile = tiles[q];
+        CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));      // warm
+        CU(cudaEventRecord(c->ev[4], c->stream));
+        for (int r = 0; r < 2; r++) CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
+        CU(cudaEventRecord(c->ev[5], c->stream));
+        CU(cudaEventSynchronize(c->ev[5]));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
+        c->launches += 3;
+        if (ms < best) { best = ms; pick = tiles[q]; }
+    }
+    c->k.tile = pick;
+    return PPM_OK;
+}
+
 bool rebuild_due(const ppm_ctx* c) {
     return c->p.rebuild_every > 0 && (c->step + 1) % c->p.rebuild_every == 0;
 }
@@ -246,8 +299,21 @@ int do_steps(ppm_ctx* c, const DevState<Real>& s, int n_steps, double* phase_ms)
         if (rc) return rc;
         c->started = true;
     }
+    const int R = c->p.rebuild_every;
     for (int t = 0; t < n_steps; t++) {
         const bool rebuild = rebuild_due(c);
+        if (!phase_ms && c->p.use_graph && rebuild && R > 1 && R <= 64 && n_steps - t >= R) {
+            if (!c->g_segment) {
+                int rc = capture_segment<Real>(c, s, R, &c->g_segment);
+                if (rc) return rc;
+                c->segment_len = R;
+            }
+            CU(cudaGraphLaunch(c->g_segment, c->stream));
+            c->launches += c->launches_segment;
+            c->step += R;
+            t += R - 1;
+            continue;
+        }
         if (phase_ms) {
             int rc = issue_step<Real>(c, s, rebuild, c->stream, c->ev, &c->launches);
             if (rc) return rc;
@@ -396,6 +462,7 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.npoints = (int)c->N;
     k.ncols = c->ncols;
     k.max_family = z.max_family;
+    k.tile = p->bond_tile ? p->bond_tile : 128;
     k.cap = c->cap;
     k.dxf = (float)k.dx;
     k.inv_dxf = (float)k.inv_dx;
@@ -452,6 +519,8 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     c->step = 0;
     c->g_plain = nullptr;
     c->g_rebuild = nullptr;
+    c->g_segment = nullptr;
+    c->segment_len = 0;
     c->launches = 1;   // initial-state kernel
     *out = c;
     return PPM_OK;
@@ -537,6 +606,7 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     out->rebuilds = (int64_t)h.rebuilds;
     out->pairs = (int64_t)h.pairs;
     out->returns_fp64 = (int64_t)h.ret64;
+    out->bond_tile = c->k.tile;
     out->launches = c->launches;
     out->status = h.status;
     out->W_int = h.W_int;
@@ -577,6 +647,7 @@ void ppm_destroy(ppm_ctx* c) {
     if (!c) return;
     if (c->g_plain) cudaGraphExecDestroy(c->g_plain);
     if (c->g_rebuild) cudaGraphExecDestroy(c->g_rebuild);
+    if (c->g_segment) cudaGraphExecDestroy(c->g_segment);
     for (int q = 0; q < 8; q++)
         if (c->ev[q]) cudaEventDestroy(c->ev[q]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("rebuild_every", C.c_int32), ("init_stress", C.c_int32), ("visc_form", C.c_int32),
         ("newton_max_iter", C.c_int32), ("newton_tol", C.c_double),
         ("lock_lateral", C.c_int32), ("precision", C.c_int32), ("max_family", C.c_int32),
-        ("use_graph", C.c_int32),
+        ("use_graph", C.c_int32), ("bond_tile", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -51,7 +51,7 @@ class Counters(C.Structure):
     _fields_ = [("steps", C.c_int64), ("nbonds", C.c_int64), ("bond_steps", C.c_int64),
                 ("plastic", C.c_int64), ("nonconv", C.c_int64), ("singular", C.c_int64),
                 ("rebuilds", C.c_int64), ("pairs", C.c_int64), ("launches", C.c_int64),
-                ("returns_fp64", C.c_int64),
+                ("returns_fp64", C.c_int64), ("bond_tile", C.c_int32), ("pad2_", C.c_int32),
                 ("status", C.c_uint32), ("pad_", C.c_uint32),
                 ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double),
                 ("W_kin0", C.c_double)]
@@ -103,10 +103,12 @@ def _check(rc: int, what: str):
         raise PPMError(f"{what}: {msg} ({rc})")
 
 
-def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_family=0) -> Params:
+def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_family=0,
+                bond_tile=128) -> Params:
     p = Params()
     for name, _ in Params._fields_:
-        if name in ("gravity", "precision", "use_graph", "max_family", "model"):
+        if name in ("gravity", "precision", "use_graph", "max_family", "model", "pad_",
+                    "bond_tile"):
             continue
         if name in cfg:
             setattr(p, name, cfg[name])
@@ -120,6 +122,7 @@ def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_famil
     p.model = cfg.get("model", 0) if model is None else model
     p.use_graph = int(use_graph)
     p.max_family = int(cfg.get("max_family", max_family))
+    p.bond_tile = int(cfg.get("bond_tile", bond_tile))
     return p
 
 
@@ -128,14 +131,14 @@ class Simulation:
     when ``columns`` (a list of dicts with nx, ny, nz, suction, M) is given."""
 
     def __init__(self, cfg: dict, columns=None, precision=None, model=None, device=None,
-                 use_graph=True, max_family=0):
+                 use_graph=True, max_family=0, bond_tile=128):
         import torch
 
         if not torch.cuda.is_available():
             raise PPMError("no CUDA device available")
         self._torch = torch
         L = library()
-        self.params = make_params(cfg, precision, model, use_graph, max_family)
+        self.params = make_params(cfg, precision, model, use_graph, max_family, bond_tile)
         self.fp64 = self.params.precision == FP64
         self.dtype = np.float64 if self.fp64 else np.float32
         self.tdtype = torch.float64 if self.fp64 else torch.float32
@@ -248,6 +251,6 @@ class Simulation:
     def status(self) -> dict:
         c = Counters()
         _check(library().ppm_status(self._ctx, C.byref(c)), "ppm_status")
-        out = {name: getattr(c, name) for name, _ in Counters._fields_ if name != "pad_"}
+        out = {name: getattr(c, name) for name, _ in Counters._fields_ if "pad" not in name}
         out["flags"] = [k for k, b in STATUS_BITS.items() if c.status & b]
         return out

@@ -185,3 +185,56 @@ def test_mixed_near_apex_returns_use_fp64():
     st = sim.status()
     assert st["returns_fp64"] > 0
     assert rel_l2(sim.read("u"), run.u) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("tile", [64, 256])
+def test_bond_tiles_match_oracle(tile):
+    from paper_2203_05562_gb300 import Simulation
+    cfg = pi.small_config(7, 6, 9, suction=50e3, rebuild_every=3)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=13)
+    run = oracle_run(cfg, 6, v0)
+    for precision, tol, norm in (("fp64", FP64_TOL, rel_inf), ("mixed", MIXED_TOL, rel_l2)):
+        sim = Simulation(cfg, precision=precision, bond_tile=tile)
+        sim.write("v", v0)
+        sim.step(6)
+        assert sim.status()["bond_tile"] == tile
+        err = state_errors(sim, run, norm=norm)
+        assert err["u"] <= tol and err["sigma"] <= tol, (precision, err)
+
+
+def test_autotuner_picks_a_tile_and_stays_correct():
+    from paper_2203_05562_gb300 import Simulation
+    cfg = pi.config(0)
+    v0 = pi.initial_velocity(cfg)
+    run = oracle_run(cfg, 10, v0)
+    sim = Simulation(cfg, precision="mixed", bond_tile=0)
+    sim.write("v", v0)
+    sim.step(10)
+    assert sim.status()["bond_tile"] in (64, 128, 256)
+    assert rel_l2(sim.read("u"), run.u) <= MIXED_TOL
+
+
+def test_rebuild_period_graph_matches_direct_launches():
+    cfg = pi.small_config(6, 7, 9, suction=30e3, rebuild_every=4)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=2)
+    a = gpu_run(cfg, 13, "mixed", v0=v0, use_graph=True)    # 3 four-step graphs + singles
+    b = gpu_run(cfg, 13, "mixed", v0=v0, use_graph=False)
+    for f in ("u", "v", "sigma", "pc"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    assert a.status()["rebuilds"] == b.status()["rebuilds"] == 4
+
+
+def test_mixed_ensemble_matches_per_column_oracle():
+    cols = pi.ensemble_columns(count=4, seed=5, n_min=200, n_max=700)
+    cfg = pi.config("ensemble_64_columns_mixed", rebuild_every=5)
+    n = sum(c["nx"] * c["ny"] * c["nz"] for c in cols)
+    v0 = np.random.default_rng(8).normal(0, 1e-6, size=(3, n))
+    sim = gpu_run(cfg, 12, "mixed", v0=v0, columns=cols)
+    u = sim.read("u")
+    off = 0
+    for c in cols:
+        cc = dict(cfg, **c)
+        m = pi.num_points(cc)
+        run = oracle_run(cc, 12, v0[:, off:off + m])
+        assert rel_l2(u[:, off:off + m], run.u) <= MIXED_TOL
+        off += m
