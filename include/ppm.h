@@ -187,6 +187,33 @@ int ppm_status(ppm_ctx* c, ppm_counters* out);
 /* Time step in use and total number of points. */
 int ppm_info(const ppm_ctx* c, double* dt, int64_t* npoints);
 
+/* Family search (as ppm_build_families) of n points with explicit FP64
+ * positions, allocating nothing.  The paper has no counterpart of this
+ * call; it exists for callers that cannot allocate device memory -- code
+ * running while a stream is captured into a CUDA graph, real-time loops
+ * that must not enter the allocator, hosts whose device memory belongs to
+ * another allocator.
+ *
+ *   d_x        device, 3n doubles, component-major (x[c*n + i])
+ *   delta      horizon; j is in the family of i iff j != i and
+ *              ((dx*dx + dy*dy) + dz*dz) <= delta*delta
+ *   max_family most bonds one point may have (1..256); a point with more
+ *              gets an empty row and the call returns PPM_ENOSPACE
+ *   d_row_ptr  device, n+1 int32 (written); d_col, d_rev: device, cap int32
+ *              each (written: rows ascending, rev[b] = index of (j,i))
+ *   nbonds     host, may be NULL: bonds found
+ * Returns PPM_EINVAL for n < 1 or n > 262,144 points (the size of the
+ * built-in scratch) or bad arguments, PPM_ENOSPACE if the bonds exceed cap
+ * (row_ptr is then all zero).  The scratch is one fixed array of about
+ * 9.5 MB that every GPU loading the library holds until exit; its device
+ * address is looked up on the first call on each device (make that first
+ * call before any stream capture).  All calls share the array: calls that
+ * overlap on the GPU race.  The call synchronises the stream to return its
+ * status. */
+int ppm_family_noalloc(int64_t n, const double* d_x, double delta, int max_family,
+                       int32_t* d_row_ptr, int32_t* d_col, int32_t* d_rev, int64_t cap,
+                       void* cuda_stream, int64_t* nbonds);
+
 const char* ppm_error_string(int code);
 
 /* sizeof of the ABI structs as compiled into the library, so that a

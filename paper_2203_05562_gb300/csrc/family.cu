@@ -15,6 +15,11 @@ namespace ppm {
 namespace {
 
 template <typename Real>
+__device__ __forceinline__ int lat_of(const DevState<Real>& s, int i) { return s.lat ? s.lat[i] : 0; }
+template <typename Real>
+__device__ __forceinline__ int col_of(const DevState<Real>& s, int i) { return s.colid ? s.colid[i] : 0; }
+
+template <typename Real>
 struct Geometry;
 
 // FP64: absolute positions x = X0 + u with X0 = (double)ix * dx, and the
@@ -25,6 +30,7 @@ template <>
 struct Geometry<double> {
     static __device__ __forceinline__ double pos(const DevState<double>& s, const StepConst& k,
                                                  int i, int c, int l) {
+        if (s.xabs) return s.xabs[(size_t)c * k.npoints + i];
         int ic = c == 0 ? lat_x(l) : (c == 1 ? lat_y(l) : lat_z(l));
         return __dadd_rn(__dmul_rn((double)ic, k.dx), s.u[(size_t)c * k.npoints + i]);
     }
@@ -82,7 +88,7 @@ __global__ void k_bbox(DevState<Real> s, StepConst k) {
         mx[c] = (long long)0x8000000000000000ULL;
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.npoints; i += gridDim.x * blockDim.x) {
-        int l = s.lat[i];
+        int l = lat_of(s, i);
         for (int c = 0; c < 3; c++) {
             long long o = ordered(Geometry<Real>::pos(s, k, i, c, l));
             mn[c] = min(mn[c], o);
@@ -148,8 +154,8 @@ __global__ void k_cell_count(DevState<Real> s, StepConst k) {
     const CellGrid g = *s.grid;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.npoints; i += gridDim.x * blockDim.x) {
         int cc[3];
-        cell_of(s, k, g, i, s.lat[i], cc);
-        int key = s.colid[i] * g.ncell + (cc[2] * g.dims[1] + cc[1]) * g.dims[0] + cc[0];
+        cell_of(s, k, g, i, lat_of(s, i), cc);
+        int key = col_of(s, i) * g.ncell + (cc[2] * g.dims[1] + cc[1]) * g.dims[0] + cc[0];
         s.cellkey[i] = key;
         atomicAdd(&s.cellcnt[key], 1);
     }
@@ -172,7 +178,7 @@ __device__ __forceinline__ void for_each_member(const DevState<Real>& s, const S
     const int lane = threadIdx.x & 31;
     int cc[3];
     cell_of(s, k, g, i, li, cc);
-    const int base = s.colid[i] * g.ncell;
+    const int base = col_of(s, i) * g.ncell;
     for (int dz = -1; dz <= 1; dz++) {
         int z = cc[2] + dz;
         if (z < 0 || z >= g.dims[2]) continue;
@@ -190,7 +196,7 @@ __device__ __forceinline__ void for_each_member(const DevState<Real>& s, const S
                     bool ok = false;
                     if (idx < b) {
                         j = s.sorted[idx];
-                        ok = (j != i) && Geometry<Real>::within(s, k, i, li, j, s.lat[j]);
+                        ok = (j != i) && Geometry<Real>::within(s, k, i, li, j, lat_of(s, j));
                     }
                     unsigned m = __ballot_sync(0xffffffffu, ok);
                     fn(m, j, ok);
@@ -208,7 +214,7 @@ __global__ void k_family_count(DevState<Real> s, StepConst k) {
     const int lane = threadIdx.x & 31;
     for (int i = warp; i < k.npoints; i += nwarps) {
         int cnt = 0;
-        for_each_member(s, k, g, i, s.lat[i], [&](unsigned m, int, bool) { cnt += __popc(m); });
+        for_each_member(s, k, g, i, lat_of(s, i), [&](unsigned m, int, bool) { cnt += __popc(m); });
         if (lane == 0) {
             if (cnt > k.max_family) {
                 atomicOr(&s.ctr->status, PPM_STATUS_ROW_FULL);
@@ -249,7 +255,7 @@ k_family_fill(DevState<Real> s, StepConst k) {
         const int len = s.row_ptr[i + 1] - r0;
         if (len == 0) continue;
         int found = 0;
-        for_each_member(s, k, g, i, s.lat[i], [&](unsigned m, int j, bool ok) {
+        for_each_member(s, k, g, i, lat_of(s, i), [&](unsigned m, int j, bool ok) {
             int pos = found + __popc(m & ((1u << lane) - 1u));
             if (ok && pos < kMaxRow) mybuf[pos] = j;
             found += __popc(m);
@@ -287,7 +293,7 @@ __global__ void k_family_rev(DevState<Real> s, StepConst k) {
             const int rb = (lo < end && s.col[lo] == i) ? lo : -1;
             s.rev[b] = rb;
             // a bond without a reverse partner receives no force state
-            if (rb < 0) {
+            if (rb < 0 && s.Trev) {
                 s.Trev[b] = (Real)0;
                 s.Trev[k.cap + b] = (Real)0;
                 s.Trev[2 * k.cap + b] = (Real)0;

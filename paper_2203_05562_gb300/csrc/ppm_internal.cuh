@@ -60,8 +60,9 @@ struct StepConst {
 // device pointers of one context (Real = double for FP64, float for mixed)
 template <typename Real>
 struct DevState {
-    int32_t* lat;        // packed lattice index, N
-    int32_t* colid;      // column of each point, N
+    const double* xabs;  // family search only: explicit FP64 positions (3N), else null
+    int32_t* lat;        // packed lattice index, N (may be null when xabs is set)
+    int32_t* colid;      // column of each point, N (null: one column)
     const ColumnConst* cols;
     Real* u;             // 3N
     float* ulo;          // 3N compensation of u (mixed only; else null)

@@ -111,6 +111,7 @@ template <typename Real>
 void carve(Layout& L, char* base, int64_t N, long long cap, int ncell_cap, int gather_blocks,
            int ncols, bool mixed, DevState<Real>& s, ColumnConst** d_cols) {
     const size_t n = (size_t)N;
+    s.xabs = nullptr;
     s.lat = L.take<int32_t>(base, n);
     s.colid = L.take<int32_t>(base, n);
     *d_cols = L.take<ColumnConst>(base, (size_t)ncols);

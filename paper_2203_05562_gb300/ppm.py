@@ -86,6 +86,8 @@ def library(build_if_missing: bool = True):
             L.ppm_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
             L.ppm_error_string.restype = C.c_char_p
             L.ppm_error_string.argtypes = [C.c_int]
+            L.ppm_family_noalloc.argtypes = [C.c_int64, vp, C.c_double, C.c_int, vp, vp, vp,
+                                             C.c_int64, vp, C.POINTER(C.c_int64)]
             L.ppm_struct_size.restype = C.c_size_t
             L.ppm_struct_size.argtypes = [C.c_int]
             L.ppm_destroy.restype = None
@@ -124,6 +126,31 @@ def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_famil
     p.max_family = int(cfg.get("max_family", max_family))
     p.bond_tile = int(cfg.get("bond_tile", bond_tile))
     return p
+
+
+def family_noalloc(x, delta: float, max_family: int = 192, cap: int | None = None):
+    """Family of the points x (torch CUDA tensor (3, n), float64) through
+    ``ppm_family_noalloc``, which allocates no device memory itself; the
+    output tensors are allocated here by the caller side.  Returns
+    (row_ptr, col, rev) as CUDA tensors."""
+    import torch
+
+    if x.dtype != torch.float64 or not x.is_cuda or x.dim() != 2 or x.shape[0] != 3:
+        raise PPMError("x must be a (3, n) float64 CUDA tensor")
+    x = x.contiguous()
+    n = x.shape[1]
+    cap = n * max_family if cap is None else cap
+    row_ptr = torch.empty(n + 1, dtype=torch.int32, device=x.device)
+    col = torch.empty(max(cap, 1), dtype=torch.int32, device=x.device)
+    rev = torch.empty(max(cap, 1), dtype=torch.int32, device=x.device)
+    nb = C.c_int64(0)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(library().ppm_family_noalloc(n, C.c_void_p(x.data_ptr()), float(delta), int(max_family),
+                                        C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()),
+                                        C.c_void_p(rev.data_ptr()), cap, C.c_void_p(stream),
+                                        C.byref(nb)), "ppm_family_noalloc")
+    B = int(nb.value)
+    return row_ptr, col[:B], rev[:B]
 
 
 class Simulation:
