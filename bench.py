@@ -42,6 +42,24 @@ SMS, LANES = 152, 128
 FLOPS_TEST, FLOPS_PAIR = 8, 30
 
 
+def profiled_traffic():
+    """DRAM bytes per launch of the bond kernel from the committed ncu
+    summary, or None when csrc/bond.cu has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "bond_kernel_collapse_40x40x80.json")
+    src = os.path.join(ROOT, "paper_2203_05562_gb300", "csrc", "bond.cu")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if prof.get("bond_cu_sha256_16") != digest:
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -251,7 +269,8 @@ def main():
     peak_tflops = SMS * LANES * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (bond_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": profiled_traffic(),
+                "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                 "kernel": "k_bond<float,0> (fused sub-horizon / constitutive / force state)",
                 "peak_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
                 "bond_kernel_ms": bond_ms, "gather_ms": phase[2] / nph,
