@@ -93,6 +93,7 @@ def lib():
             L.ppmo_internal_force.argtypes = [pp, C.c_int64, dp, dp, ip, ip, ip, dp]
             L.ppmo_init.argtypes = [pp, dp, C.POINTER(State)]
             L.ppmo_step.argtypes = [pp, C.POINTER(State), C.c_int]
+            L.ppmo_objective_gradient.argtypes = [pp, dp, C.c_int, C.c_int64, dp, dp]
             L.ppmo_num_threads.restype = C.c_int
             L.ppmo_set_num_threads.argtypes = [C.c_int]
             L.ppmo_set_num_threads.restype = None
@@ -228,6 +229,29 @@ def internal_force(cfg, x, sig, row_ptr, col, rev):
                               _i(np.ascontiguousarray(col, np.int32)),
                               _i(np.ascontiguousarray(rev, np.int32)), _d(f))
     return f.reshape(3, n)
+
+
+def objective(cfg, v0, n_steps):
+    """J = sum over the top layer of u_x^2 + u_y^2 after n_steps (forward only)."""
+    r = Run(cfg, v0)
+    r.step(n_steps)
+    nxy = r.p.nx * r.p.ny
+    top = slice(r.n - nxy, r.n)
+    return float((r.u[0, top] ** 2).sum() + (r.u[1, top] ** 2).sum())
+
+
+def objective_gradient(cfg, v0, n_steps, cap_per_point=256):
+    """J and dJ/d(M, eta, suction, pc0) by the reverse of every step."""
+    p = make_params(cfg)
+    n = p.nx * p.ny * p.nz
+    v = np.ascontiguousarray(v0, np.float64).reshape(3 * n) if v0 is not None else None
+    J = np.zeros(1)
+    g = np.zeros(4)
+    rc = lib().ppmo_objective_gradient(C.byref(p), _d(v) if v is not None else None, int(n_steps),
+                                       n * cap_per_point, _d(J), _d(g))
+    if rc != 0:
+        raise RuntimeError(f"ppmo_objective_gradient failed ({rc})")
+    return float(J[0]), g
 
 
 def set_threads(t: int):

@@ -318,84 +318,107 @@ static int return_map(const ppmo_params* p, double c, double p_tr, double q_tr, 
     }
 }
 
-int ppmo_material_update(const ppmo_params* p, const double sig_n[6], double pc_n,
-                         const double L[9], double dt, double sig_out[6], double* pc_out,
-                         double* deps_s, int32_t* flags) {
-    double D[3][3], W[3][3];
+/* Everything one constitutive update computes, kept for its reverse. */
+typedef struct {
+    double dt, pc_n;
+    double W[3][3], Bm[3][3], Cm[3][3], Bi[3][3], Q[3][3], S[3][3], R[3][3];
+    double de[3][3], Str[3][3], s_tr[3][3];
+    double p_tr, q_tr, f_tr, c, eta_eff;
+    double x[3];
+    int plastic, converged, floored;
+    double sig_out[6], pc_out, deps_s;
+} mu_trace;
+
+/* Sec. 2.3 / 3.2.1: rotation, trial stress, yield test and return */
+static int mu_forward(const ppmo_params* p, const double sig_n[6], double pc_n, const double L[9],
+                      double dt, mu_trace* t) {
+    double D[3][3];
+    t->dt = dt;
+    t->pc_n = pc_n;
     for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
             D[r][c] = 0.5 * (L[r * 3 + c] + L[c * 3 + r]);   /* Eq. 26 */
-            W[r][c] = 0.5 * (L[r * 3 + c] - L[c * 3 + r]);
+            t->W[r][c] = 0.5 * (L[r * 3 + c] - L[c * 3 + r]);
         }
     /* Hughes-Winget: Q = (I - dt/2 W)^-1 (I + dt/2 W), sigma_rot = Q sigma Q^T */
-    double Bm[3][3], Cm[3][3], Bi[3][3], Q[3][3];
     for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
             double I = (r == c) ? 1.0 : 0.0;
-            Bm[r][c] = I - 0.5 * dt * W[r][c];
-            Cm[r][c] = I + 0.5 * dt * W[r][c];
+            t->Bm[r][c] = I - 0.5 * dt * t->W[r][c];
+            t->Cm[r][c] = I + 0.5 * dt * t->W[r][c];
         }
-    if (!inv3(Bm, Bi)) return -1;
-    matmul3(Bi, Cm, Q);
-    double S[3][3], QS[3][3], QT[3][3], R[3][3];
-    sym_to_mat(sig_n, S);
-    matmul3(Q, S, QS);
+    if (!inv3(t->Bm, t->Bi)) return -1;
+    matmul3(t->Bi, t->Cm, t->Q);
+    double QS[3][3], QT[3][3];
+    sym_to_mat(sig_n, t->S);
+    matmul3(t->Q, t->S, QS);
     for (int r = 0; r < 3; r++)
-        for (int c = 0; c < 3; c++) QT[r][c] = Q[c][r];
-    matmul3(QS, QT, R);
+        for (int c = 0; c < 3; c++) QT[r][c] = t->Q[c][r];
+    matmul3(QS, QT, t->R);
     /* strain increment (Eq. 59) and linear hypo-elastic trial (Eq. 41) */
-    double de[3][3];
     for (int r = 0; r < 3; r++)
-        for (int c = 0; c < 3; c++) de[r][c] = dt * D[r][c];
-    double trv = de[0][0] + de[1][1] + de[2][2];
-    double Str[3][3];
+        for (int c = 0; c < 3; c++) t->de[r][c] = dt * D[r][c];
+    double trv = t->de[0][0] + t->de[1][1] + t->de[2][2];
     for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
             double I = (r == c) ? 1.0 : 0.0;
-            Str[r][c] = R[r][c] + p->K * trv * I + 2.0 * p->mu * (de[r][c] - trv / 3.0 * I);
+            t->Str[r][c] = t->R[r][c] + p->K * trv * I + 2.0 * p->mu * (t->de[r][c] - trv / 3.0 * I);
         }
     /* equivalent shear strain of the increment */
     double ss = 0.0;
     for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
             double I = (r == c) ? 1.0 : 0.0;
-            double e = de[r][c] - trv / 3.0 * I;
+            double e = t->de[r][c] - trv / 3.0 * I;
             ss += e * e;
         }
-    *deps_s = sqrt(2.0 / 3.0 * ss);
+    t->deps_s = sqrt(2.0 / 3.0 * ss);
     /* invariants and yield function, Eq. 40 */
-    double p_tr = (Str[0][0] + Str[1][1] + Str[2][2]) / 3.0;
-    double s_tr[3][3], sn = 0.0;
+    t->p_tr = (t->Str[0][0] + t->Str[1][1] + t->Str[2][2]) / 3.0;
+    double sn = 0.0;
     for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
             double I = (r == c) ? 1.0 : 0.0;
-            s_tr[r][c] = Str[r][c] - p_tr * I;
-            sn += s_tr[r][c] * s_tr[r][c];
+            t->s_tr[r][c] = t->Str[r][c] - t->p_tr * I;
+            sn += t->s_tr[r][c] * t->s_tr[r][c];
         }
-    double q_tr = sqrt(1.5 * sn);
-    double f_tr = q_tr * q_tr / (p->M * p->M) + p_tr * (p_tr - pc_n);
-    *flags = 0;
-    if (!(f_tr > 0.0) || dt == 0.0) {          /* elastic, Eq. 44 */
-        mat_to_sym(Str, sig_out);
-        *pc_out = pc_n;
+    t->q_tr = sqrt(1.5 * sn);
+    t->f_tr = t->q_tr * t->q_tr / (p->M * p->M) + t->p_tr * (t->p_tr - pc_n);
+    t->plastic = 0;
+    t->converged = 1;
+    t->floored = 0;
+    if (!(t->f_tr > 0.0) || dt == 0.0) {          /* elastic, Eq. 44 */
+        mat_to_sym(t->Str, t->sig_out);
+        t->pc_out = pc_n;
         return 0;
     }
-    double eta_eff = (p->visc_form == 0) ? p->eta * pc_n * pc_n : p->eta;
-    double c = dt / eta_eff;
-    double x[3];
-    int ok = return_map(p, c, p_tr, q_tr, pc_n, x);
-    *flags = 1 | (ok ? 0 : 2);
-    double ratio = (q_tr > 0.0) ? x[1] / q_tr : 0.0;
+    t->plastic = 1;
+    t->eta_eff = (p->visc_form == 0) ? p->eta * pc_n * pc_n : p->eta;
+    t->c = dt / t->eta_eff;
+    t->converged = return_map(p, t->c, t->p_tr, t->q_tr, pc_n, t->x);
+    double ratio = (t->q_tr > 0.0) ? t->x[1] / t->q_tr : 0.0;
     double out[3][3];
     for (int r = 0; r < 3; r++)
         for (int cc = 0; cc < 3; cc++) {
             double I = (r == cc) ? 1.0 : 0.0;
-            out[r][cc] = x[0] * I + ratio * s_tr[r][cc];
+            out[r][cc] = t->x[0] * I + ratio * t->s_tr[r][cc];
         }
-    mat_to_sym(out, sig_out);
-    double pc_new = x[2];
-    if (pc_new > -1.0) pc_new = -1.0;             /* floor at the apex */
-    *pc_out = pc_new;
+    mat_to_sym(out, t->sig_out);
+    double pc_new = t->x[2];
+    if (pc_new > -1.0) { pc_new = -1.0; t->floored = 1; }   /* floor at the apex */
+    t->pc_out = pc_new;
+    return 0;
+}
+
+int ppmo_material_update(const ppmo_params* p, const double sig_n[6], double pc_n,
+                         const double L[9], double dt, double sig_out[6], double* pc_out,
+                         double* deps_s, int32_t* flags) {
+    mu_trace t;
+    if (mu_forward(p, sig_n, pc_n, L, dt, &t) != 0) return -1;
+    for (int c = 0; c < 6; c++) sig_out[c] = t.sig_out[c];
+    *pc_out = t.pc_out;
+    *deps_s = t.deps_s;
+    *flags = t.plastic ? (1 | (t.converged ? 0 : 2)) : 0;
     return 0;
 }
 
@@ -765,6 +788,441 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         s->step++;
     }
     free(x); free(vh); free(f_old);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* reverse (adjoint) of the step, for the gradient of an objective     */
+/* ------------------------------------------------------------------ */
+
+static void transpose3(double A[3][3], double T[3][3]) {
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) T[r][c] = A[c][r];
+}
+
+/* full symmetric adjoint (off-diagonals shared) -> 6 stored components */
+static void sym_adj_to6(double M[3][3], double a6[6]) {
+    a6[0] = M[0][0]; a6[1] = M[1][1]; a6[2] = M[2][2];
+    a6[3] = M[1][2] + M[2][1]; a6[4] = M[0][2] + M[2][0]; a6[5] = M[0][1] + M[1][0];
+}
+
+/* 6 stored components -> full symmetric adjoint */
+static void six_to_sym_adj(const double a6[6], double M[3][3]) {
+    M[0][0] = a6[0]; M[1][1] = a6[1]; M[2][2] = a6[2];
+    M[1][2] = M[2][1] = 0.5 * a6[3];
+    M[0][2] = M[2][0] = 0.5 * a6[4];
+    M[0][1] = M[1][0] = 0.5 * a6[5];
+}
+
+/* Reverse of mu_forward.  In: Sbo (adjoint of the output stress, full
+ * symmetric), pcbo (of the output pc).  Out (accumulated): Sbi (of the input
+ * stress, full), *pcbi, Lb (of L), *Mb, *etab. */
+static void mu_reverse(const ppmo_params* p, const mu_trace* t, double Sbo[3][3], double pcbo,
+                       double Sbi[3][3], double* pcbi, double Lb[3][3], double* Mb,
+                       double* etab) {
+    double Strb[3][3];
+    const double dt = t->dt;
+    if (!t->plastic) {
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) Strb[r][c] = Sbo[r][c];
+        *pcbi += pcbo;
+    } else {
+        const double q_tr = t->q_tr;
+        const double ratio = (q_tr > 0.0) ? t->x[1] / q_tr : 0.0;
+        double xb[3], sb[3][3];
+        xb[0] = Sbo[0][0] + Sbo[1][1] + Sbo[2][2];
+        double ratiob = 0.0;
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) {
+                ratiob += Sbo[r][c] * t->s_tr[r][c];
+                sb[r][c] = ratio * Sbo[r][c];
+            }
+        double q_trb = 0.0;
+        xb[1] = 0.0;
+        if (q_tr > 0.0) {
+            xb[1] = ratiob / q_tr;
+            q_trb = -ratiob * t->x[1] / (q_tr * q_tr);
+        }
+        xb[2] = t->floored ? 0.0 : pcbo;
+        /* implicit function: J_x^T lambda = xb, ybar = -J_y^T lambda */
+        double r[3], J[9], JT[9], lam[3] = {0, 0, 0};
+        ppmo_return_residual(p, t->c, t->p_tr, q_tr, t->pc_n, t->x, r, J);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) JT[a * 3 + b] = J[b * 3 + a];
+        if (!solve3(JT, xb, lam)) { lam[0] = lam[1] = lam[2] = 0.0; }
+        const double M2 = p->M * p->M, lk = p->lambda_t - p->kappa_t, c = t->c;
+        const double pb = t->x[0], q = t->x[1], pc = t->x[2];
+        const double f = q * q / M2 + pb * (pb - pc);
+        const double fp = 2.0 * pb - pc, fq = 2.0 * q / M2;
+        double p_trb = lam[0];
+        q_trb += lam[1];
+        double pc_nb = lam[2] / t->pc_n;
+        double cb = -(lam[0] * p->K * f * fp + lam[1] * 3.0 * p->mu * f * fq + lam[2] * f * fp / lk);
+        const double dfdM = -2.0 * q * q / (M2 * p->M), dfqdM = -4.0 * q / (M2 * p->M);
+        *Mb -= lam[0] * p->K * c * fp * dfdM + lam[1] * 3.0 * p->mu * c * (dfdM * fq + f * dfqdM) +
+               lam[2] * c * fp * dfdM / lk;
+        /* c = dt / eta_eff */
+        *etab += cb * (-c / p->eta);
+        if (p->visc_form == 0) pc_nb += cb * (-2.0 * c / t->pc_n);
+        *pcbi += pc_nb;
+        /* p_tr = tr(Str)/3, s_tr = Str - p_tr 1, q_tr = sqrt(1.5 s:s) */
+        if (q_tr > 0.0)
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) sb[a][b] += q_trb * 1.5 * t->s_tr[a][b] / q_tr;
+        double trs = sb[0][0] + sb[1][1] + sb[2][2];
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                Strb[a][b] = sb[a][b] + ((a == b) ? (p_trb - trs) / 3.0 : 0.0);
+    }
+    /* Str = R + K tr(de) 1 + 2 mu dev(de) */
+    double trS = Strb[0][0] + Strb[1][1] + Strb[2][2], deb[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            deb[a][b] = 2.0 * p->mu * (Strb[a][b] - ((a == b) ? trS / 3.0 : 0.0)) +
+                        ((a == b) ? p->K * trS : 0.0);
+    /* R = Q S Q^T */
+    double QT[3][3], tmp[3][3], Sb[3][3], Qb[3][3], RRT[3][3];
+    transpose3((double(*)[3])t->Q, QT);
+    matmul3(QT, Strb, tmp);
+    matmul3(tmp, (double(*)[3])t->Q, Sb);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            Sbi[a][b] += Sb[a][b];
+            RRT[a][b] = Strb[a][b] + Strb[b][a];
+        }
+    matmul3(RRT, (double(*)[3])t->Q, tmp);
+    matmul3(tmp, (double(*)[3])t->S, Qb);
+    /* Q = Bi Cm, Bi = Bm^-1 */
+    double BiT[3][3], CmT[3][3], Cmb[3][3], Bib[3][3], Bmb[3][3];
+    transpose3((double(*)[3])t->Bi, BiT);
+    transpose3((double(*)[3])t->Cm, CmT);
+    matmul3(BiT, Qb, Cmb);
+    matmul3(Qb, CmT, Bib);
+    matmul3(BiT, Bib, tmp);
+    matmul3(tmp, BiT, Bmb);
+    double Wb[3][3], Db[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            Wb[a][b] = 0.5 * dt * (Cmb[a][b] + Bmb[a][b]);   /* adjoint of Bm is -Bmb; Bm = I - dt/2 W */
+            Db[a][b] = dt * deb[a][b];
+        }
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            Lb[a][b] += 0.5 * (Db[a][b] + Db[b][a]) + 0.5 * (Wb[a][b] - Wb[b][a]);
+}
+
+typedef struct {
+    int32_t *row_ptr, *col, *rev;
+} family_copy;
+
+/* Reverse of one step n -> n+1 from its start state, with the family the
+ * forward step used.  ub, vb, ab (3n), sb (6n), pcb (n) hold the adjoint of
+ * the state after the step on entry and of the state before it on exit;
+ * thb accumulates (M, eta, S_r s). */
+static void reverse_step(const ppmo_params* p, int64_t n, const double* u, const double* v,
+                         const double* a, const double* sig, const double* pc,
+                         const family_copy* F, double* ub, double* vb, double* ab, double* sb,
+                         double* pcb, double thb[3]) {
+    const double dt = ppmo_time_step(p), h = 0.5 * dt;
+    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
+    const double Srs = ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
+    const double delta = p->horizon_factor * p->dx, d2max = delta * delta;
+    double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* vh = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* fb = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* u1b = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* vhb = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* sbn = (double*)calloc(6 * (size_t)n, sizeof(double));
+    double* pcbn = (double*)calloc((size_t)n, sizeof(double));
+    ppmo_reference_positions(p, x);
+    for (int64_t i = 0; i < n; i++)
+        for (int c = 0; c < 3; c++) {
+            size_t t = (size_t)c * n + i;
+            double w = v[t] + h * a[t];
+            int fixed = is_base(p, i) || (p->lock_lateral && c < 2);
+            if (fixed) w = 0.0;
+            vh[t] = w;
+            x[t] += u[t] + dt * w;
+            /* v' = vh + h a' ; a' = f/m + g (fixed components: a' = 0) */
+            double abt = ab[t] + h * vb[t];
+            fb[t] = fixed ? 0.0 : abt / m;
+            vhb[t] = vb[t];
+            u1b[t] = ub[t];
+        }
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t r0 = F->row_ptr[i], r1 = F->row_ptr[i + 1], nb = r1 - r0;
+        double sig_i[6];
+        for (int c = 0; c < 6; c++) sig_i[c] = sig[c * n + i];
+        /* forward recompute: active bonds and their weights */
+        double w = 0.0;
+        for (int64_t b = r0; b < r1; b++) {
+            subhorizon_sums ss;
+            subhorizon(p, n, x, vh, F->row_ptr, F->col, i, F->col[b], &ss);
+            double Ki[3][3];
+            if (shape_ok(ss.count, ss.K) && inv3(ss.K, Ki)) w += (double)ss.count / (double)nb;
+        }
+        double Spt[3][3];
+        double a6[6];
+        for (int c = 0; c < 6; c++) a6[c] = sb[c * n + i];
+        six_to_sym_adj(a6, Spt);
+        const double pcpt = pcb[i];
+        double Sbi[3][3] = {{0}};
+        double pcbi = 0.0;
+        if (!(w > 0.0)) {
+            for (int c = 0; c < 6; c++) sbn[c * n + i] += a6[c];
+            pcbn[i] += pcpt;
+        }
+        for (int64_t b = r0; b < r1; b++) {
+            const int64_t j = F->col[b];
+            subhorizon_sums ss;
+            subhorizon(p, n, x, vh, F->row_ptr, F->col, i, j, &ss);
+            double Ki[3][3];
+            if (!(shape_ok(ss.count, ss.K) && inv3(ss.K, Ki))) continue;
+            const double varpi = (double)ss.count / (double)nb;
+            double L[3][3], Lf[9];
+            matmul3(ss.A, Ki, L);
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Lf[r * 3 + c] = L[r][c];
+            mu_trace t;
+            mu_forward(p, sig_i, pc[i], Lf, dt, &t);
+            double Sh[3][3], zj[3], g[3], Tb[3];
+            sym_to_mat(t.sig_out, Sh);
+            for (int c = 0; c < 3; c++) Sh[c][c] += Srs;
+            for (int c = 0; c < 3; c++) {
+                zj[c] = x[c * n + j] - x[c * n + i];
+                Tb[c] = V * V * (fb[c * n + i] - fb[c * n + j]);   /* Eq. 49 reversed */
+            }
+            for (int r = 0; r < 3; r++) {
+                g[r] = 0.0;
+                for (int c = 0; c < 3; c++) g[r] += Ki[r][c] * zj[c];
+            }
+            /* T = varpi Sh Ki zj */
+            double Sob[3][3], STb[3], Kib[3][3], zjb[3];
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Sob[r][c] = varpi * 0.5 * (Tb[r] * g[c] + g[r] * Tb[c]);
+            thb[2] += Sob[0][0] + Sob[1][1] + Sob[2][2];
+            for (int r = 0; r < 3; r++) {
+                STb[r] = 0.0;
+                for (int c = 0; c < 3; c++) STb[r] += Sh[c][r] * Tb[c];
+            }
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Kib[r][c] = varpi * STb[r] * zj[c];
+            for (int r = 0; r < 3; r++) {
+                zjb[r] = 0.0;
+                for (int c = 0; c < 3; c++) zjb[r] += varpi * Ki[r][c] * STb[c];
+            }
+            /* point state: sig' = sum varpi sig_b / w */
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Sob[r][c] += varpi / w * Spt[r][c];
+            const double pcbo = varpi / w * pcpt;
+            double Lb[3][3] = {{0}};
+            mu_reverse(p, &t, Sob, pcbo, Sbi, &pcbi, Lb, &thb[0], &thb[1]);
+            /* L = A Ki */
+            double KiT[3][3], AT[3][3], Ab[3][3], tmp[3][3], Kb[3][3];
+            transpose3(Ki, KiT);
+            transpose3(ss.A, AT);
+            matmul3(Lb, KiT, Ab);
+            matmul3(AT, Lb, tmp);
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Kib[r][c] += tmp[r][c];
+            /* Ki = K^-1 */
+            matmul3(KiT, Kib, tmp);
+            matmul3(tmp, KiT, Kb);
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Kb[r][c] = -Kb[r][c];
+            /* K = V sum zeta zeta^T, A = V sum Ydot zeta^T over the sub-horizon */
+            for (int64_t b2 = r0; b2 < r1; b2++) {
+                const int64_t k = F->col[b2];
+                if (!((p->model == 1) || (dist2(x, n, j, k) <= d2max))) continue;
+                double zk[3], yk[3], zb[3], yb[3];
+                for (int c = 0; c < 3; c++) {
+                    zk[c] = x[c * n + k] - x[c * n + i];
+                    yk[c] = vh[c * n + k] - vh[c * n + i];
+                }
+                for (int r = 0; r < 3; r++) {
+                    zb[r] = 0.0;
+                    yb[r] = 0.0;
+                    for (int c = 0; c < 3; c++) {
+                        zb[r] += V * (Kb[r][c] + Kb[c][r]) * zk[c] + V * Ab[c][r] * yk[c];
+                        yb[r] += V * Ab[r][c] * zk[c];
+                    }
+                }
+                for (int c = 0; c < 3; c++) {
+                    u1b[c * n + k] += zb[c];
+                    u1b[c * n + i] -= zb[c];
+                    vhb[c * n + k] += yb[c];
+                    vhb[c * n + i] -= yb[c];
+                }
+            }
+            for (int c = 0; c < 3; c++) {
+                u1b[c * n + j] += zjb[c];
+                u1b[c * n + i] -= zjb[c];
+            }
+        }
+        double s6[6];
+        sym_adj_to6(Sbi, s6);
+        for (int c = 0; c < 6; c++) sbn[c * n + i] += s6[c];
+        pcbn[i] += pcbi;
+    }
+    /* predictor: u' = u + dt vh, vh = v + h a (fixed components: 0) */
+    for (int64_t i = 0; i < n; i++)
+        for (int c = 0; c < 3; c++) {
+            size_t t = (size_t)c * n + i;
+            double vht = vhb[t] + dt * u1b[t];
+            int fixed = is_base(p, i) || (p->lock_lateral && c < 2);
+            ub[t] = u1b[t];
+            vb[t] = fixed ? 0.0 : vht;
+            ab[t] = fixed ? 0.0 : h * vht;
+        }
+    memcpy(sb, sbn, sizeof(double) * 6 * (size_t)n);
+    memcpy(pcb, pcbn, sizeof(double) * (size_t)n);
+    free(x); free(vh); free(fb); free(u1b); free(vhb); free(sbn); free(pcbn);
+}
+
+/* Reverse of the initial pass a0 = f0/m + g (every bond carries sigma0). */
+static void reverse_initial(const ppmo_params* p, int64_t n, const double* sig0,
+                            const family_copy* F, const double* ab, double* sb, double* Srsb) {
+    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
+    double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* fb = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* zero = (double*)calloc(3 * (size_t)n, sizeof(double));
+    ppmo_reference_positions(p, x);
+    for (int64_t i = 0; i < n; i++)
+        for (int c = 0; c < 3; c++) {
+            size_t t = (size_t)c * n + i;
+            int fixed = is_base(p, i) || (p->lock_lateral && c < 2);
+            fb[t] = fixed ? 0.0 : ab[t] / m;
+        }
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t r0 = F->row_ptr[i], r1 = F->row_ptr[i + 1], nb = r1 - r0;
+        double Sacc[3][3] = {{0}};
+        for (int64_t b = r0; b < r1; b++) {
+            const int64_t j = F->col[b];
+            subhorizon_sums ss;
+            subhorizon(p, n, x, zero, F->row_ptr, F->col, i, j, &ss);
+            double Ki[3][3];
+            if (!(shape_ok(ss.count, ss.K) && inv3(ss.K, Ki))) continue;
+            const double varpi = (double)ss.count / (double)nb;
+            double zj[3], g[3], Tb[3];
+            for (int c = 0; c < 3; c++) {
+                zj[c] = x[c * n + j] - x[c * n + i];
+                Tb[c] = V * V * (fb[c * n + i] - fb[c * n + j]);
+            }
+            for (int r = 0; r < 3; r++) {
+                g[r] = 0.0;
+                for (int c = 0; c < 3; c++) g[r] += Ki[r][c] * zj[c];
+            }
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Sacc[r][c] += varpi * 0.5 * (Tb[r] * g[c] + g[r] * Tb[c]);
+        }
+        *Srsb += Sacc[0][0] + Sacc[1][1] + Sacc[2][2];
+        double s6[6];
+        sym_adj_to6(Sacc, s6);
+        for (int c = 0; c < 6; c++) sb[c * n + i] += s6[c];
+    }
+    free(x); free(fb); free(zero);
+}
+
+static double dSrs_ds(const ppmo_params* p) {
+    const double s = p->suction, al = p->vg_alpha, nn = p->vg_n, mm = 1.0 - 1.0 / nn;
+    if (s <= 0.0) return 1.0;
+    const double base = 1.0 + pow(al * s, nn);
+    const double Sr = pow(base, -mm);
+    const double dSr = -mm * pow(base, -mm - 1.0) * nn * pow(al * s, nn - 1.0) * al;
+    return Sr + s * dSr;
+}
+
+static int is_top(const ppmo_params* p, int64_t id) {
+    return (id / ((int64_t)p->nx * p->ny)) == p->nz - 1;
+}
+
+int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps, int64_t cap,
+                            double* J, double grad[4]) {
+    if (!params_ok(p) || p->model == 2 || n_steps < 0) return -1;
+    const int64_t n = (int64_t)p->nx * p->ny * p->nz;
+    ppmo_state s;
+    memset(&s, 0, sizeof(s));
+    s.n = n;
+    s.cap = cap;
+    s.u = (double*)calloc(3 * (size_t)n, sizeof(double));
+    s.v = (double*)calloc(3 * (size_t)n, sizeof(double));
+    s.a = (double*)calloc(3 * (size_t)n, sizeof(double));
+    s.sig = (double*)calloc(6 * (size_t)n, sizeof(double));
+    s.pc = (double*)calloc((size_t)n, sizeof(double));
+    s.eps_s = (double*)calloc((size_t)n, sizeof(double));
+    s.fint = (double*)calloc(3 * (size_t)n, sizeof(double));
+    s.tforce = (double*)calloc(3 * (size_t)cap, sizeof(double));
+    s.row_ptr = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    s.col = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
+    s.rev = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
+    /* states before every step and the family each step used */
+    const size_t N3 = 3 * (size_t)n, N6 = 6 * (size_t)n;
+    double* hist = (double*)malloc(sizeof(double) * (N3 * 3 + N6 + (size_t)n) * ((size_t)n_steps + 1));
+    family_copy* fam = (family_copy*)calloc((size_t)n_steps + 1, sizeof(family_copy));
+    int rc = ppmo_init(p, v0, &s);
+    if (rc != 0) return rc;
+    const size_t per = N3 * 3 + N6 + (size_t)n;
+    double* sig0 = (double*)malloc(sizeof(double) * N6);
+    memcpy(sig0, s.sig, sizeof(double) * N6);
+    family_copy fam0;
+    fam0.row_ptr = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    fam0.col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s.nbonds > 0 ? s.nbonds : 1));
+    fam0.rev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s.nbonds > 0 ? s.nbonds : 1));
+    memcpy(fam0.row_ptr, s.row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+    memcpy(fam0.col, s.col, sizeof(int32_t) * (size_t)s.nbonds);
+    memcpy(fam0.rev, s.rev, sizeof(int32_t) * (size_t)s.nbonds);
+    for (int st = 0; st < n_steps; st++) {
+        double* hp = hist + per * (size_t)st;
+        memcpy(hp, s.u, sizeof(double) * N3);
+        memcpy(hp + N3, s.v, sizeof(double) * N3);
+        memcpy(hp + 2 * N3, s.a, sizeof(double) * N3);
+        memcpy(hp + 3 * N3, s.sig, sizeof(double) * N6);
+        memcpy(hp + 3 * N3 + N6, s.pc, sizeof(double) * (size_t)n);
+        ppmo_step(p, &s, 1);
+        fam[st].row_ptr = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+        fam[st].col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s.nbonds > 0 ? s.nbonds : 1));
+        fam[st].rev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s.nbonds > 0 ? s.nbonds : 1));
+        memcpy(fam[st].row_ptr, s.row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+        memcpy(fam[st].col, s.col, sizeof(int32_t) * (size_t)s.nbonds);
+        memcpy(fam[st].rev, s.rev, sizeof(int32_t) * (size_t)s.nbonds);
+    }
+    /* objective: sum over the top layer of u_x^2 + u_y^2 */
+    double* ub = (double*)calloc(N3, sizeof(double));
+    double* vb = (double*)calloc(N3, sizeof(double));
+    double* ab = (double*)calloc(N3, sizeof(double));
+    double* sb = (double*)calloc(N6, sizeof(double));
+    double* pcb = (double*)calloc((size_t)n, sizeof(double));
+    double Jv = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        if (is_top(p, i))
+            for (int c = 0; c < 2; c++) {
+                Jv += s.u[c * n + i] * s.u[c * n + i];
+                ub[c * n + i] = 2.0 * s.u[c * n + i];
+            }
+    double thb[3] = {0.0, 0.0, 0.0};
+    for (int st = n_steps - 1; st >= 0; st--) {
+        double* hp = hist + per * (size_t)st;
+        reverse_step(p, n, hp, hp + N3, hp + 2 * N3, hp + 3 * N3, hp + 3 * N3 + N6, &fam[st], ub,
+                     vb, ab, sb, pcb, thb);
+    }
+    reverse_initial(p, n, sig0, &fam0, ab, sb, &thb[2]);
+    /* initial state: sigma0 = geostatic - S_r s 1 (init_stress 0), pc = -pc0 */
+    double pc0b = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        if (p->init_stress == 0) thb[2] -= sb[0 * n + i] + sb[1 * n + i] + sb[2 * n + i];
+        pc0b -= pcb[i];
+    }
+    *J = Jv;
+    grad[0] = thb[0];
+    grad[1] = thb[1];
+    grad[2] = thb[2] * dSrs_ds(p);
+    grad[3] = pc0b;
+    for (int st = 0; st < n_steps; st++) { free(fam[st].row_ptr); free(fam[st].col); free(fam[st].rev); }
+    free(fam); free(hist); free(sig0);
+    free(fam0.row_ptr); free(fam0.col); free(fam0.rev);
+    free(ub); free(vb); free(ab); free(sb); free(pcb);
+    free(s.u); free(s.v); free(s.a); free(s.sig); free(s.pc); free(s.eps_s); free(s.fint);
+    free(s.tforce); free(s.row_ptr); free(s.col); free(s.rev);
     return 0;
 }
 

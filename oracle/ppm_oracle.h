@@ -113,6 +113,13 @@ int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s);
 /* Alg. 2, lines 5-13: n_steps explicit central-difference steps. */
 int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps);
 
+/* J = sum over the top layer of (u_x^2 + u_y^2) after n_steps (Alg. 2 from
+ * the initial state with velocities v0) and dJ/d(M, eta, suction, pc0) by
+ * the reverse of every step, with the families, sub-horizons and
+ * elastic/plastic branches of the forward run held fixed.  Models 0 and 1. */
+int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps, int64_t cap,
+                            double* J, double grad[4]);
+
 /* Threads used by the OpenMP loops (results do not depend on it). */
 int ppmo_num_threads(void);
 void ppmo_set_num_threads(int t);
