@@ -168,6 +168,28 @@ int ppm_step(ppm_ctx* c, int n_steps);
  * Synchronises the stream after every step. */
 int ppm_step_timed(ppm_ctx* c, int n_steps, double ms[3]);
 
+/* Adjoint (reverse-mode gradient) of n_steps explicit steps.  The paper has
+ * no sensitivity analysis; this exposes the discrete adjoint of the step
+ * it defines (Eq. 23-26, 31-32, 40-46, 49-51, 60-64, 73-75), with the
+ * families, sub-horizons and elastic/plastic branches of the forward run
+ * held fixed.  Single-column contexts, force-state models 0 and 1.
+ *
+ * ppm_adjoint_workspace_size: device bytes for checkpoints every ckpt_every
+ * steps, one segment of step states and the adjoint arrays.
+ * ppm_adjoint_forward: from a fresh context (after ppm_init and
+ * ppm_write_state of the velocities, before any ppm_step), runs the initial
+ * pass and n_steps steps, saving checkpoints in d_ws (caller-allocated,
+ * 256-byte aligned, kept until the reverse call).  The context then holds
+ * the final state.
+ * ppm_adjoint_reverse: given dJ/du of the final displacement (3N doubles,
+ * component-major, device or host), recomputes every segment from its
+ * checkpoint and sweeps backwards; grad receives dJ/dM, dJ/deta, dJ/ds
+ * (suction, through S_r s and the initial stress) and dJ/dpc0.  The context
+ * is left at the final state again.  Synchronises the stream. */
+int ppm_adjoint_workspace_size(const ppm_ctx* c, int n_steps, int ckpt_every, size_t* bytes);
+int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, size_t bytes);
+int ppm_adjoint_reverse(ppm_ctx* c, const double* dJ_du, int src_is_device, double grad[4]);
+
 /* Copies a state field (PPM_FIELD_*) to dst (device pointer if
  * dst_is_device, else host).  bytes must be at least the field's size.
  * Synchronises the stream when dst is a host pointer. */

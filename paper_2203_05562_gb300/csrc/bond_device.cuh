@@ -1,0 +1,467 @@
+// Device routines shared by the forward bond kernel (bond.cu) and its
+// reverse (adjoint.cu): shape-tensor inverses, the visco-plastic return in
+// FP64 and FP32, the constitutive update of one bond, predicated
+// sub-horizon accumulation and deterministic block sums.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ppm_internal.cuh"
+
+namespace ppm {
+namespace {
+
+template <typename Real>
+struct alignas(4 * sizeof(Real)) R4 {
+    Real x, y, z, w;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 pieces: symmetric 3x3 inverse and the visco-plastic return
+// ---------------------------------------------------------------------------
+
+// K in order xx yy zz yz xz xy; returns false for a degenerate tensor
+// (the same rule as the oracle: det <= 1e-12 (tr K / 3)^3 or det == 0)
+__device__ __forceinline__ bool inverse_sym_fp64(const double k[6], double inv[6]) {
+    const double k00 = k[0], k11 = k[1], k22 = k[2], k12 = k[3], k02 = k[4], k01 = k[5];
+    const double c00 = k11 * k22 - k12 * k12;
+    const double c11 = k00 * k22 - k02 * k02;
+    const double c22 = k00 * k11 - k01 * k01;
+    const double c12 = k01 * k02 - k00 * k12;
+    const double c02 = k01 * k12 - k02 * k11;
+    const double c01 = k02 * k12 - k01 * k22;
+    const double det = k00 * c00 + k01 * c01 + k02 * c02;
+    const double t = (k00 + k11 + k22) * (1.0 / 3.0);
+    if (!(det > 1e-12 * t * t * t) || det == 0.0) return false;
+    const double r = 1.0 / det;
+    inv[0] = c00 * r; inv[1] = c11 * r; inv[2] = c22 * r;
+    inv[3] = c12 * r; inv[4] = c02 * r; inv[5] = c01 * r;
+    return true;
+}
+
+// Mixed path: the cancellation-prone steps -- cofactors and determinant --
+// in FP64 from the FP32 sums; the degeneracy test, the reciprocal of the
+// determinant and the final scaling in FP32 (the result is FP32 either
+// way, so a full FP64 division would change it by at most an ulp).
+__device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K22, float K12,
+                                                  float K02, float K01, float inv[6]) {
+    const double k00 = K00, k11 = K11, k22 = K22, k12 = K12, k02 = K02, k01 = K01;
+    const double c00 = k11 * k22 - k12 * k12;
+    const double c11 = k00 * k22 - k02 * k02;
+    const double c22 = k00 * k11 - k01 * k01;
+    const double c12 = k01 * k02 - k00 * k12;
+    const double c02 = k01 * k12 - k02 * k11;
+    const double c01 = k02 * k12 - k01 * k22;
+    const float det = (float)(k00 * c00 + k01 * c01 + k02 * c02);
+    const float t = (K00 + K11 + K22) * (1.0f / 3.0f);
+    if (!(det > 1e-12f * t * t * t) || det == 0.0f) return false;
+    const float r = 1.0f / det;
+    inv[0] = (float)c00 * r; inv[1] = (float)c11 * r; inv[2] = (float)c22 * r;
+    inv[3] = (float)c12 * r; inv[4] = (float)c02 * r; inv[5] = (float)c01 * r;
+    return true;
+}
+
+struct ReturnConst {
+    double K, mu, M2, lk, c, inv_scale;
+    double p_tr, q_tr, pc_n;
+};
+
+// Eq. 73-75 (Eq. 75 in log form, hardening sign of Eq. 46), stress rows
+// divided by the stress scale; J is the exact Jacobian of the scaled rows.
+template <bool WANT_J>
+__device__ __forceinline__ void return_residual(const ReturnConst& R, const double x[3],
+                                                double r[3], double J[9]) {
+    const double pb = x[0], q = x[1], pc = x[2];
+    const double f = q * q / R.M2 + pb * (pb - pc);
+    const double fp = 2.0 * pb - pc;
+    const double fq = 2.0 * q / R.M2;
+    const double fc = -pb;
+    r[0] = (pb - R.p_tr + R.K * R.c * f * fp) * R.inv_scale;
+    r[1] = (q - R.q_tr + 3.0 * R.mu * R.c * f * fq) * R.inv_scale;
+    const double ratio = pc / R.pc_n;
+    r[2] = (ratio > 0.0) ? log(ratio) + R.c * f * fp / R.lk : (double)INFINITY;
+    if (WANT_J) {
+        const double a = R.K * R.c * R.inv_scale, b = 3.0 * R.mu * R.c * R.inv_scale;
+        const double g = R.c / R.lk;
+        J[0] = R.inv_scale + a * (fp * fp + 2.0 * f);
+        J[1] = a * fq * fp;
+        J[2] = a * (fc * fp - f);
+        J[3] = b * fp * fq;
+        J[4] = R.inv_scale + b * (fq * fq + 2.0 * f / R.M2);
+        J[5] = b * fc * fq;
+        J[6] = g * (fp * fp + 2.0 * f);
+        J[7] = g * (fq * fp);
+        J[8] = 1.0 / pc + g * (fc * fp - f);
+    }
+}
+
+// Newton with backtracking from the trial state; the same stopping rules as
+// the oracle (scaled residual max-norm <= tol, or a step below 1e-14 of the
+// state; at most max_iter steps; a step is halved up to 20 times until the
+// residual is finite and its 2-norm decreases).  3x3 solve by Cramer's rule.
+__device__ __noinline__ int return_map(const ReturnConst& R, double tol, int max_iter,
+                                       double x[3]) {
+    const double scale = 1.0 / R.inv_scale;
+    x[0] = R.p_tr; x[1] = R.q_tr; x[2] = R.pc_n;
+    double r[3], J[9];
+    for (int it = 0;; it++) {
+        return_residual<true>(R, x, r, J);
+        if (fmax(fabs(r[0]), fmax(fabs(r[1]), fabs(r[2]))) <= tol) return 1;
+        if (it >= max_iter) return 0;
+        const double m0 = J[4] * J[8] - J[5] * J[7];
+        const double m1 = J[3] * J[8] - J[5] * J[6];
+        const double m2 = J[3] * J[7] - J[4] * J[6];
+        const double det = J[0] * m0 - J[1] * m1 + J[2] * m2;
+        if (det == 0.0 || !isfinite(det)) return 0;
+        const double id = 1.0 / det;
+        double dx[3];
+        dx[0] = (r[0] * m0 - J[1] * (r[1] * J[8] - J[5] * r[2]) + J[2] * (r[1] * J[7] - J[4] * r[2])) * id;
+        dx[1] = (J[0] * (r[1] * J[8] - J[5] * r[2]) - r[0] * m1 + J[2] * (J[3] * r[2] - r[1] * J[6])) * id;
+        dx[2] = (J[0] * (J[4] * r[2] - r[1] * J[7]) - J[1] * (J[3] * r[2] - r[1] * J[6]) + r[0] * m2) * id;
+        if (fabs(dx[0]) <= 1e-14 * scale && fabs(dx[1]) <= 1e-14 * scale &&
+            fabs(dx[2]) <= 1e-14 * fabs(x[2]))
+            return 1;
+        const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        double lam = 1.0, xt[3], rt[3];
+        bool accepted = false;
+        for (int ls = 0; ls < 20; ls++) {
+            for (int q = 0; q < 3; q++) xt[q] = x[q] - lam * dx[q];
+            return_residual<false>(R, xt, rt, nullptr);
+            if (isfinite(rt[0]) && isfinite(rt[1]) && isfinite(rt[2]) &&
+                sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]) < rn) {
+                accepted = true;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!accepted) return 0;
+        x[0] = xt[0]; x[1] = xt[1]; x[2] = xt[2];
+    }
+}
+
+// Mixed path: the same return solved in FP32, in increments from the trial
+// state, x = (dp, dq, dpc) with p = p_tr + dp, q = q_tr + dq, pc = pc_n + dpc,
+// so that the small corrections keep their precision; Eq. 75 in the form
+// log1p(dpc / pc_n) + c f f_p / (lambda - kappa) = 0.  Stopping rules as in
+// the FP64 solve with an FP32 tolerance.  Returns 1 if converged.
+struct ReturnConstF {
+    float K, mu, M2, lk, c, inv_scale, scale;
+    float p_tr, q_tr, pc_n, tol;
+    int max_iter;
+};
+
+template <bool WANT_J>
+__device__ __forceinline__ void return_residual_f(const ReturnConstF& R, const float x[3],
+                                                  float r[3], float J[9]) {
+    const float pb = R.p_tr + x[0], q = R.q_tr + x[1], pc = R.pc_n + x[2];
+    const float f = q * q / R.M2 + pb * (pb - pc);
+    const float fp = 2.0f * pb - pc;
+    const float fq = 2.0f * q / R.M2;
+    const float fc = -pb;
+    r[0] = (x[0] + R.K * R.c * f * fp) * R.inv_scale;
+    r[1] = (x[1] + 3.0f * R.mu * R.c * f * fq) * R.inv_scale;
+    const float rel = x[2] / R.pc_n;
+    r[2] = (rel > -1.0f) ? log1pf(rel) + R.c * f * fp / R.lk : INFINITY;
+    if (WANT_J) {
+        const float a = R.K * R.c * R.inv_scale, b = 3.0f * R.mu * R.c * R.inv_scale;
+        const float g = R.c / R.lk;
+        J[0] = R.inv_scale + a * (fp * fp + 2.0f * f);
+        J[1] = a * fq * fp;
+        J[2] = a * (fc * fp - f);
+        J[3] = b * fp * fq;
+        J[4] = R.inv_scale + b * (fq * fq + 2.0f * f / R.M2);
+        J[5] = b * fc * fq;
+        J[6] = g * (fp * fp + 2.0f * f);
+        J[7] = g * (fq * fp);
+        J[8] = 1.0f / pc + g * (fc * fp - f);
+    }
+}
+
+__device__ __noinline__ int return_map_f32(const ReturnConstF& R, float x[3]) {
+    x[0] = 0.0f; x[1] = 0.0f; x[2] = 0.0f;
+    float r[3], J[9];
+    for (int it = 0;; it++) {
+        return_residual_f<true>(R, x, r, J);
+        if (fmaxf(fabsf(r[0]), fmaxf(fabsf(r[1]), fabsf(r[2]))) <= R.tol) return 1;
+        if (it >= R.max_iter) return 0;
+        const float m0 = J[4] * J[8] - J[5] * J[7];
+        const float m1 = J[3] * J[8] - J[5] * J[6];
+        const float m2 = J[3] * J[7] - J[4] * J[6];
+        const float det = J[0] * m0 - J[1] * m1 + J[2] * m2;
+        if (det == 0.0f || !isfinite(det)) return 0;
+        const float id = 1.0f / det;
+        float dx[3];
+        dx[0] = (r[0] * m0 - J[1] * (r[1] * J[8] - J[5] * r[2]) + J[2] * (r[1] * J[7] - J[4] * r[2])) * id;
+        dx[1] = (J[0] * (r[1] * J[8] - J[5] * r[2]) - r[0] * m1 + J[2] * (J[3] * r[2] - r[1] * J[6])) * id;
+        dx[2] = (J[0] * (J[4] * r[2] - r[1] * J[7]) - J[1] * (J[3] * r[2] - r[1] * J[6]) + r[0] * m2) * id;
+        const float small = 2e-7f * R.scale;
+        if (fabsf(dx[0]) <= small && fabsf(dx[1]) <= small && fabsf(dx[2]) <= small) return 1;
+        const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        float lam = 1.0f, xt[3], rt[3];
+        bool accepted = false;
+        for (int ls = 0; ls < 20; ls++) {
+            for (int q = 0; q < 3; q++) xt[q] = x[q] - lam * dx[q];
+            return_residual_f<false>(R, xt, rt, nullptr);
+            if (isfinite(rt[0]) && isfinite(rt[1]) && isfinite(rt[2]) &&
+                sqrtf(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]) < rn) {
+                accepted = true;
+                break;
+            }
+            lam *= 0.5f;
+        }
+        if (!accepted) return 0;
+        x[0] = xt[0]; x[1] = xt[1]; x[2] = xt[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// constitutive update of one bond (Sec. 2.3; Sec. 3.2.1)
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct BondStress {
+    Real sig[6];
+    Real pc, des;
+    int plastic, nonconv, ret64;
+};
+
+// what the reverse of one update needs from its forward
+template <typename Real>
+struct MatTrace {
+    Real Q[9];          // rotation
+    Real a[3], kap;     // axial vector of dt/2 W and 2 / (1 + a.a)
+    Real st[6];         // trial stress
+    Real p_tr, q_tr;
+    int plastic, floored;
+    double x[3];        // return solution (p, q, pc) before the floor
+    double c;           // dt / eta_eff
+};
+
+template <typename Real>
+__device__ __forceinline__ void material_update(const Real L[9], const Real sn[6], Real pc_n,
+                                                const StepConst& k, double M, float Mf,
+                                                BondStress<Real>& o,
+                                                MatTrace<Real>* trace = nullptr) {
+    constexpr bool F64 = sizeof(Real) == 8;
+    const Real dt = F64 ? (Real)k.dt : (Real)k.dtf;
+    const Real Kb = F64 ? (Real)k.K : (Real)k.Kf;
+    const Real mu = F64 ? (Real)k.mu : (Real)k.muf;
+    // rate of deformation and spin (Eq. 26)
+    const Real D00 = L[0], D11 = L[4], D22 = L[8];
+    const Real D12 = (Real)0.5 * (L[5] + L[7]);
+    const Real D02 = (Real)0.5 * (L[2] + L[6]);
+    const Real D01 = (Real)0.5 * (L[1] + L[3]);
+    // Hughes-Winget: Q = (I - A)^-1 (I + A) with A = dt/2 W, in closed
+    // (Cayley) form Q = I + 2/(1 + a.a) (A + a a^T - (a.a) I), a = axial(A)
+    const Real h = (Real)0.5 * dt;
+    const Real a1 = h * (Real)0.5 * (L[7] - L[5]);
+    const Real a2 = h * (Real)0.5 * (L[2] - L[6]);
+    const Real a3 = h * (Real)0.5 * (L[3] - L[1]);
+    const Real aa = a1 * a1 + a2 * a2 + a3 * a3;
+    const Real kap = (Real)2 / ((Real)1 + aa);
+    Real Q[9];
+    Q[0] = (Real)1 + kap * (a1 * a1 - aa); Q[1] = kap * (-a3 + a1 * a2); Q[2] = kap * (a2 + a1 * a3);
+    Q[3] = kap * (a3 + a2 * a1); Q[4] = (Real)1 + kap * (a2 * a2 - aa); Q[5] = kap * (-a1 + a2 * a3);
+    Q[6] = kap * (-a2 + a3 * a1); Q[7] = kap * (a1 + a3 * a2); Q[8] = (Real)1 + kap * (a3 * a3 - aa);
+    const Real S[9] = {sn[0], sn[5], sn[4], sn[5], sn[1], sn[3], sn[4], sn[3], sn[2]};
+    Real P[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            P[r * 3 + c] = Q[r * 3 + 0] * S[0 * 3 + c] + Q[r * 3 + 1] * S[1 * 3 + c] + Q[r * 3 + 2] * S[2 * 3 + c];
+    auto rot = [&](int r, int c) {
+        return P[r * 3 + 0] * Q[c * 3 + 0] + P[r * 3 + 1] * Q[c * 3 + 1] + P[r * 3 + 2] * Q[c * 3 + 2];
+    };
+    // strain increment (Eq. 59) and linear trial stress (Eq. 41)
+    const Real e00 = dt * D00, e11 = dt * D11, e22 = dt * D22;
+    const Real e12 = dt * D12, e02 = dt * D02, e01 = dt * D01;
+    const Real tr = e00 + e11 + e22, tr3 = tr * (Real)(1.0 / 3.0);
+    const Real lam = Kb * tr;
+    Real st[6];
+    st[0] = rot(0, 0) + lam + (Real)2 * mu * (e00 - tr3);
+    st[1] = rot(1, 1) + lam + (Real)2 * mu * (e11 - tr3);
+    st[2] = rot(2, 2) + lam + (Real)2 * mu * (e22 - tr3);
+    st[3] = (Real)0.5 * (rot(1, 2) + rot(2, 1)) + (Real)2 * mu * e12;
+    st[4] = (Real)0.5 * (rot(0, 2) + rot(2, 0)) + (Real)2 * mu * e02;
+    st[5] = (Real)0.5 * (rot(0, 1) + rot(1, 0)) + (Real)2 * mu * e01;
+    const Real d0 = e00 - tr3, d1 = e11 - tr3, d2 = e22 - tr3;
+    o.des = sqrt((Real)(2.0 / 3.0) *
+                 (d0 * d0 + d1 * d1 + d2 * d2 + (Real)2 * (e12 * e12 + e02 * e02 + e01 * e01)));
+    // invariants and yield function (Eq. 40)
+    const Real p_tr = (st[0] + st[1] + st[2]) * (Real)(1.0 / 3.0);
+    const Real s0 = st[0] - p_tr, s1 = st[1] - p_tr, s2 = st[2] - p_tr;
+    const Real q_tr = sqrt((Real)1.5 * (s0 * s0 + s1 * s1 + s2 * s2 +
+                                        (Real)2 * (st[3] * st[3] + st[4] * st[4] + st[5] * st[5])));
+    const Real Mr = F64 ? (Real)M : (Real)Mf;
+    const Real f_tr = q_tr * q_tr / (Mr * Mr) + p_tr * (p_tr - pc_n);
+    o.plastic = 0;
+    o.nonconv = 0;
+    o.ret64 = 0;
+    if (trace) {
+#pragma unroll
+        for (int e = 0; e < 9; e++) trace->Q[e] = Q[e];
+        trace->a[0] = a1; trace->a[1] = a2; trace->a[2] = a3; trace->kap = kap;
+#pragma unroll
+        for (int e = 0; e < 6; e++) trace->st[e] = st[e];
+        trace->p_tr = p_tr; trace->q_tr = q_tr;
+        trace->plastic = 0; trace->floored = 0;
+    }
+    if (!(f_tr > (Real)0)) {
+#pragma unroll
+        for (int c = 0; c < 6; c++) o.sig[c] = st[c];
+        o.pc = pc_n;
+        return;
+    }
+    o.plastic = 1;
+    o.ret64 = 0;
+    Real p_new = p_tr, q_new = q_tr, pc_new = pc_n;
+    bool need64 = F64;
+    if constexpr (!F64) {
+        // FP32 return unless the state is near the critical-state apex
+        // (mean stress within 5% of the preconsolidation pressure from
+        // zero, or tensile) or the preconsolidation pressure has nearly
+        // vanished; any FP32 solve that fails is redone in FP64
+        need64 = (p_tr > 0.05f * pc_n) || (pc_n > -100.0f);
+        if (!need64) {
+            ReturnConstF R;
+            R.K = k.Kf; R.mu = k.muf; R.M2 = Mf * Mf; R.lk = (float)k.lk;
+            R.p_tr = p_tr; R.q_tr = q_tr; R.pc_n = pc_n;
+            const float eta_eff = (k.visc_form == 0) ? k.etaf * pc_n * pc_n : k.etaf;
+            R.c = k.dtf / eta_eff;
+            float scale = fmaxf(fmaxf(fabsf(pc_n), fabsf(p_tr)), fmaxf(q_tr, 1.0f));
+            R.scale = scale;
+            R.inv_scale = 1.0f / scale;
+            R.tol = fmaxf((float)k.tol, 2e-6f);
+            R.max_iter = k.max_iter;
+            float x[3];
+            if (return_map_f32(R, x)) {
+                p_new = p_tr + x[0];
+                q_new = q_tr + x[1];
+                pc_new = pc_n + x[2];
+                o.nonconv = 0;
+            } else {
+                need64 = true;
+            }
+        }
+    }
+    if (need64) {
+        // visco-plastic return in FP64
+        ReturnConst R;
+        R.K = k.K; R.mu = k.mu; R.M2 = M * M; R.lk = k.lk;
+        R.p_tr = (double)p_tr; R.q_tr = (double)q_tr; R.pc_n = (double)pc_n;
+        const double eta_eff = (k.visc_form == 0) ? k.eta * R.pc_n * R.pc_n : k.eta;
+        R.c = k.dt / eta_eff;
+        double scale = fabs(R.pc_n);
+        if (fabs(R.p_tr) > scale) scale = fabs(R.p_tr);
+        if (R.q_tr > scale) scale = R.q_tr;
+        if (scale < 1.0) scale = 1.0;
+        R.inv_scale = 1.0 / scale;
+        double x[3];
+        const int ok = return_map(R, k.tol, k.max_iter, x);
+        o.nonconv = !ok;
+        o.ret64 = 1;
+        p_new = (Real)x[0];
+        q_new = (Real)x[1];
+        pc_new = (Real)x[2];
+    }
+    const Real ratio = (q_tr > (Real)0) ? q_new / q_tr : (Real)0;
+    const Real pn = p_new;
+    o.sig[0] = pn + ratio * s0;
+    o.sig[1] = pn + ratio * s1;
+    o.sig[2] = pn + ratio * s2;
+    o.sig[3] = ratio * st[3];
+    o.sig[4] = ratio * st[4];
+    o.sig[5] = ratio * st[5];
+    if (trace) {
+        trace->plastic = 1;
+        trace->x[0] = (double)p_new; trace->x[1] = (double)q_new; trace->x[2] = (double)pc_new;
+        trace->floored = pc_new > (Real)-1;
+        const double pcn = (double)pc_n;
+        trace->c = k.dt / ((k.visc_form == 0) ? k.eta * pcn * pcn : k.eta);
+    }
+    if (pc_new > (Real)-1) pc_new = (Real)-1;   // floor at the apex
+    o.pc = pc_new;
+}
+
+// Predicated sub-horizon accumulation: when tst <= 0 (member), add the
+// outer products zeta~ zeta~^T (6), Ydot zeta~^T (9) and 1 to the count; the
+// predicate guards each FMA, so non-members cost no extra multiplies and the
+// warp never branches.
+__device__ __forceinline__ void masked_accumulate(float tst, float zx, float zy, float zz,
+                                                  float yx, float yy, float yz, float (&K)[6],
+                                                  float (&A)[9], float& cnt) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.f32 p, %16, 0f00000000;\n\t"
+        "@p fma.rn.f32 %0, %17, %17, %0;\n\t"
+        "@p fma.rn.f32 %1, %18, %18, %1;\n\t"
+        "@p fma.rn.f32 %2, %19, %19, %2;\n\t"
+        "@p fma.rn.f32 %3, %18, %19, %3;\n\t"
+        "@p fma.rn.f32 %4, %17, %19, %4;\n\t"
+        "@p fma.rn.f32 %5, %17, %18, %5;\n\t"
+        "@p fma.rn.f32 %6, %20, %17, %6;\n\t"
+        "@p fma.rn.f32 %7, %20, %18, %7;\n\t"
+        "@p fma.rn.f32 %8, %20, %19, %8;\n\t"
+        "@p fma.rn.f32 %9, %21, %17, %9;\n\t"
+        "@p fma.rn.f32 %10, %21, %18, %10;\n\t"
+        "@p fma.rn.f32 %11, %21, %19, %11;\n\t"
+        "@p fma.rn.f32 %12, %22, %17, %12;\n\t"
+        "@p fma.rn.f32 %13, %22, %18, %13;\n\t"
+        "@p fma.rn.f32 %14, %22, %19, %14;\n\t"
+        "@p add.f32 %15, %15, 0f3F800000;\n\t"
+        "}"
+        : "+f"(K[0]), "+f"(K[1]), "+f"(K[2]), "+f"(K[3]), "+f"(K[4]), "+f"(K[5]),
+          "+f"(A[0]), "+f"(A[1]), "+f"(A[2]), "+f"(A[3]), "+f"(A[4]), "+f"(A[5]),
+          "+f"(A[6]), "+f"(A[7]), "+f"(A[8]), "+f"(cnt)
+        : "f"(tst), "f"(zx), "f"(zy), "f"(zz), "f"(yx), "f"(yy), "f"(yz));
+}
+
+// Predicated sum of a sender's 3x3 matrix (M) into N when tst <= 0.
+__device__ __forceinline__ void masked_add9(float tst, const float4& m0, const float4& m1,
+                                            float m8, float (&N)[9]) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.f32 p, %9, 0f00000000;\n\t"
+        "@p add.f32 %0, %0, %10;\n\t"
+        "@p add.f32 %1, %1, %11;\n\t"
+        "@p add.f32 %2, %2, %12;\n\t"
+        "@p add.f32 %3, %3, %13;\n\t"
+        "@p add.f32 %4, %4, %14;\n\t"
+        "@p add.f32 %5, %5, %15;\n\t"
+        "@p add.f32 %6, %6, %16;\n\t"
+        "@p add.f32 %7, %7, %17;\n\t"
+        "@p add.f32 %8, %8, %18;\n\t"
+        "}"
+        : "+f"(N[0]), "+f"(N[1]), "+f"(N[2]), "+f"(N[3]), "+f"(N[4]), "+f"(N[5]), "+f"(N[6]),
+          "+f"(N[7]), "+f"(N[8])
+        : "f"(tst), "f"(m0.x), "f"(m0.y), "f"(m0.z), "f"(m0.w), "f"(m1.x), "f"(m1.y), "f"(m1.z),
+          "f"(m1.w), "f"(m8));
+}
+
+// deterministic block sum: butterfly within warps, then warps in order
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T (*sm)[NV]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < NV; e++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], off);
+    if (lane == 0)
+#pragma unroll
+        for (int e = 0; e < NV; e++) sm[w][e] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < NV; e++) {
+        T t = sm[0][e];
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) t += sm[q][e];
+        v[e] = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+}  // namespace
+}  // namespace ppm

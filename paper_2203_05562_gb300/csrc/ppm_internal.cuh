@@ -94,6 +94,18 @@ struct DevState {
     int ncell_cap;
 };
 
+// adjoint arrays (adjoint.cu); Real as the forward path
+template <typename Real>
+struct AdjState {
+    Real *ub, *vb, *ab;        // 3N: adjoint of u, v, a (after the step on entry, before on exit)
+    Real *sb, *pcb;            // 6N, N: adjoint of the point stress and pc
+    Real *sbn, *pcbn;          // 6N, N: their new values (before the step)
+    Real *fb, *u1b, *vhb;      // 3N: force, positions after the predictor, half-step velocity
+    Real *zsum, *ysum;         // 3N: row sums of the position / velocity adjoints
+    Real *Zrev, *Yrev;         // 3 x cap: neighbour adjoints at their reverse slots
+    double* thpart;            // 3N: per-point partial adjoints of (M, eta, S_r s)
+};
+
 // ---- launchers (family.cu) ----
 // *nlaunch (if not null) is incremented by the number of kernels launched
 template <typename Real>
@@ -119,5 +131,15 @@ cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt
                           int gather_blocks, cudaStream_t st);
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
                                  const int32_t* row_ptr, int npoints, cudaStream_t st);
+
+// ---- launchers (adjoint.cu) ----
+// one reverse step from the restored start state (predictor already
+// recomputed): acc[0..2] += adjoints of (M, eta, S_r s); with initial, the
+// reverse of the initial pass and acc[3] = sum tr(sigma-bar), acc[4] = sum pc-bar
+template <typename Real>
+cudaError_t launch_adjoint_step(const DevState<Real>& s, const AdjState<Real>& a, const StepConst& k,
+                                double* acc, int initial, cudaStream_t st);
+template <typename Real>
+cudaError_t launch_convert_adjoint(const double* src, Real* dst, size_t count, cudaStream_t st);
 
 }  // namespace ppm

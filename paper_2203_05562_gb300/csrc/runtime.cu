@@ -37,6 +37,11 @@ struct ppm_ctx {
     long long launches;          // kernels issued (graph replays count their kernels)
     long long launches_plain, launches_rebuild, launches_segment;   // kernels per graph
     int segment_len;             // steps in g_segment (the rebuild period)
+    // adjoint bookkeeping (ppm_adjoint_forward / ppm_adjoint_reverse)
+    bool adj_ready;
+    int adj_steps, adj_every, adj_nck, adj_nver;
+    char* adj_ws;
+    size_t adj_bytes;
 };
 
 namespace {
@@ -402,6 +407,216 @@ int read_nbonds(ppm_ctx* c, int64_t* nb) {
 
 }  // namespace
 
+namespace {
+
+// ---- adjoint workspace: checkpoints, one segment of step states, family
+// versions, the final forward state and the adjoint arrays ----
+struct AdjLayout {
+    size_t state_bytes, fam_bytes, total;
+    size_t off_ck, off_seg, off_ver, off_final, off_ctr, off_adj, off_acc;
+    int nck, nver, every;
+};
+
+template <typename Real>
+size_t state_bytes_of(int64_t N, bool mixed) {
+    const size_t n = (size_t)N;
+    return align_up(sizeof(Real) * (3 * 3 * n + 6 * n + n) + (mixed ? sizeof(float) * 3 * n : 0), 256);
+}
+
+size_t adj_region_bytes(bool f64, size_t n, size_t cap);
+
+AdjLayout adj_layout(const ppm_ctx* c, int n_steps, int every) {
+    AdjLayout L;
+    const bool f64 = c->p.precision == PPM_FP64;
+    const bool mixed = !f64;
+    const size_t n = (size_t)c->N, cap = (size_t)c->cap;
+    L.every = every;
+    L.state_bytes = f64 ? state_bytes_of<double>(c->N, false) : state_bytes_of<float>(c->N, true);
+    L.fam_bytes = align_up(sizeof(int32_t) * (n + 1 + 2 * cap), 256);
+    L.nck = (n_steps + every - 1) / every + 1;
+    const int rb = c->p.rebuild_every;
+    L.nver = rb > 0 ? (every < (every + rb - 1) / rb + 1 ? every : (every + rb - 1) / rb + 1) + 1 : 1;
+    size_t off = 0;
+    L.off_ck = off; off += (size_t)L.nck * (L.state_bytes + L.fam_bytes);
+    L.off_seg = off; off += (size_t)every * L.state_bytes;
+    L.off_ver = off; off += (size_t)L.nver * L.fam_bytes;
+    L.off_final = off; off += L.state_bytes + L.fam_bytes;
+    L.off_ctr = off; off += align_up(sizeof(DevCounters), 256);
+    L.off_adj = off;
+    off += adj_region_bytes(f64, n, cap);
+    L.off_acc = off; off += 256;
+    L.total = off;
+    (void)mixed;
+    return L;
+}
+
+template <typename Real>
+int copy_state(ppm_ctx* c, const DevState<Real>& s, char* buf, bool save, cudaStream_t st) {
+    const size_t n = (size_t)c->N;
+    const size_t R = sizeof(Real);
+    struct Part { void* p; size_t bytes; } parts[7] = {
+        {s.u, R * 3 * n}, {s.v, R * 3 * n}, {s.a, R * 3 * n}, {s.sig, R * 6 * n}, {s.pc, R * n},
+        {s.ulo, s.ulo ? sizeof(float) * 3 * n : 0}, {nullptr, 0}};
+    size_t off = 0;
+    for (int q = 0; parts[q].p; q++) {
+        if (!parts[q].bytes) continue;
+        if (save) CU(cudaMemcpyAsync(buf + off, parts[q].p, parts[q].bytes, cudaMemcpyDeviceToDevice, st));
+        else CU(cudaMemcpyAsync(parts[q].p, buf + off, parts[q].bytes, cudaMemcpyDeviceToDevice, st));
+        off += parts[q].bytes;
+    }
+    return PPM_OK;
+}
+
+template <typename Real>
+int copy_family(ppm_ctx* c, const DevState<Real>& s, char* buf, bool save, cudaStream_t st) {
+    const size_t n = (size_t)c->N, cap = (size_t)c->cap;
+    void* parts[3] = {s.row_ptr, s.col, s.rev};
+    const size_t bytes[3] = {sizeof(int32_t) * (n + 1), sizeof(int32_t) * cap, sizeof(int32_t) * cap};
+    size_t off = 0;
+    for (int q = 0; q < 3; q++) {
+        if (save) CU(cudaMemcpyAsync(buf + off, parts[q], bytes[q], cudaMemcpyDeviceToDevice, st));
+        else CU(cudaMemcpyAsync(parts[q], buf + off, bytes[q], cudaMemcpyDeviceToDevice, st));
+        off += bytes[q];
+    }
+    return PPM_OK;
+}
+
+template <typename Real>
+void adj_take(Layout& Q, char* base, size_t n, size_t cap, AdjState<Real>& a) {
+    a.ub = Q.take<Real>(base, 3 * n); a.vb = Q.take<Real>(base, 3 * n); a.ab = Q.take<Real>(base, 3 * n);
+    a.fb = Q.take<Real>(base, 3 * n); a.u1b = Q.take<Real>(base, 3 * n); a.vhb = Q.take<Real>(base, 3 * n);
+    a.zsum = Q.take<Real>(base, 3 * n); a.ysum = Q.take<Real>(base, 3 * n);
+    a.sb = Q.take<Real>(base, 6 * n); a.sbn = Q.take<Real>(base, 6 * n);
+    a.pcb = Q.take<Real>(base, n); a.pcbn = Q.take<Real>(base, n);
+    a.Zrev = Q.take<Real>(base, 3 * cap); a.Yrev = Q.take<Real>(base, 3 * cap);
+    a.thpart = Q.take<double>(base, 3 * n);
+}
+
+size_t adj_region_bytes(bool f64, size_t n, size_t cap) {
+    Layout Q;
+    if (f64) {
+        AdjState<double> a;
+        adj_take<double>(Q, nullptr, n, cap, a);
+    } else {
+        AdjState<float> a;
+        adj_take<float>(Q, nullptr, n, cap, a);
+    }
+    return Q.total;
+}
+
+template <typename Real>
+AdjState<Real> adj_arrays(ppm_ctx* c, const AdjLayout& L) {
+    Layout Q;
+    AdjState<Real> a;
+    adj_take<Real>(Q, c->adj_ws + L.off_adj, (size_t)c->N, (size_t)c->cap, a);
+    return a;
+}
+
+template <typename Real>
+int adjoint_forward(ppm_ctx* c, const DevState<Real>& s, int n_steps, int every) {
+    const AdjLayout L = adj_layout(c, n_steps, every);
+    cudaStream_t st = c->stream;
+    int rc = issue_initial<Real>(c, s);
+    if (rc) return rc;
+    c->started = true;
+    auto ck = [&](int q) { return c->adj_ws + L.off_ck + (size_t)q * (L.state_bytes + L.fam_bytes); };
+    for (int t = 0; t < n_steps; t++) {
+        if (t % every == 0) {
+            char* b = ck(t / every);
+            if ((rc = copy_state<Real>(c, s, b, true, st))) return rc;
+            if ((rc = copy_family<Real>(c, s, b + L.state_bytes, true, st))) return rc;
+        }
+        if ((rc = issue_step<Real>(c, s, rebuild_due(c), st, nullptr, &c->launches))) return rc;
+        c->step++;
+    }
+    char* fin = c->adj_ws + L.off_final;
+    if ((rc = copy_state<Real>(c, s, fin, true, st))) return rc;
+    if ((rc = copy_family<Real>(c, s, fin + L.state_bytes, true, st))) return rc;
+    CU(cudaMemcpyAsync(c->adj_ws + L.off_ctr, s.ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, st));
+    CU(cudaGetLastError());
+    return PPM_OK;
+}
+
+double dsrs_ds(const ppm_params* p) {
+    const double sct = p->suction, al = p->vg_alpha, nn = p->vg_n, mm = 1.0 - 1.0 / nn;
+    if (sct <= 0.0) return 1.0;
+    const double base = 1.0 + pow(al * sct, nn);
+    const double Sr = pow(base, -mm);
+    const double dSr = -mm * pow(base, -mm - 1.0) * nn * pow(al * sct, nn - 1.0) * al;
+    return Sr + sct * dSr;
+}
+
+template <typename Real>
+int adjoint_reverse(ppm_ctx* c, const DevState<Real>& s, const double* d_dJdu, double grad[4]) {
+    const int n_steps = c->adj_steps, every = c->adj_every;
+    const AdjLayout L = adj_layout(c, n_steps, every);
+    cudaStream_t st = c->stream;
+    const size_t n = (size_t)c->N;
+    AdjState<Real> a = adj_arrays<Real>(c, L);
+    double* acc = reinterpret_cast<double*>(c->adj_ws + L.off_acc);
+    CU(cudaMemsetAsync(c->adj_ws + L.off_adj, 0, L.off_acc - L.off_adj, st));
+    CU(cudaMemsetAsync(acc, 0, 8 * sizeof(double), st));
+    CU(launch_convert_adjoint<Real>(d_dJdu, a.ub, 3 * n, st));   // before the segment buffer is reused
+    auto ck = [&](int q) { return c->adj_ws + L.off_ck + (size_t)q * (L.state_bytes + L.fam_bytes); };
+    std::vector<int> ver_of(every);
+    int rc;
+    for (int seg = (n_steps - 1) / every; seg >= 0 && n_steps > 0; seg--) {
+        const int t0 = seg * every, t1 = (t0 + every < n_steps) ? t0 + every : n_steps;
+        char* b = ck(seg);
+        if ((rc = copy_state<Real>(c, s, b, false, st))) return rc;
+        if ((rc = copy_family<Real>(c, s, b + L.state_bytes, false, st))) return rc;
+        if ((rc = copy_family<Real>(c, s, c->adj_ws + L.off_ver, true, st))) return rc;
+        int ver = 0;
+        c->step = t0;
+        for (int t = t0; t < t1; t++) {
+            if ((rc = copy_state<Real>(c, s, c->adj_ws + L.off_seg + (size_t)(t - t0) * L.state_bytes, true, st)))
+                return rc;
+            const bool rb = rebuild_due(c);
+            if ((rc = issue_step<Real>(c, s, rb, st, nullptr, &c->launches))) return rc;
+            if (rb) {
+                ver++;
+                if (ver >= L.nver) return PPM_ESTATE;
+                if ((rc = copy_family<Real>(c, s, c->adj_ws + L.off_ver + (size_t)ver * L.fam_bytes, true, st)))
+                    return rc;
+            }
+            ver_of[t - t0] = ver;
+            c->step++;
+        }
+        for (int t = t1 - 1; t >= t0; t--) {
+            if ((rc = copy_state<Real>(c, s, c->adj_ws + L.off_seg + (size_t)(t - t0) * L.state_bytes, false, st)))
+                return rc;
+            if ((rc = copy_family<Real>(c, s, c->adj_ws + L.off_ver + (size_t)ver_of[t - t0] * L.fam_bytes, false, st)))
+                return rc;
+            CU(launch_predictor<Real>(s, c->k, st));
+            CU(launch_adjoint_step<Real>(s, a, c->k, acc, 0, st));
+            c->launches += 5;
+        }
+    }
+    // reverse of the initial pass, from checkpoint 0 (initial stress and family)
+    if ((rc = copy_state<Real>(c, s, ck(0), false, st))) return rc;
+    if ((rc = copy_family<Real>(c, s, ck(0) + L.state_bytes, false, st))) return rc;
+    CU(launch_adjoint_step<Real>(s, a, c->k, acc, 1, st));
+    c->launches += 3;
+    double h[5];
+    CU(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    // back to the state at the end of the forward run
+    char* fin = c->adj_ws + L.off_final;
+    if ((rc = copy_state<Real>(c, s, fin, false, st))) return rc;
+    if ((rc = copy_family<Real>(c, s, fin + L.state_bytes, false, st))) return rc;
+    CU(cudaMemcpyAsync(s.ctr, c->adj_ws + L.off_ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    c->step = n_steps;
+    // initial state: sigma0 = geostatic - S_r s 1 (K0 start), pc = -pc0
+    const double srsb = h[2] - (c->p.init_stress == 0 ? h[3] : 0.0);
+    grad[0] = h[0];
+    grad[1] = h[1];
+    grad[2] = srsb * dsrs_ds(&c->p);
+    grad[3] = -h[4];
+    return PPM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int ppm_workspace_size(const ppm_params* p, int n_columns, const ppm_column* cols, size_t* bytes) {
@@ -522,6 +737,7 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     c->g_rebuild = nullptr;
     c->g_segment = nullptr;
     c->segment_len = 0;
+    c->adj_ready = false;
     c->launches = 1;   // initial-state kernel
     *out = c;
     return PPM_OK;
@@ -633,6 +849,43 @@ const char* ppm_error_string(int code) {
         case PPM_ESTATE: return "call not valid in the context's current state";
         default: return "unknown error";
     }
+}
+
+int ppm_adjoint_workspace_size(const ppm_ctx* c, int n_steps, int ckpt_every, size_t* bytes) {
+    if (!c || !bytes || n_steps < 0 || ckpt_every < 1) return PPM_EINVAL;
+    *bytes = adj_layout(c, n_steps, ckpt_every).total;
+    return PPM_OK;
+}
+
+int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, size_t bytes) {
+    if (!c || n_steps < 0 || ckpt_every < 1 || !d_ws || ((uintptr_t)d_ws & 255u)) return PPM_EINVAL;
+    if (c->started || c->ncols != 1 || c->p.model == 2) return PPM_ESTATE;
+    if (bytes < adj_layout(c, n_steps, ckpt_every).total) return PPM_ENOSPACE;
+    c->adj_ws = (char*)d_ws;
+    c->adj_bytes = bytes;
+    c->adj_steps = n_steps;
+    c->adj_every = ckpt_every;
+    int rc = c->p.precision == PPM_FP64 ? adjoint_forward<double>(c, c->sd, n_steps, ckpt_every)
+                                        : adjoint_forward<float>(c, c->sf, n_steps, ckpt_every);
+    c->adj_ready = rc == PPM_OK;
+    return rc;
+}
+
+int ppm_adjoint_reverse(ppm_ctx* c, const double* dJ_du, int src_is_device, double grad[4]) {
+    if (!c || !dJ_du || !grad) return PPM_EINVAL;
+    if (!c->adj_ready) return PPM_ESTATE;
+    const AdjLayout L = adj_layout(c, c->adj_steps, c->adj_every);
+    const double* d_src = dJ_du;
+    if (!src_is_device) {
+        // stage the host values in the segment buffer (at least 3N doubles)
+        double* stage = reinterpret_cast<double*>(c->adj_ws + L.off_seg);
+        CU(cudaMemcpyAsync(stage, dJ_du, sizeof(double) * 3 * (size_t)c->N, cudaMemcpyHostToDevice,
+                           c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        d_src = stage;
+    }
+    return c->p.precision == PPM_FP64 ? adjoint_reverse<double>(c, c->sd, d_src, grad)
+                                      : adjoint_reverse<float>(c, c->sf, d_src, grad);
 }
 
 size_t ppm_struct_size(int which) {

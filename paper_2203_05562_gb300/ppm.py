@@ -88,6 +88,9 @@ def library(build_if_missing: bool = True):
             L.ppm_error_string.argtypes = [C.c_int]
             L.ppm_family_noalloc.argtypes = [C.c_int64, vp, C.c_double, C.c_int, vp, vp, vp,
                                              C.c_int64, vp, C.POINTER(C.c_int64)]
+            L.ppm_adjoint_workspace_size.argtypes = [vp, C.c_int, C.c_int, szp]
+            L.ppm_adjoint_forward.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t]
+            L.ppm_adjoint_reverse.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double)]
             L.ppm_struct_size.restype = C.c_size_t
             L.ppm_struct_size.argtypes = [C.c_int]
             L.ppm_destroy.restype = None
@@ -223,6 +226,33 @@ class Simulation:
         ms = (C.c_double * 3)(0.0, 0.0, 0.0)
         _check(library().ppm_step_timed(self._ctx, int(n_steps), ms), "ppm_step_timed")
         return [ms[0], ms[1], ms[2]]
+
+    # -- adjoint -----------------------------------------------------------
+    def adjoint_forward(self, n_steps: int, ckpt_every: int):
+        """Run n_steps from the initial state keeping checkpoints for the
+        reverse sweep (workspace allocated here with torch)."""
+        nbytes = C.c_size_t(0)
+        _check(library().ppm_adjoint_workspace_size(self._ctx, int(n_steps), int(ckpt_every),
+                                                    C.byref(nbytes)), "ppm_adjoint_workspace_size")
+        self._adj_ws = self._torch.empty(int(nbytes.value) + 256, dtype=self._torch.uint8,
+                                         device=self.device)
+        base = (self._adj_ws.data_ptr() + 255) // 256 * 256
+        _check(library().ppm_adjoint_forward(self._ctx, int(n_steps), int(ckpt_every),
+                                             C.c_void_p(base), nbytes.value), "ppm_adjoint_forward")
+
+    def adjoint_reverse(self, dJ_du):
+        """dJ/d(M, eta, suction, pc0) for dJ/du of the final displacement
+        (a (3, n) float64 CUDA tensor or numpy array)."""
+        grad = (C.c_double * 4)()
+        if hasattr(dJ_du, "data_ptr"):
+            t = dJ_du.to(device=self.device, dtype=self._torch.float64).contiguous()
+            _check(library().ppm_adjoint_reverse(self._ctx, C.c_void_p(t.data_ptr()), 1, grad),
+                   "ppm_adjoint_reverse")
+        else:
+            a = np.ascontiguousarray(np.asarray(dJ_du, np.float64).reshape(3 * self.n))
+            _check(library().ppm_adjoint_reverse(self._ctx, C.c_void_p(a.ctypes.data), 0, grad),
+                   "ppm_adjoint_reverse")
+        return np.array([grad[q] for q in range(4)])
 
     def num_bonds(self) -> int:
         nb = C.c_int64(0)
