@@ -195,6 +195,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=50)
     ap.add_argument("--tile", type=int, default=128, help="bond-kernel tile for --profile-only")
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--profile-only", action="store_true",
@@ -301,6 +304,52 @@ def main():
                "graph": "one CUDA graph per 50-step rebuild period"}
         del esim0
 
+    # ---- large column (64x64x256, 1,048,576 points), mixed ----
+    large = None
+    if not args.no_large:
+        lcfg = pi.config("large_64x64x256_mixed")
+        lsim = Simulation(lcfg, precision="mixed", bond_tile=0)
+        lsim.write("v", pi.initial_velocity(lcfg))
+        lsim.step(args.warmup)
+        torch.cuda.synchronize()
+        l0 = lsim.status()
+        la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        la.record(lsim.stream)
+        lsim.step(args.large_steps)
+        lb.record(lsim.stream)
+        torch.cuda.synchronize()
+        l1 = lsim.status()
+        lms = la.elapsed_time(lb)
+        large = {"workload": "large_64x64x256_mixed", "points": lsim.n, "bonds": l1["nbonds"],
+                 "steps": args.large_steps, "value": (l1["bond_steps"] - l0["bond_steps"]) / (lms * 1e-3),
+                 "unit": UNIT, "ms_per_step": lms / args.large_steps, "bond_tile": l1["bond_tile"]}
+        del lsim
+
+    # ---- adjoint: 40x40x80 column, 200 steps, checkpoints every 20 ----
+    adj = None
+    if not args.no_adjoint:
+        acfg = pi.config("adjoint_40x40x80")
+        av0 = pi.initial_velocity(acfg)
+        asim = Simulation(acfg, precision="mixed", use_graph=False)
+        asim.write("v", av0)
+        ta = time.perf_counter()
+        asim.adjoint_forward(acfg["steps"], acfg["ckpt_every"])
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        u = asim.read("u", device=True).double()
+        nxy = acfg["nx"] * acfg["ny"]
+        dJ = torch.zeros_like(u)
+        dJ[0:2, -nxy:] = 2.0 * u[0:2, -nxy:]
+        g = asim.adjoint_reverse(dJ)
+        torch.cuda.synchronize()
+        tc = time.perf_counter()
+        adj = {"workload": "adjoint_40x40x80", "steps": acfg["steps"], "ckpt_every": acfg["ckpt_every"],
+               "objective": float((u[0:2, -nxy:] ** 2).sum()),
+               "grad": {"M": g[0], "eta": g[1], "suction": g[2], "pc0": g[3]},
+               "forward_s": tb - ta, "reverse_s": tc - tb,
+               "reverse_over_forward": (tc - tb) / (tb - ta)}
+        del asim
+
     # ---- FP64 path on the same column (fewer steps: FP64 is ~1/64 rate) ----
     sim64, fig64 = time_path(cfg, "fp64", args.fp64_steps, 1, barrier)
     fp64_rate = fig64["bond_steps"] / (fig64["ms"] * 1e-3)
@@ -349,6 +398,7 @@ def main():
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
+            "large": large, "adjoint": adj,
             "clocks": clocks, "gpu_launches": fig["launches"],
             "status": {k: st[k] for k in ("plastic", "nonconv", "singular", "flags")},
         }

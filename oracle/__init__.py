@@ -93,6 +93,9 @@ def lib():
             L.ppmo_internal_force.argtypes = [pp, C.c_int64, dp, dp, ip, ip, ip, dp]
             L.ppmo_init.argtypes = [pp, dp, C.POINTER(State)]
             L.ppmo_step.argtypes = [pp, C.POINTER(State), C.c_int]
+            L.ppmo_init_with_stress.argtypes = [pp, dp, dp, C.POINTER(State)]
+            L.ppmo_initial_stress.restype = None
+            L.ppmo_initial_stress.argtypes = [pp, dp]
             L.ppmo_objective_gradient.argtypes = [pp, dp, C.c_int, C.c_int64, dp, dp]
             L.ppmo_num_threads.restype = C.c_int
             L.ppmo_set_num_threads.argtypes = [C.c_int]
@@ -254,6 +257,15 @@ def objective_gradient(cfg, v0, n_steps, cap_per_point=256):
     return float(J[0]), g
 
 
+def initial_stress(cfg) -> np.ndarray:
+    """R13 geostatic initial effective stress (6, n), O(n)."""
+    p = make_params(cfg)
+    n = p.nx * p.ny * p.nz
+    sig = np.zeros(6 * n)
+    lib().ppmo_initial_stress(C.byref(p), _d(sig))
+    return sig.reshape(6, n)
+
+
 def set_threads(t: int):
     lib().ppmo_set_num_threads(int(t))
 
@@ -266,7 +278,8 @@ class Run:
     """One soil column stepped by the oracle (Alg. 2).  Arrays are numpy
     views in the oracle's component-major layout."""
 
-    def __init__(self, cfg: dict, v0: np.ndarray | None = None, cap_per_point: int = 256):
+    def __init__(self, cfg: dict, v0: np.ndarray | None = None, cap_per_point: int = 256,
+                 sig0: np.ndarray | None = None):
         self.cfg = dict(cfg)
         self.p = make_params(self.cfg)
         n = self.p.nx * self.p.ny * self.p.nz
@@ -290,7 +303,10 @@ class Run:
         self.s = s
         v0a = None if v0 is None else np.ascontiguousarray(v0, np.float64).reshape(3 * n)
         self._v0 = v0a
-        rc = lib().ppmo_init(C.byref(self.p), _d(v0a) if v0a is not None else None, C.byref(s))
+        s0 = None if sig0 is None else np.ascontiguousarray(sig0, np.float64).reshape(6 * n)
+        self._sig0 = s0
+        rc = lib().ppmo_init_with_stress(C.byref(self.p), _d(v0a) if v0a is not None else None,
+                                         _d(s0) if s0 is not None else None, C.byref(s))
         if rc != 0:
             raise RuntimeError(f"ppmo_init failed ({rc})")
 

@@ -683,38 +683,47 @@ static int rebuild(const ppmo_params* p, ppmo_state* s, const double* x) {
     return 0;
 }
 
-int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s) {
-    if (!params_ok(p)) return -1;
+/* R13: geostatic effective stress with a traction-free top -- total stress
+ * sigma_zz = -rho g d, sigma_xx = sigma_yy = K0 sigma_zz with K0 = nu/(1 - nu),
+ * d the depth below the top layer; effective = total - S_r s 1.  Zero when
+ * init_stress = 1.  sig is 6n. */
+void ppmo_initial_stress(const ppmo_params* p, double* sig) {
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
-    if (s->n != n) return -1;
-    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
     const double Srs = ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
-    /* K0 = nu / (1 - nu) with nu from K and mu */
     const double nu = (3.0 * p->K - 2.0 * p->mu) / (2.0 * (3.0 * p->K + p->mu));
     const double K0 = nu / (1.0 - nu);
     const double gmag = -p->gravity[2];
     for (int64_t i = 0; i < n; i++) {
         int64_t iz = i / ((int64_t)p->nx * p->ny);
+        for (int c = 0; c < 6; c++) sig[c * n + i] = 0.0;
+        if (p->init_stress == 0) {
+            double d = (double)(p->nz - 1 - iz) * p->dx;
+            double szz = -p->rho * gmag * d;
+            sig[0 * n + i] = K0 * szz - Srs;
+            sig[1 * n + i] = K0 * szz - Srs;
+            sig[2 * n + i] = szz - Srs;
+        }
+    }
+}
+
+int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* sig0,
+                          ppmo_state* s) {
+    if (!params_ok(p)) return -1;
+    int64_t n = (int64_t)p->nx * p->ny * p->nz;
+    if (s->n != n) return -1;
+    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
+    for (int64_t i = 0; i < n; i++) {
         for (int c = 0; c < 3; c++) {
             s->u[c * n + i] = 0.0;
             double vv = v0 ? v0[c * n + i] : 0.0;
             if (is_base(p, i) || (p->lock_lateral && c < 2)) vv = 0.0;
             s->v[c * n + i] = vv;
         }
-        for (int c = 0; c < 6; c++) s->sig[c * n + i] = 0.0;
-        if (p->init_stress == 0) {
-            /* geostatic effective stress with a traction-free top: total
-             * stress sigma_zz = -rho g d, sigma_xx = sigma_yy = K0 sigma_zz,
-             * effective = total - S_r s 1 */
-            double d = (double)(p->nz - 1 - iz) * p->dx;
-            double szz = -p->rho * gmag * d;
-            s->sig[0 * n + i] = K0 * szz - Srs;
-            s->sig[1 * n + i] = K0 * szz - Srs;
-            s->sig[2 * n + i] = szz - Srs;
-        }
         s->pc[i] = -p->pc0;        /* b1 = 0, b2 = 1: pbar_c = p_c (Eq. 45) */
         s->eps_s[i] = 0.0;
     }
+    if (sig0) memcpy(s->sig, sig0, sizeof(double) * 6 * (size_t)n);
+    else ppmo_initial_stress(p, s->sig);
     double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     if (!x) return -2;
     current_positions(p, n, s->u, x);
@@ -736,6 +745,10 @@ int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s) {
     s->W_int = 0.0; s->W_ext = 0.0; s->W_kin = wk; s->W_kin0 = wk;
     s->n_plastic = s->n_nonconv = s->n_singular = 0;
     return 0;
+}
+
+int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s) {
+    return ppmo_init_with_stress(p, v0, NULL, s);
 }
 
 int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {

@@ -110,6 +110,12 @@ int ppmo_internal_force(const ppmo_params* p, int64_t n, const double* x, const 
 
 /* Alg. 2, lines 1-3: initial state.  v0 is 3n (base layer is zeroed). */
 int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s);
+/* The same with a given initial effective stress sig0 (6n; NULL: the
+ * geostatic state of ppmo_initial_stress). */
+int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* sig0,
+                          ppmo_state* s);
+/* Initial effective stress of the column (6n), O(n). */
+void ppmo_initial_stress(const ppmo_params* p, double* sig);
 /* Alg. 2, lines 5-13: n_steps explicit central-difference steps. */
 int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps);
 
