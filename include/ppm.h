@@ -101,10 +101,10 @@ typedef struct {
     int32_t max_family;          /* bond capacity per point (0: 192; max 256)  */
     int32_t use_graph;           /* 1: replay steps through CUDA graphs; a whole
                                     rebuild period (R <= 64) is one graph      */
-    int32_t bond_tile;           /* bond-kernel threads per point: 64, 128, 256,
-                                    or 0 to time all three on the first pass
-                                    and keep the fastest (results are bitwise
-                                    reproducible for a fixed tile)             */
+    int32_t bond_tile;           /* bond-kernel threads per point: 32, 64, 128,
+                                    256, or 0 to time each on the first call's
+                                    bond pass and keep the fastest (results
+                                    are bitwise reproducible for a fixed tile) */
     int32_t pad_;
 } ppm_params;
 

@@ -58,7 +58,7 @@ __global__ void k_predictor(DevState<Real> s, StepConst k) {
 // ---------------------------------------------------------------------------
 // fused bond kernel: one CTA per point, one thread per bond
 // ---------------------------------------------------------------------------
-// TPP threads per point (a tile the autotuner picks among 64, 128, 256); the
+// TPP threads per point (a tile the autotuner picks among 32, 64, 128, 256); the
 // register budget targets 640 resident threads per SM for FP32
 template <typename Real, int MODEL, int TPP>
 __global__ void __launch_bounds__(TPP, sizeof(Real) == 4 ? (640 / TPP) : (256 / TPP > 0 ? 256 / TPP : 1))
@@ -352,14 +352,15 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         s.tsum[i] = red[9];
         s.tsum[n + i] = red[10];
         s.tsum[2 * n + i] = red[11];
-        if (with_dt && cnts[3]) atomicAdd(&s.ctr->pairs, (unsigned long long)cnts[3]);
-        if (cnts[0]) atomicAdd(&s.ctr->plastic, (unsigned long long)cnts[0]);
-        if (cnts[4]) atomicAdd(&s.ctr->ret64, (unsigned long long)cnts[4]);
-        if (cnts[1]) {
+        // only committed passes count (not the initial pass or the autotuner's)
+        if (update && cnts[3]) atomicAdd(&s.ctr->pairs, (unsigned long long)cnts[3]);
+        if (update && cnts[0]) atomicAdd(&s.ctr->plastic, (unsigned long long)cnts[0]);
+        if (update && cnts[4]) atomicAdd(&s.ctr->ret64, (unsigned long long)cnts[4]);
+        if (update && cnts[1]) {
             atomicAdd(&s.ctr->nonconv, (unsigned long long)cnts[1]);
             atomicOr(&s.ctr->status, PPM_STATUS_NONCONV);
         }
-        if (with_dt && cnts[2]) {
+        if (update && cnts[2]) {
             atomicAdd(&s.ctr->singular, (unsigned long long)cnts[2]);
             atomicOr(&s.ctr->status, PPM_STATUS_SINGULAR);
         }
@@ -472,9 +473,10 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     }
 }
 
-__global__ void k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
-                                const int32_t* row_ptr, int npoints) {
-    __shared__ double sm[3][256];
+__global__ void __launch_bounds__(1024)
+k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
+                const int32_t* row_ptr, int npoints) {
+    __shared__ double sm[3][1024];
     double t[3] = {0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
         for (int e = 0; e < 3; e++) t[e] += epart[(size_t)b * 3 + e];
@@ -580,10 +582,11 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
                         cudaStream_t st) {
     if (k.npoints <= 0) return cudaSuccess;
     const int with_dt = dt != 0.0;
-    const int tpp = (k.tile == 64 || k.tile == 256) ? k.tile : 128;
+    const int tpp = (k.tile == 32 || k.tile == 64 || k.tile == 256) ? k.tile : 128;
 #define PPM_BOND(M, T) k_bond<Real, M, T><<<k.npoints, T, 0, st>>>(s, k, with_dt, update)
 #define PPM_BOND_TILES(M)                           \
-    if (tpp == 64) PPM_BOND(M, 64);                 \
+    if (tpp == 32) PPM_BOND(M, 32);                 \
+    else if (tpp == 64) PPM_BOND(M, 64);            \
     else if (tpp == 256) PPM_BOND(M, 256);          \
     else PPM_BOND(M, 128);
     switch (k.model) {
@@ -605,7 +608,7 @@ cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt
 
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
                                  const int32_t* row_ptr, int npoints, cudaStream_t st) {
-    k_energy_reduce<<<1, 256, 0, st>>>(epart, nblocks, ctr, initial, row_ptr, npoints);
+    k_energy_reduce<<<1, 1024, 0, st>>>(epart, nblocks, ctr, initial, row_ptr, npoints);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,8 @@ int check_params(const ppm_params* p) {
     if (p->precision != PPM_FP64 && p->precision != PPM_MIXED) return PPM_EINVAL;
     if (p->newton_max_iter < 1 || !(p->newton_tol > 0)) return PPM_EINVAL;
     if (p->max_family < 0 || p->max_family > kMaxRow) return PPM_EINVAL;
-    if (p->bond_tile != 0 && p->bond_tile != 64 && p->bond_tile != 128 && p->bond_tile != 256)
+    if (p->bond_tile != 0 && p->bond_tile != 32 && p->bond_tile != 64 && p->bond_tile != 128 &&
+        p->bond_tile != 256)
         return PPM_EINVAL;
     if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
         return PPM_EINVAL;
@@ -271,18 +272,19 @@ int capture_segment(ppm_ctx* c, const DevState<Real>& s, int len, cudaGraphExec_
     return e == cudaSuccess ? PPM_OK : PPM_ECUDA;
 }
 
-// bond-kernel tile: time the initial (dt = 0, state-preserving) bond pass
-// with 64, 128 and 256 threads per point and keep the fastest
+// bond-kernel tile: time a full bond pass (with the time step, so the
+// constitutive update runs, but without committing the point state) with
+// 32, 64, 128 and 256 threads per point and keep the fastest
 template <typename Real>
 int autotune_tile(ppm_ctx* c, const DevState<Real>& s) {
-    const int tiles[3] = {64, 128, 256};
+    const int tiles[4] = {32, 64, 128, 256};
     float best = 1e30f;
     int pick = 128;
-    for (int q = 0; q < 3; q++) {
+    for (int q = 0; q < 4; q++) {
         c->k.tile = tiles[q];
-        CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));      // warm
+        CU(launch_bond<Real>(s, c->k, c->k.dt, 0, c->stream));      // warm
         CU(cudaEventRecord(c->ev[4], c->stream));
-        for (int r = 0; r < 2; r++) CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
+        for (int r = 0; r < 2; r++) CU(launch_bond<Real>(s, c->k, c->k.dt, 0, c->stream));
         CU(cudaEventRecord(c->ev[5], c->stream));
         CU(cudaEventSynchronize(c->ev[5]));
         float ms = 0.f;
