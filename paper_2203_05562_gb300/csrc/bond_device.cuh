@@ -139,14 +139,76 @@ __device__ __noinline__ int return_map(const ReturnConst& R, double tol, int max
     }
 }
 
+// Mixed path, near the apex: FP64 Newton refinement of the FP32 root.  The
+// residual is Eq. 73-75 as above with the divisions by M^2, pc_n and
+// lambda - kappa taken as products with reciprocals; each step's residual is also its
+// convergence test, so a start within the FP32 tolerance costs one Jacobian
+// and two residuals.  A step is accepted only if the residual is finite and
+// its 2-norm decreases; returns 0 (the caller then solves from the trial
+// state) otherwise, or after max_iter steps.
+__device__ __forceinline__ void refine_residual(const ReturnConst& R, double inv_M2, double inv_pcn,
+                                                double g, const double x[3], double r[3]) {
+    const double pb = x[0], q = x[1], pc = x[2];
+    const double f = q * q * inv_M2 + pb * (pb - pc);
+    const double fp = 2.0 * pb - pc;
+    r[0] = (pb - R.p_tr + R.K * R.c * f * fp) * R.inv_scale;
+    r[1] = (q - R.q_tr + 6.0 * R.mu * R.c * f * q * inv_M2) * R.inv_scale;
+    const double ratio = pc * inv_pcn;
+    r[2] = (ratio > 0.0) ? log(ratio) + g * f * fp : (double)INFINITY;
+}
+
+__device__ __noinline__ int return_refine64(const ReturnConst& R, double tol, int max_iter,
+                                            double x[3]) {
+    const double inv_M2 = 1.0 / R.M2, inv_pcn = 1.0 / R.pc_n, g = R.c / R.lk;
+    const double a = R.K * R.c * R.inv_scale, b = 3.0 * R.mu * R.c * R.inv_scale;
+    double r[3];
+    refine_residual(R, inv_M2, inv_pcn, g, x, r);
+    if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) return 0;
+    for (int it = 0; it < max_iter; it++) {
+        if (fmax(fabs(r[0]), fmax(fabs(r[1]), fabs(r[2]))) <= tol) return 1;
+        const double pb = x[0], q = x[1], pc = x[2];
+        const double f = q * q * inv_M2 + pb * (pb - pc);
+        const double fp = 2.0 * pb - pc, fq = 2.0 * q * inv_M2, fc = -pb;
+        double J[9];
+        J[0] = R.inv_scale + a * (fp * fp + 2.0 * f);
+        J[1] = a * fq * fp;
+        J[2] = a * (fc * fp - f);
+        J[3] = b * fp * fq;
+        J[4] = R.inv_scale + b * (fq * fq + 2.0 * f * inv_M2);
+        J[5] = b * fc * fq;
+        J[6] = g * (fp * fp + 2.0 * f);
+        J[7] = g * (fq * fp);
+        J[8] = 1.0 / pc + g * (fc * fp - f);
+        const double m0 = J[4] * J[8] - J[5] * J[7];
+        const double m1 = J[3] * J[8] - J[5] * J[6];
+        const double m2 = J[3] * J[7] - J[4] * J[6];
+        const double det = J[0] * m0 - J[1] * m1 + J[2] * m2;
+        if (det == 0.0 || !isfinite(det)) return 0;
+        const double id = 1.0 / det;
+        double xt[3], rt[3];
+        xt[0] = x[0] - (r[0] * m0 - J[1] * (r[1] * J[8] - J[5] * r[2]) + J[2] * (r[1] * J[7] - J[4] * r[2])) * id;
+        xt[1] = x[1] - (J[0] * (r[1] * J[8] - J[5] * r[2]) - r[0] * m1 + J[2] * (J[3] * r[2] - r[1] * J[6])) * id;
+        xt[2] = x[2] - (J[0] * (J[4] * r[2] - r[1] * J[7]) - J[1] * (J[3] * r[2] - r[1] * J[6]) + r[0] * m2) * id;
+        refine_residual(R, inv_M2, inv_pcn, g, xt, rt);
+        if (!(isfinite(rt[0]) && isfinite(rt[1]) && isfinite(rt[2])) ||
+            !(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2] < r[0] * r[0] + r[1] * r[1] + r[2] * r[2]))
+            return 0;
+        x[0] = xt[0]; x[1] = xt[1]; x[2] = xt[2];
+        r[0] = rt[0]; r[1] = rt[1]; r[2] = rt[2];
+    }
+    return fmax(fabs(r[0]), fmax(fabs(r[1]), fabs(r[2]))) <= tol;
+}
+
 // Mixed path: the same return solved in FP32, in increments from the trial
 // state, x = (dp, dq, dpc) with p = p_tr + dp, q = q_tr + dq, pc = pc_n + dpc,
 // so that the small corrections keep their precision; Eq. 75 in the form
-// log1p(dpc / pc_n) + c f f_p / (lambda - kappa) = 0.  Stopping rules as in
+// log1p(dpc / pc_n) + c f f_p / (lambda - kappa) = 0, divisions by constants
+// taken as products with their reciprocals.  Stopping rules as in
 // the FP64 solve with an FP32 tolerance.  Returns 1 if converged.
 struct ReturnConstF {
     float K, mu, M2, lk, c, inv_scale, scale;
     float p_tr, q_tr, pc_n, tol;
+    float inv_M2, inv_pcn, g;   // 1 / M^2, 1 / pc_n, c / (lambda - kappa)
     int max_iter;
 };
 
@@ -154,22 +216,22 @@ template <bool WANT_J>
 __device__ __forceinline__ void return_residual_f(const ReturnConstF& R, const float x[3],
                                                   float r[3], float J[9]) {
     const float pb = R.p_tr + x[0], q = R.q_tr + x[1], pc = R.pc_n + x[2];
-    const float f = q * q / R.M2 + pb * (pb - pc);
+    const float f = q * q * R.inv_M2 + pb * (pb - pc);
     const float fp = 2.0f * pb - pc;
-    const float fq = 2.0f * q / R.M2;
+    const float fq = 2.0f * q * R.inv_M2;
     const float fc = -pb;
     r[0] = (x[0] + R.K * R.c * f * fp) * R.inv_scale;
     r[1] = (x[1] + 3.0f * R.mu * R.c * f * fq) * R.inv_scale;
-    const float rel = x[2] / R.pc_n;
-    r[2] = (rel > -1.0f) ? log1pf(rel) + R.c * f * fp / R.lk : INFINITY;
+    const float rel = x[2] * R.inv_pcn;
+    r[2] = (rel > -1.0f) ? log1pf(rel) + R.g * f * fp : INFINITY;
     if (WANT_J) {
         const float a = R.K * R.c * R.inv_scale, b = 3.0f * R.mu * R.c * R.inv_scale;
-        const float g = R.c / R.lk;
+        const float g = R.g;
         J[0] = R.inv_scale + a * (fp * fp + 2.0f * f);
         J[1] = a * fq * fp;
         J[2] = a * (fc * fp - f);
         J[3] = b * fp * fq;
-        J[4] = R.inv_scale + b * (fq * fq + 2.0f * f / R.M2);
+        J[4] = R.inv_scale + b * (fq * fq + 2.0f * f * R.inv_M2);
         J[5] = b * fc * fq;
         J[6] = g * (fp * fp + 2.0f * f);
         J[7] = g * (fq * fp);
@@ -316,18 +378,25 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
     o.ret64 = 0;
     Real p_new = p_tr, q_new = q_tr, pc_new = pc_n;
     bool need64 = F64;
+    bool warm = false;
+    double x64[3] = {0.0, 0.0, 0.0};
     if constexpr (!F64) {
-        // FP32 return unless the state is near the critical-state apex
-        // (mean stress within 5% of the preconsolidation pressure from
-        // zero, or tensile) or the preconsolidation pressure has nearly
-        // vanished; any FP32 solve that fails is redone in FP64
-        need64 = (p_tr > 0.05f * pc_n) || (pc_n > -100.0f);
-        if (!need64) {
+        // FP32 return first.  Near the critical-state apex (mean stress within
+        // 5% of the preconsolidation pressure from zero, or tensile) or where
+        // the preconsolidation pressure has nearly vanished, the FP32 root
+        // only starts the FP64 Newton solve, which then takes one or two
+        // steps to the FP64 tolerance (mixed-precision refinement); an FP32
+        // solve that fails is redone in FP64 from the trial state
+        const bool near_apex = (p_tr > 0.05f * pc_n) || (pc_n > -100.0f);
+        {
             ReturnConstF R;
             R.K = k.Kf; R.mu = k.muf; R.M2 = Mf * Mf; R.lk = (float)k.lk;
             R.p_tr = p_tr; R.q_tr = q_tr; R.pc_n = pc_n;
             const float eta_eff = (k.visc_form == 0) ? k.etaf * pc_n * pc_n : k.etaf;
             R.c = k.dtf / eta_eff;
+            R.inv_M2 = 1.0f / R.M2;
+            R.inv_pcn = 1.0f / pc_n;
+            R.g = R.c / R.lk;
             float scale = fmaxf(fmaxf(fabsf(pc_n), fabsf(p_tr)), fmaxf(q_tr, 1.0f));
             R.scale = scale;
             R.inv_scale = 1.0f / scale;
@@ -339,6 +408,12 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
                 q_new = q_tr + x[1];
                 pc_new = pc_n + x[2];
                 o.nonconv = 0;
+                if (near_apex) {
+                    need64 = warm = true;
+                    x64[0] = (double)p_tr + (double)x[0];
+                    x64[1] = (double)q_tr + (double)x[1];
+                    x64[2] = (double)pc_n + (double)x[2];
+                }
             } else {
                 need64 = true;
             }
@@ -356,8 +431,9 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
         if (R.q_tr > scale) scale = R.q_tr;
         if (scale < 1.0) scale = 1.0;
         R.inv_scale = 1.0 / scale;
-        double x[3];
-        const int ok = return_map(R, k.tol, k.max_iter, x);
+        double x[3] = {x64[0], x64[1], x64[2]};
+        int ok = warm ? return_refine64(R, k.tol, k.max_iter, x) : 0;
+        if (!ok) ok = return_map(R, k.tol, k.max_iter, x);
         o.nonconv = !ok;
         o.ret64 = 1;
         p_new = (Real)x[0];
