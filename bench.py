@@ -42,20 +42,30 @@ SMS, LANES = 152, 128
 FLOPS_TEST, FLOPS_PAIR = 8, 30
 
 
+BOND_SOURCES = ("bond.cu", "bond_device.cuh", "ppm_internal.cuh")
+
+
+def bond_source_digest():
+    """sha256 prefix over the sources the bond kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in BOND_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_05562_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the bond kernel from the committed ncu
-    summary, or None when csrc/bond.cu has changed since the capture."""
-    import hashlib
+    summary, or None when the kernel's sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "bond_kernel_collapse_40x40x80.json")
-    src = os.path.join(ROOT, "paper_2203_05562_gb300", "csrc", "bond.cu")
     try:
         with open(path) as f:
             prof = json.load(f)
-        with open(src, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        digest = bond_source_digest()
     except OSError:
         return None
-    if prof.get("bond_cu_sha256_16") != digest:
+    if prof.get("bond_src_sha256_16") != digest:
         return None
     return prof.get("dram_bytes_per_launch")
 

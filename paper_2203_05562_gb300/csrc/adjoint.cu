@@ -293,7 +293,7 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
     for (int t = threadIdx.x; t < nb; t += kAdjThreads) {
         const R4<Real> zj = s_z[t];
         const Real mjx = (Real)-2 * zj.x, mjy = (Real)-2 * zj.y, mjz = (Real)-2 * zj.z;
-        const Real cj = zj.w - hf2;
+        const Real thj = hf2 - zj.w;   // the forward's test, the same rounding
         Real K00 = 0, K11 = 0, K22 = 0, K12 = 0, K02 = 0, K01 = 0;
         Real A00 = 0, A01 = 0, A02 = 0, A10 = 0, A11 = 0, A12 = 0, A20 = 0, A21 = 0, A22 = 0;
         int cnt = 0;
@@ -327,8 +327,8 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
             for (int q = 0; q < nb; q++) {
                 const R4<Real> zk = s_z[q];
                 const R4<Real> yk = s_y[q];
-                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + (zk.w + cj)));
-                masked_accumulate(tst, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
+                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + zk.w));
+                masked_accumulate(tst, thj, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
             }
             K00 = Kf[0]; K11 = Kf[1]; K22 = Kf[2]; K12 = Kf[3]; K02 = Kf[4]; K01 = Kf[5];
             A00 = Af[0]; A01 = Af[1]; A02 = Af[2]; A10 = Af[3]; A11 = Af[4]; A12 = Af[5];
@@ -349,7 +349,7 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
         }
         sb[15] = (Real)cnt;
         sb[16] = active ? (Real)1 : (Real)0;
-        sb[18] = mjx; sb[19] = mjy; sb[20] = mjz; sb[21] = cj;
+        sb[18] = mjx; sb[19] = mjy; sb[20] = mjz; sb[21] = thj;
         if (active) wpart[0] += (Real)cnt * inv_nb;
     }
     block_sum<1, Real>(wpart, reinterpret_cast<Real(*)[1]>(&s_red[0][0]));
@@ -498,8 +498,8 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
                         member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
                                            __dmul_rn(d2, d2)) <= k.delta2;
                     } else {
-                        const float tst = zt.x * sq[18] + (zt.y * sq[19] + (zt.z * sq[20] + (zt.w + sq[21])));
-                        member = tst <= 0.0f;
+                        const float tst = zt.x * sq[18] + (zt.y * sq[19] + (zt.z * sq[20] + zt.w));
+                        member = tst <= sq[21];
                     }
                 }
                 if (member) {

@@ -73,6 +73,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     __shared__ alignas(16) Real s_M[MODEL == 2 ? kMaxRow : 1][F64 ? 9 : 16];
     __shared__ Real s_red[NW][12];
     __shared__ unsigned s_cnt[NW][5];
+    // FP32 path: a plastic bond's trial stress, K~^-1, varpi and strain
+    // measure, parked by its thread while the return runs (model 2 parks in
+    // the bond's own row of s_M, which is written only after the return)
+    __shared__ alignas(16) Real s_park[(F64 || MODEL == 2) ? 1 : TPP][16];
 
     const int i = blockIdx.x;
     const size_t n = (size_t)k.npoints;
@@ -136,9 +140,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 
     for (int t = threadIdx.x; t < nb; t += TPP) {
         const R4<Real> zj = s_z[t];
-        // mixed-path test |z_k - z_j|^2 - hf^2 = |z_k|^2 + (|z_j|^2 - hf^2) - 2 z_k.z_j
+        // mixed-path test |z_k - z_j|^2 <= hf^2 as
+        // |z_k|^2 - 2 z_k.z_j <= hf^2 - |z_j|^2 (threshold thj per bond)
         const Real mjx = (Real)-2 * zj.x, mjy = (Real)-2 * zj.y, mjz = (Real)-2 * zj.z;
-        const Real cj = zj.w - hf2;
+        const Real thj = hf2 - zj.w;
         double pjx = 0, pjy = 0, pjz = 0;
         if constexpr (F64) { pjx = s_p[0][t]; pjy = s_p[F64 ? 1 : 0][t]; pjz = s_p[F64 ? 2 : 0][t]; }
         Real K00 = 0, K11 = 0, K22 = 0, K12 = 0, K02 = 0, K01 = 0;
@@ -176,8 +181,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             for (int q = 0; q < nb; q++) {
                 const R4<Real> zk = s_z[q];
                 const R4<Real> yk = s_y[q];
-                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + (zk.w + cj)));
-                masked_accumulate(tst, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
+                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + zk.w));
+                masked_accumulate(tst, thj, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
             }
             K00 = Kf[0]; K11 = Kf[1]; K22 = Kf[2]; K12 = Kf[3]; K02 = Kf[4]; K01 = Kf[5];
             A00 = Af[0]; A01 = Af[1]; A02 = Af[2]; A10 = Af[3]; A11 = Af[4]; A12 = Af[5];
@@ -210,15 +215,15 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 #pragma unroll
                 for (int e = 0; e < 9; e++) s_M[t][e] = (Real)0;
                 if constexpr (!F64) {
-                    s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = cj;
+                    s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = thj;
                 }
             }
             continue;
         }
-        const Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
-                            (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
-                            (Real)Kid[4], (Real)Kid[3], (Real)Kid[2]};
-        const Real varpi = (Real)cnt * inv_nb;              // Eq. 55
+        Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
+                      (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
+                      (Real)Kid[4], (Real)Kid[3], (Real)Kid[2]};
+        Real varpi = (Real)cnt * inv_nb;                    // Eq. 55
         BondStress<Real> bs;
         if (with_dt) {
             // velocity gradient L = A~ K~^-1 / dx (Eq. 25, 57)
@@ -230,10 +235,44 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 for (int c = 0; c < 3; c++)
                     L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
                                     A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
-            material_update<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, bs);
-            n_plastic += bs.plastic;
-            n_nonconv += bs.nonconv;
-            n_ret64 += bs.ret64;
+            Real st[6], des;
+            if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
+                if constexpr (!F64) {
+                    // the bond waits in shared memory while the return runs, so
+                    // that none of it is held in registers across the return's
+                    // calls (the compiler barriers keep it from being forwarded)
+                    Real* pk = (MODEL == 2) ? s_M[t] : s_park[threadIdx.x];
+#pragma unroll
+                    for (int c = 0; c < 6; c++) pk[c] = st[c];
+#pragma unroll
+                    for (int c = 0; c < 6; c++) pk[6 + c] = Kid[c];
+                    pk[12] = varpi;
+                    pk[13] = des;
+                    asm volatile("" ::: "memory");
+                    Real stp[6];
+#pragma unroll
+                    for (int c = 0; c < 6; c++) stp[c] = pk[c];
+                    material_return<Real>(stp, pc_i, k, cc.M, cc.Mf, bs);
+                    asm volatile("" ::: "memory");
+                    const Real* q = (MODEL == 2) ? s_M[t] : s_park[threadIdx.x];
+                    Ki[0] = q[6]; Ki[1] = q[11]; Ki[2] = q[10];
+                    Ki[3] = q[11]; Ki[4] = q[7]; Ki[5] = q[9];
+                    Ki[6] = q[10]; Ki[7] = q[9]; Ki[8] = q[8];
+                    varpi = q[12];
+                    bs.des = q[13];
+                } else {
+                    material_return<Real>(st, pc_i, k, cc.M, cc.Mf, bs);
+                    bs.des = des;
+                }
+                n_plastic++;
+                n_nonconv += bs.nonconv;
+                n_ret64 += bs.ret64;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; c++) bs.sig[c] = st[c];
+                bs.pc = pc_i;
+                bs.des = des;
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < 6; c++) bs.sig[c] = sig_i[c];
@@ -270,7 +309,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 #pragma unroll
             for (int e = 0; e < 9; e++) s_M[t][e] = SK[e];
             if constexpr (!F64) {
-                s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = cj;
+                s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = thj;
             }
         }
         red[0] += varpi;
@@ -315,8 +354,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                     const float4 m1 = *reinterpret_cast<const float4*>(&s_M[q][4]);
                     const float4 m2 = *reinterpret_cast<const float4*>(&s_M[q][8]);
                     const float4 m3 = *reinterpret_cast<const float4*>(&s_M[q][12]);
-                    const float tst = zt.x * m2.y + (zt.y * m2.z + (zt.z * m2.w + (zt.w + m3.x)));
-                    masked_add9(tst, m0, m1, m2.x, Nf);
+                    const float tst = zt.x * m2.y + (zt.y * m2.z + (zt.z * m2.w + zt.w));
+                    masked_add9(tst, m3.x, m0, m1, m2.x, Nf);
                 }
 #pragma unroll
                 for (int e = 0; e < 9; e++) N[e] = Nf[e];

@@ -298,16 +298,19 @@ struct MatTrace {
     double c;           // dt / eta_eff
 };
 
+// Elastic part of the update of one bond: rate of deformation and spin
+// (Eq. 26), Hughes-Winget rotation of the stress, linear trial stress
+// (Eq. 41), its invariants and the yield test (Eq. 40).  Returns true when
+// the trial state lies outside the yield surface (plastic).
 template <typename Real>
-__device__ __forceinline__ void material_update(const Real L[9], const Real sn[6], Real pc_n,
-                                                const StepConst& k, double M, float Mf,
-                                                BondStress<Real>& o,
-                                                MatTrace<Real>* trace = nullptr) {
+__device__ __forceinline__ bool material_trial(const Real L[9], const Real sn[6], Real pc_n,
+                                               const StepConst& k, double M, float Mf,
+                                               Real st[6], Real& des,
+                                               MatTrace<Real>* trace = nullptr) {
     constexpr bool F64 = sizeof(Real) == 8;
     const Real dt = F64 ? (Real)k.dt : (Real)k.dtf;
     const Real Kb = F64 ? (Real)k.K : (Real)k.Kf;
     const Real mu = F64 ? (Real)k.mu : (Real)k.muf;
-    // rate of deformation and spin (Eq. 26)
     const Real D00 = L[0], D11 = L[4], D22 = L[8];
     const Real D12 = (Real)0.5 * (L[5] + L[7]);
     const Real D02 = (Real)0.5 * (L[2] + L[6]);
@@ -339,7 +342,6 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
     const Real e12 = dt * D12, e02 = dt * D02, e01 = dt * D01;
     const Real tr = e00 + e11 + e22, tr3 = tr * (Real)(1.0 / 3.0);
     const Real lam = Kb * tr;
-    Real st[6];
     st[0] = rot(0, 0) + lam + (Real)2 * mu * (e00 - tr3);
     st[1] = rot(1, 1) + lam + (Real)2 * mu * (e11 - tr3);
     st[2] = rot(2, 2) + lam + (Real)2 * mu * (e22 - tr3);
@@ -347,8 +349,8 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
     st[4] = (Real)0.5 * (rot(0, 2) + rot(2, 0)) + (Real)2 * mu * e02;
     st[5] = (Real)0.5 * (rot(0, 1) + rot(1, 0)) + (Real)2 * mu * e01;
     const Real d0 = e00 - tr3, d1 = e11 - tr3, d2 = e22 - tr3;
-    o.des = sqrt((Real)(2.0 / 3.0) *
-                 (d0 * d0 + d1 * d1 + d2 * d2 + (Real)2 * (e12 * e12 + e02 * e02 + e01 * e01)));
+    des = sqrt((Real)(2.0 / 3.0) *
+               (d0 * d0 + d1 * d1 + d2 * d2 + (Real)2 * (e12 * e12 + e02 * e02 + e01 * e01)));
     // invariants and yield function (Eq. 40)
     const Real p_tr = (st[0] + st[1] + st[2]) * (Real)(1.0 / 3.0);
     const Real s0 = st[0] - p_tr, s1 = st[1] - p_tr, s2 = st[2] - p_tr;
@@ -356,9 +358,6 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
                                         (Real)2 * (st[3] * st[3] + st[4] * st[4] + st[5] * st[5])));
     const Real Mr = F64 ? (Real)M : (Real)Mf;
     const Real f_tr = q_tr * q_tr / (Mr * Mr) + p_tr * (p_tr - pc_n);
-    o.plastic = 0;
-    o.nonconv = 0;
-    o.ret64 = 0;
     if (trace) {
 #pragma unroll
         for (int e = 0; e < 9; e++) trace->Q[e] = Q[e];
@@ -368,13 +367,22 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
         trace->p_tr = p_tr; trace->q_tr = q_tr;
         trace->plastic = 0; trace->floored = 0;
     }
-    if (!(f_tr > (Real)0)) {
-#pragma unroll
-        for (int c = 0; c < 6; c++) o.sig[c] = st[c];
-        o.pc = pc_n;
-        return;
-    }
+    return f_tr > (Real)0;
+}
+
+// Plastic part: the visco-plastic return from the trial stress st (Eq. 42-46,
+// 70-76) and the radial scaling of its deviator; o.des is left to the caller.
+template <typename Real>
+__device__ __forceinline__ void material_return(const Real st[6], Real pc_n, const StepConst& k,
+                                                double M, float Mf, BondStress<Real>& o,
+                                                MatTrace<Real>* trace = nullptr) {
+    constexpr bool F64 = sizeof(Real) == 8;
+    const Real p_tr = (st[0] + st[1] + st[2]) * (Real)(1.0 / 3.0);
+    const Real s0 = st[0] - p_tr, s1 = st[1] - p_tr, s2 = st[2] - p_tr;
+    const Real q_tr = sqrt((Real)1.5 * (s0 * s0 + s1 * s1 + s2 * s2 +
+                                        (Real)2 * (st[3] * st[3] + st[4] * st[4] + st[5] * st[5])));
     o.plastic = 1;
+    o.nonconv = 0;
     o.ret64 = 0;
     Real p_new = p_tr, q_new = q_tr, pc_new = pc_n;
     bool need64 = F64;
@@ -459,15 +467,37 @@ __device__ __forceinline__ void material_update(const Real L[9], const Real sn[6
     o.pc = pc_new;
 }
 
-// Predicated sub-horizon accumulation: when tst <= 0 (member), add the
+
+// The whole update of one bond (elastic trial, then the return if plastic).
+template <typename Real>
+__device__ __forceinline__ void material_update(const Real L[9], const Real sn[6], Real pc_n,
+                                                const StepConst& k, double M, float Mf,
+                                                BondStress<Real>& o,
+                                                MatTrace<Real>* trace = nullptr) {
+    Real st[6], des;
+    const bool plastic = material_trial<Real>(L, sn, pc_n, k, M, Mf, st, des, trace);
+    if (plastic) {
+        material_return<Real>(st, pc_n, k, M, Mf, o, trace);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; c++) o.sig[c] = st[c];
+        o.pc = pc_n;
+        o.plastic = 0;
+        o.nonconv = 0;
+        o.ret64 = 0;
+    }
+    o.des = des;
+}
+
+// Predicated sub-horizon accumulation: when tst <= thr (member), add the
 // outer products zeta~ zeta~^T (6), Ydot zeta~^T (9) and 1 to the count; the
 // predicate guards each FMA, so non-members cost no extra multiplies and the
 // warp never branches.
-__device__ __forceinline__ void masked_accumulate(float tst, float zx, float zy, float zz,
-                                                  float yx, float yy, float yz, float (&K)[6],
-                                                  float (&A)[9], float& cnt) {
+__device__ __forceinline__ void masked_accumulate(float tst, float thr, float zx, float zy,
+                                                  float zz, float yx, float yy, float yz,
+                                                  float (&K)[6], float (&A)[9], float& cnt) {
     asm("{\n\t.reg .pred p;\n\t"
-        "setp.le.f32 p, %16, 0f00000000;\n\t"
+        "setp.le.f32 p, %16, %23;\n\t"
         "@p fma.rn.f32 %0, %17, %17, %0;\n\t"
         "@p fma.rn.f32 %1, %18, %18, %1;\n\t"
         "@p fma.rn.f32 %2, %19, %19, %2;\n\t"
@@ -488,14 +518,14 @@ __device__ __forceinline__ void masked_accumulate(float tst, float zx, float zy,
         : "+f"(K[0]), "+f"(K[1]), "+f"(K[2]), "+f"(K[3]), "+f"(K[4]), "+f"(K[5]),
           "+f"(A[0]), "+f"(A[1]), "+f"(A[2]), "+f"(A[3]), "+f"(A[4]), "+f"(A[5]),
           "+f"(A[6]), "+f"(A[7]), "+f"(A[8]), "+f"(cnt)
-        : "f"(tst), "f"(zx), "f"(zy), "f"(zz), "f"(yx), "f"(yy), "f"(yz));
+        : "f"(tst), "f"(zx), "f"(zy), "f"(zz), "f"(yx), "f"(yy), "f"(yz), "f"(thr));
 }
 
-// Predicated sum of a sender's 3x3 matrix (M) into N when tst <= 0.
-__device__ __forceinline__ void masked_add9(float tst, const float4& m0, const float4& m1,
-                                            float m8, float (&N)[9]) {
+// Predicated sum of a sender's 3x3 matrix (M) into N when tst <= thr.
+__device__ __forceinline__ void masked_add9(float tst, float thr, const float4& m0,
+                                            const float4& m1, float m8, float (&N)[9]) {
     asm("{\n\t.reg .pred p;\n\t"
-        "setp.le.f32 p, %9, 0f00000000;\n\t"
+        "setp.le.f32 p, %9, %19;\n\t"
         "@p add.f32 %0, %0, %10;\n\t"
         "@p add.f32 %1, %1, %11;\n\t"
         "@p add.f32 %2, %2, %12;\n\t"
@@ -509,7 +539,7 @@ __device__ __forceinline__ void masked_add9(float tst, const float4& m0, const f
         : "+f"(N[0]), "+f"(N[1]), "+f"(N[2]), "+f"(N[3]), "+f"(N[4]), "+f"(N[5]), "+f"(N[6]),
           "+f"(N[7]), "+f"(N[8])
         : "f"(tst), "f"(m0.x), "f"(m0.y), "f"(m0.z), "f"(m0.w), "f"(m1.x), "f"(m1.y), "f"(m1.z),
-          "f"(m1.w), "f"(m8));
+          "f"(m1.w), "f"(m8), "f"(thr));
 }
 
 // deterministic block sum: butterfly within warps, then warps in order
