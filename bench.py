@@ -70,6 +70,19 @@ def profiled_traffic():
     return prof.get("dram_bytes_per_launch")
 
 
+def algorithmic_bytes(nbonds: int, npoints: int, mixed: bool) -> float:
+    """DRAM bytes one step must move (R = 4 B mixed, 8 B FP64).
+    Per bond: col and rev read (8 B), the force state written in bond order
+    and at its reverse slot (2 x 3R), the reverse-slot row read back by the
+    gather (3R).  Per point: the bond kernel reads lat, colid, row_ptr
+    (12 B), u, vh, sigma, pc, eps (14R) and writes sigma, pc, eps, tsum
+    (11R); the gather reads row_ptr, lat (8 B), tsum, vh (6R) and writes
+    fint, a, v (9R); the predictor reads u, v, a (9R) and writes u, vh (6R),
+    plus the FP32 displacement compensation (read and written, 24 B)."""
+    R = 4 if mixed else 8
+    return nbonds * (8 + 9 * R) + npoints * (20 + 55 * R + (24 if mixed else 0))
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -395,6 +408,18 @@ def main():
         rate, threads, desc = oracle_sample(3)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
+    # HBM GB/s of both paths: algorithmic bytes per step x steps per second,
+    # and the bond kernel's profiled DRAM bytes over its event-timed launch
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    b_mixed = algorithmic_bytes(nb, n, True)
+    b_fp64 = algorithmic_bytes(nb, n, False)
+    traffic = roofline["traffic"]
+    hbm = {"unit": "GB/s", "peak": hbm_peak, "peak_kind": peak_kind,
+           "mixed": {"bytes_per_step": b_mixed, "gbs": b_mixed * (value / world / nb) / 1e9,
+                     "bond_kernel_dram_gbs": traffic / (bond_ms * 1e-3) / 1e9 if traffic else None},
+           "fp64": {"bytes_per_step": b_fp64, "gbs": b_fp64 * (fp64_rate / nb) / 1e9},
+           "note": "the path is FP32-issue-bound (roofline above); these are far below the HBM roof"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -407,6 +432,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
+            "hbm": hbm,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "large": large, "adjoint": adj,
             "clocks": clocks, "gpu_launches": fig["launches"],
