@@ -151,6 +151,21 @@ def dist_setup():
     return world, rank, local
 
 
+def aggregate_over_ranks(ms: float, bond_steps: float, dist=None, device="cuda"):
+    """Whole-job figures of N replicas: the slowest rank's time (max) and
+    every rank's bond-steps (sum).  dist is torch.distributed (or None for
+    one process); device is where the collective's tensors live ("cuda"
+    under NCCL, "cpu" under gloo)."""
+    if dist is None:
+        return ms, bond_steps
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([bond_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(b)
+    return float(t.item()), float(b.item())
+
+
 def oracle_sample(steps: int = 3):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the
     workload: a 20x20x40 sub-column (same material, dx, suction) for a few
@@ -259,16 +274,7 @@ def main():
     sampler.start()
     sim, fig = time_path(cfg, "mixed", args.steps, args.warmup, barrier)
     clocks = sampler.stop()
-    ms = fig["ms"]
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        b = torch.tensor([float(fig["bond_steps"])], device="cuda")
-        dist.all_reduce(b)
-        total_bond_steps = float(b.item())
-    else:
-        total_bond_steps = float(fig["bond_steps"])
+    ms, total_bond_steps = aggregate_over_ranks(fig["ms"], float(fig["bond_steps"]), dist)
     value = total_bond_steps / (ms * 1e-3)
 
     # ---- dominant kernel: per-phase CUDA-event times on the launching stream,
@@ -398,7 +404,8 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     s1 = esim.status()["bond_steps"]
-    e2e = {"value": (s1 - s0) / e2e_s * world, "unit": UNIT,
+    e2e_ms, e2e_bond_steps = aggregate_over_ranks(e2e_s * 1e3, float(s1 - s0), dist)
+    e2e = {"value": e2e_bond_steps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": int(host_v0.numel() * 4 / args.steps),
            "d2h_bytes_per_step": int(host_u.numel() * 4)}
 
