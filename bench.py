@@ -282,7 +282,8 @@ def main():
     st = sim.status()
     del sim
     from paper_2203_05562_gb300 import Simulation
-    tsim = Simulation(cfg, precision="mixed", bond_tile=fig["status"]["bond_tile"])
+    tile = fig["status"]["bond_tile"]          # the autotuner's choice, reused below
+    tsim = Simulation(cfg, precision="mixed", bond_tile=tile)
     tsim.write("v", pi.initial_velocity(cfg))
     tsim.step(args.warmup)
     t0 = tsim.status()
@@ -359,7 +360,7 @@ def main():
     if not args.no_adjoint:
         acfg = pi.config("adjoint_40x40x80")
         av0 = pi.initial_velocity(acfg)
-        asim = Simulation(acfg, precision="mixed", use_graph=False)
+        asim = Simulation(acfg, precision="mixed", use_graph=False, bond_tile=tile)
         asim.write("v", av0)
         ta = time.perf_counter()
         asim.adjoint_forward(acfg["steps"], acfg["ckpt_every"])
@@ -389,7 +390,7 @@ def main():
     from paper_2203_05562_gb300 import Simulation
     host_v0 = torch.from_numpy(pi.initial_velocity(cfg).astype(np.float32)).pin_memory()
     host_u = torch.empty((3, n), dtype=torch.float32).pin_memory()
-    esim = Simulation(cfg, precision="mixed")
+    esim = Simulation(cfg, precision="mixed", bond_tile=tile)
     esim.write("v", host_v0.numpy())
     esim.step(args.warmup)
     torch.cuda.synchronize()

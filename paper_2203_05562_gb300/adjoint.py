@@ -23,15 +23,16 @@ PARAMS = ("M", "eta", "suction", "pc0")
 class ColumnRun(torch.autograd.Function):
     """u_N = run(theta): n_steps explicit steps of one soil column from its
     initial state; backward runs the reverse sweep from checkpoints kept
-    every ckpt_every steps, recomputing the steps between them."""
+    every ckpt_every steps, recomputing the steps between them.  bond_tile
+    is the bond kernel's threads per point (32, 64, 128, 256)."""
 
     @staticmethod
-    def forward(ctx, theta, cfg, v0, n_steps, ckpt_every, precision="mixed"):
+    def forward(ctx, theta, cfg, v0, n_steps, ckpt_every, precision="mixed", bond_tile=128):
         vals = theta.detach().cpu().double().numpy()
         run_cfg = dict(cfg)
         for name, val in zip(PARAMS, vals):
             run_cfg[name] = float(val)
-        sim = Simulation(run_cfg, precision=precision, use_graph=False)
+        sim = Simulation(run_cfg, precision=precision, use_graph=False, bond_tile=bond_tile)
         if v0 is not None:
             sim.write("v", v0)
         sim.adjoint_forward(int(n_steps), int(ckpt_every))
@@ -43,7 +44,7 @@ class ColumnRun(torch.autograd.Function):
     def backward(ctx, grad_u):
         g = ctx.sim.adjoint_reverse(grad_u.detach().double().contiguous())
         ctx.sim = None
-        return torch.from_numpy(np.asarray(g)), None, None, None, None, None
+        return torch.from_numpy(np.asarray(g)), None, None, None, None, None, None
 
 
 def top_surface_runout(u: torch.Tensor, cfg: dict) -> torch.Tensor:
