@@ -203,7 +203,11 @@ __global__ void k_adj_pre(DevState<Real> s, AdjState<Real> a, StepConst k, int i
 }
 
 constexpr int kAdjThreads = 128;
-constexpr int kAdjSlots = 24;   // per-bond shared slots
+constexpr int kAdjSlots = 24;   // per-bond shared slots:
+constexpr int kSlTest = 0;      //   -2 zeta~_j (3) and hf^2 - |zeta~_j|^2: the membership test
+constexpr int kSlG = 4;         //   K~ sums (pass 1), then G = K~-bar + K~-bar^T (pass 2): 6
+constexpr int kSlAb = 10;       //   A~ sums (pass 1), then A~-bar (pass 2): 9
+constexpr int kSlCnt = 19, kSlAct = 20, kSlZown = 21;   // |S|, active, own zeta~-bar (3)
 
 template <typename Real>
 size_t adj_smem_bytes() {
@@ -215,7 +219,7 @@ size_t adj_smem_bytes() {
 // reverse it.  INITIAL: the state-preserving initial pass (no constitutive
 // update, positions fixed).
 template <typename Real, int MODEL, bool INITIAL>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, sizeof(Real) == 4 ? 4 : 2)
 k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
     constexpr bool F64 = sizeof(Real) == 8;
     constexpr int NW = kAdjThreads / 32;
@@ -336,9 +340,11 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
             cnt = (int)cntf;
         }
         Real* sb = s_b + (size_t)t * kAdjSlots;
-        sb[0] = K00; sb[1] = K11; sb[2] = K22; sb[3] = K12; sb[4] = K02; sb[5] = K01;
-        sb[6] = A00; sb[7] = A01; sb[8] = A02; sb[9] = A10; sb[10] = A11; sb[11] = A12;
-        sb[12] = A20; sb[13] = A21; sb[14] = A22;
+        sb[kSlG + 0] = K00; sb[kSlG + 1] = K11; sb[kSlG + 2] = K22;
+        sb[kSlG + 3] = K12; sb[kSlG + 4] = K02; sb[kSlG + 5] = K01;
+        sb[kSlAb + 0] = A00; sb[kSlAb + 1] = A01; sb[kSlAb + 2] = A02;
+        sb[kSlAb + 3] = A10; sb[kSlAb + 4] = A11; sb[kSlAb + 5] = A12;
+        sb[kSlAb + 6] = A20; sb[kSlAb + 7] = A21; sb[kSlAb + 8] = A22;
         Real Kid[6];
         bool active = cnt >= 3;
         if constexpr (F64) {
@@ -347,9 +353,9 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
         } else {
             active = active && inverse_sym_mixed(K00, K11, K22, K12, K02, K01, Kid);
         }
-        sb[15] = (Real)cnt;
-        sb[16] = active ? (Real)1 : (Real)0;
-        sb[18] = mjx; sb[19] = mjy; sb[20] = mjz; sb[21] = thj;
+        sb[kSlCnt] = (Real)cnt;
+        sb[kSlAct] = active ? (Real)1 : (Real)0;
+        sb[kSlTest + 0] = mjx; sb[kSlTest + 1] = mjy; sb[kSlTest + 2] = mjz; sb[kSlTest + 3] = thj;
         if (active) wpart[0] += (Real)cnt * inv_nb;
     }
     block_sum<1, Real>(wpart, reinterpret_cast<Real(*)[1]>(&s_red[0][0]));
@@ -368,22 +374,25 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
     double Mb = 0.0, etab = 0.0, Srsb = 0.0;
     for (int t = threadIdx.x; t < nb; t += kAdjThreads) {
         Real* sb = s_b + (size_t)t * kAdjSlots;
-        const bool active = sb[16] != (Real)0;
+        const bool active = sb[kSlAct] != (Real)0;
         const R4<Real> zj = s_z[t];
         Real Kid[6];
         if (active) {
             if constexpr (F64) {
-                const double Kd[6] = {sb[0], sb[1], sb[2], sb[3], sb[4], sb[5]};
+                const double Kd[6] = {sb[kSlG + 0], sb[kSlG + 1], sb[kSlG + 2],
+                                      sb[kSlG + 3], sb[kSlG + 4], sb[kSlG + 5]};
                 inverse_sym_fp64(Kd, Kid);
             } else {
-                inverse_sym_mixed(sb[0], sb[1], sb[2], sb[3], sb[4], sb[5], Kid);
+                inverse_sym_mixed(sb[kSlG + 0], sb[kSlG + 1], sb[kSlG + 2], sb[kSlG + 3],
+                                  sb[kSlG + 4], sb[kSlG + 5], Kid);
             }
         }
         Real G[6] = {0, 0, 0, 0, 0, 0}, Ab[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, zown[3] = {0, 0, 0};
         if (active) {
             const Real Ki[9] = {Kid[0], Kid[5], Kid[4], Kid[5], Kid[1], Kid[3], Kid[4], Kid[3], Kid[2]};
-            const Real varpi = sb[15] * inv_nb;
-            const Real A[9] = {sb[6], sb[7], sb[8], sb[9], sb[10], sb[11], sb[12], sb[13], sb[14]};
+            const Real varpi = sb[kSlCnt] * inv_nb;
+            const Real A[9] = {sb[kSlAb + 0], sb[kSlAb + 1], sb[kSlAb + 2], sb[kSlAb + 3], sb[kSlAb + 4],
+                               sb[kSlAb + 5], sb[kSlAb + 6], sb[kSlAb + 7], sb[kSlAb + 8]};
             Real L[9];
 #pragma unroll
             for (int r = 0; r < 3; r++)
@@ -468,53 +477,72 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
         if constexpr (!INITIAL) {
             // sender data for the receiver pass (reuses the slots of the sums)
 #pragma unroll
-            for (int e = 0; e < 6; e++) sb[e] = G[e];
+            for (int e = 0; e < 6; e++) sb[kSlG + e] = G[e];
 #pragma unroll
-            for (int e = 0; e < 9; e++) sb[6 + e] = Ab[e];
+            for (int e = 0; e < 9; e++) sb[kSlAb + e] = Ab[e];
         }
-        sb[22] = zown[0];
-        sb[23] = zown[1];
-        sb[17] = zown[2];
+        sb[kSlZown + 0] = zown[0];
+        sb[kSlZown + 1] = zown[1];
+        sb[kSlZown + 2] = zown[2];
     }
     __syncthreads();
 
     Real zs[6] = {0, 0, 0, 0, 0, 0};   // sums over the row of the position / velocity adjoints
     if constexpr (!INITIAL) {
-        // pass 3: receiver t gathers from every sender q whose sub-horizon holds it
+        // pass 3: receiver t gathers from every sender q whose sub-horizon holds
+        // it: zeta~-bar += G zeta~_t + Ab^T Ydot_t and Ydot-bar += Ab zeta~_t,
+        // with G and Ab first summed over those senders
         for (int t = threadIdx.x; t < nb; t += kAdjThreads) {
             const R4<Real> zt = s_z[t];
             const R4<Real> yt = s_y[t];
             const Real* sbt = s_b + (size_t)t * kAdjSlots;
-            Real Zb[3] = {sbt[22], sbt[23], sbt[17]};
-            Real Yb[3] = {0, 0, 0};
-            for (int q = 0; q < nb; q++) {
-                const Real* sq = s_b + (size_t)q * kAdjSlots;
-                bool member = true;
-                if constexpr (MODEL != 1) {
-                    if constexpr (F64) {
+            Real Gs[6] = {0, 0, 0, 0, 0, 0}, As[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if constexpr (!F64 && MODEL != 1) {
+                // the sender's own membership test, same operands and rounding
+                float Gf[6] = {0, 0, 0, 0, 0, 0}, Af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 2
+                for (int q = 0; q < nb; q++) {
+                    const float* sq = s_b + (size_t)q * kAdjSlots;
+                    const float4 m = *reinterpret_cast<const float4*>(sq + kSlTest);
+                    const float4 g0 = *reinterpret_cast<const float4*>(sq + 4);
+                    const float4 g1 = *reinterpret_cast<const float4*>(sq + 8);
+                    const float4 g2 = *reinterpret_cast<const float4*>(sq + 12);
+                    const float4 g3 = *reinterpret_cast<const float4*>(sq + 16);
+                    const float tst = zt.x * m.x + (zt.y * m.y + (zt.z * m.z + zt.w));
+                    masked_add15(tst, m.w, g0, g1, g2, g3, Gf, Af);
+                }
+#pragma unroll
+                for (int e = 0; e < 6; e++) Gs[e] = Gf[e];
+#pragma unroll
+                for (int e = 0; e < 9; e++) As[e] = Af[e];
+            } else {
+                for (int q = 0; q < nb; q++) {
+                    const Real* sq = s_b + (size_t)q * kAdjSlots;
+                    bool member = true;
+                    if constexpr (MODEL != 1) {
                         const double d0 = __dsub_rn(s_p[t], s_p[q]);
                         const double d1 = __dsub_rn(s_p[kMaxRow + t], s_p[kMaxRow + q]);
                         const double d2 = __dsub_rn(s_p[2 * kMaxRow + t], s_p[2 * kMaxRow + q]);
                         member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
                                            __dmul_rn(d2, d2)) <= k.delta2;
-                    } else {
-                        const float tst = zt.x * sq[18] + (zt.y * sq[19] + (zt.z * sq[20] + zt.w));
-                        member = tst <= sq[21];
+                    }
+                    if (member) {
+#pragma unroll
+                        for (int e = 0; e < 6; e++) Gs[e] += sq[kSlG + e];
+#pragma unroll
+                        for (int e = 0; e < 9; e++) As[e] += sq[kSlAb + e];
                     }
                 }
-                if (member) {
-                    // zeta~-bar += G zeta~ + Ab^T Ydot;  Ydot-bar += Ab zeta~
-                    Zb[0] += sq[0] * zt.x + sq[5] * zt.y + sq[4] * zt.z +
-                             sq[6] * yt.x + sq[9] * yt.y + sq[12] * yt.z;
-                    Zb[1] += sq[5] * zt.x + sq[1] * zt.y + sq[3] * zt.z +
-                             sq[7] * yt.x + sq[10] * yt.y + sq[13] * yt.z;
-                    Zb[2] += sq[4] * zt.x + sq[3] * zt.y + sq[2] * zt.z +
-                             sq[8] * yt.x + sq[11] * yt.y + sq[14] * yt.z;
-                    Yb[0] += sq[6] * zt.x + sq[7] * zt.y + sq[8] * zt.z;
-                    Yb[1] += sq[9] * zt.x + sq[10] * zt.y + sq[11] * zt.z;
-                    Yb[2] += sq[12] * zt.x + sq[13] * zt.y + sq[14] * zt.z;
-                }
             }
+            // G holds (00, 11, 22, 12, 02, 01); Ab is row-major
+            Real Zb[3] = {sbt[kSlZown + 0], sbt[kSlZown + 1], sbt[kSlZown + 2]};
+            Zb[0] += Gs[0] * zt.x + Gs[5] * zt.y + Gs[4] * zt.z + As[0] * yt.x + As[3] * yt.y + As[6] * yt.z;
+            Zb[1] += Gs[5] * zt.x + Gs[1] * zt.y + Gs[3] * zt.z + As[1] * yt.x + As[4] * yt.y + As[7] * yt.z;
+            Zb[2] += Gs[4] * zt.x + Gs[3] * zt.y + Gs[2] * zt.z + As[2] * yt.x + As[5] * yt.y + As[8] * yt.z;
+            Real Yb[3];
+            Yb[0] = As[0] * zt.x + As[1] * zt.y + As[2] * zt.z;
+            Yb[1] = As[3] * zt.x + As[4] * zt.y + As[5] * zt.z;
+            Yb[2] = As[6] * zt.x + As[7] * zt.y + As[8] * zt.z;
             // zeta~ = (x_k - x_i) / dx: position adjoint of the neighbour
 #pragma unroll
             for (int c = 0; c < 3; c++) Zb[c] *= inv_dx;
@@ -611,13 +639,20 @@ k_adj_post(DevState<Real> s, AdjState<Real> a, StepConst k) {
 // deterministic sums: acc[0..2] += sum over points of thpart; when
 // with_state (after the initial pass), acc[3] = sum tr(sigma0-bar) and
 // acc[4] = sum pc0-bar
+// per-step sums of the parameter partials (and, for the initial pass, of
+// the state adjoints): a fixed chunk of points per block, then the blocks'
+// partials in order, so the result does not depend on scheduling
 template <typename Real>
-__global__ void k_adj_reduce(AdjState<Real> a, int npoints, double* acc, int with_state) {
+__global__ void __launch_bounds__(256)
+k_adj_reduce_part(AdjState<Real> a, int npoints, double* part, int with_state) {
     __shared__ double sm[5][256];
     double t[5] = {0, 0, 0, 0, 0};
     const size_t n = (size_t)npoints;
-    for (int p = threadIdx.x; p < npoints; p += blockDim.x) {
-        for (int e = 0; e < 3; e++) t[e] += a.thpart[(size_t)p * 3 + e];
+    const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const size_t p0 = (size_t)blockIdx.x * chunk;
+    const size_t p1 = p0 + chunk < n ? p0 + chunk : n;
+    for (size_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        for (int e = 0; e < 3; e++) t[e] += a.thpart[p * 3 + e];
         if (with_state) {
             t[3] += (double)a.sbn[p] + (double)a.sbn[n + p] + (double)a.sbn[2 * n + p];
             t[4] += (double)a.pcbn[p];
@@ -630,10 +665,16 @@ __global__ void k_adj_reduce(AdjState<Real> a, int npoints, double* acc, int wit
             for (int e = 0; e < 5; e++) sm[e][threadIdx.x] += sm[e][threadIdx.x + wdt];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        for (int e = 0; e < 3; e++) acc[e] += sm[e][0];
-        if (with_state) { acc[3] = sm[3][0]; acc[4] = sm[4][0]; }
-    }
+    if (threadIdx.x < 5) part[(size_t)blockIdx.x * 5 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_adj_reduce_final(const double* part, int nparts, double* acc, int with_state) {
+    const int e = threadIdx.x;
+    if (e >= 5) return;
+    double t = 0.0;
+    for (int b = 0; b < nparts; b++) t += part[(size_t)b * 5 + e];
+    if (e < 3) acc[e] += t;
+    else if (with_state) acc[e] = t;
 }
 
 template <typename Real>
@@ -667,7 +708,9 @@ cudaError_t launch_adjoint_step(const DevState<Real>& s, const AdjState<Real>& a
                            kWarpPointsPerBlock * 32, 0, st>>>(s, a, k);
     }
 #undef PPM_ADJ
-    k_adj_reduce<Real><<<1, 256, 0, st>>>(a, n, acc, initial);
+    double* part = acc + kAdjAccDoubles;
+    k_adj_reduce_part<Real><<<kAdjRedBlocks, 256, 0, st>>>(a, n, part, initial);
+    k_adj_reduce_final<<<1, 32, 0, st>>>(part, kAdjRedBlocks, acc, initial);
     return cudaGetLastError();
 }
 

@@ -139,13 +139,15 @@ __device__ __noinline__ int return_map(const ReturnConst& R, double tol, int max
     }
 }
 
-// Mixed path, near the apex: FP64 Newton refinement of the FP32 root.  The
-// residual is Eq. 73-75 as above with the divisions by M^2, pc_n and
-// lambda - kappa taken as products with reciprocals; each step's residual is also its
-// convergence test, so a start within the FP32 tolerance costs one Jacobian
-// and two residuals.  A step is accepted only if the residual is finite and
-// its 2-norm decreases; returns 0 (the caller then solves from the trial
-// state) otherwise, or after max_iter steps.
+// Mixed path, near the apex: iterative refinement of the FP32 root in FP64.
+// Each step evaluates the residual of Eq. 73-75 in FP64 (as above, with the
+// divisions by M^2, pc_n and lambda - kappa taken as products with
+// reciprocals) and corrects x by the FP32 Jacobian's solve, which the FP32
+// Newton formed at its root; the iteration contracts by about the FP32
+// rounding of that Jacobian per step, so a start within the FP32 tolerance
+// reaches the FP64 tolerance in one or two steps.  A step is accepted only
+// if the residual is finite and its 2-norm decreases; returns 0 (the caller
+// then solves from the trial state in FP64) otherwise, or after max_iter.
 __device__ __forceinline__ void refine_residual(const ReturnConst& R, double inv_M2, double inv_pcn,
                                                 double g, const double x[3], double r[3]) {
     const double pb = x[0], q = x[1], pc = x[2];
@@ -158,37 +160,28 @@ __device__ __forceinline__ void refine_residual(const ReturnConst& R, double inv
 }
 
 __device__ __noinline__ int return_refine64(const ReturnConst& R, double tol, int max_iter,
-                                            double x[3]) {
+                                            double x[3], const float Jf[9]) {
+    // inverse of the FP32 Jacobian by its adjugate
+    const float m0 = Jf[4] * Jf[8] - Jf[5] * Jf[7];
+    const float m1 = Jf[5] * Jf[6] - Jf[3] * Jf[8];
+    const float m2 = Jf[3] * Jf[7] - Jf[4] * Jf[6];
+    const float det = Jf[0] * m0 + Jf[1] * m1 + Jf[2] * m2;
+    if (det == 0.0f || !isfinite(det)) return 0;
+    const float id = __frcp_rn(det);
+    const float Ji[9] = {m0 * id, (Jf[2] * Jf[7] - Jf[1] * Jf[8]) * id, (Jf[1] * Jf[5] - Jf[2] * Jf[4]) * id,
+                         m1 * id, (Jf[0] * Jf[8] - Jf[2] * Jf[6]) * id, (Jf[2] * Jf[3] - Jf[0] * Jf[5]) * id,
+                         m2 * id, (Jf[1] * Jf[6] - Jf[0] * Jf[7]) * id, (Jf[0] * Jf[4] - Jf[1] * Jf[3]) * id};
     const double inv_M2 = 1.0 / R.M2, inv_pcn = 1.0 / R.pc_n, g = R.c / R.lk;
-    const double a = R.K * R.c * R.inv_scale, b = 3.0 * R.mu * R.c * R.inv_scale;
     double r[3];
     refine_residual(R, inv_M2, inv_pcn, g, x, r);
     if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) return 0;
     for (int it = 0; it < max_iter; it++) {
         if (fmax(fabs(r[0]), fmax(fabs(r[1]), fabs(r[2]))) <= tol) return 1;
-        const double pb = x[0], q = x[1], pc = x[2];
-        const double f = q * q * inv_M2 + pb * (pb - pc);
-        const double fp = 2.0 * pb - pc, fq = 2.0 * q * inv_M2, fc = -pb;
-        double J[9];
-        J[0] = R.inv_scale + a * (fp * fp + 2.0 * f);
-        J[1] = a * fq * fp;
-        J[2] = a * (fc * fp - f);
-        J[3] = b * fp * fq;
-        J[4] = R.inv_scale + b * (fq * fq + 2.0 * f * inv_M2);
-        J[5] = b * fc * fq;
-        J[6] = g * (fp * fp + 2.0 * f);
-        J[7] = g * (fq * fp);
-        J[8] = 1.0 / pc + g * (fc * fp - f);
-        const double m0 = J[4] * J[8] - J[5] * J[7];
-        const double m1 = J[3] * J[8] - J[5] * J[6];
-        const double m2 = J[3] * J[7] - J[4] * J[6];
-        const double det = J[0] * m0 - J[1] * m1 + J[2] * m2;
-        if (det == 0.0 || !isfinite(det)) return 0;
-        const double id = 1.0 / det;
+        const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
         double xt[3], rt[3];
-        xt[0] = x[0] - (r[0] * m0 - J[1] * (r[1] * J[8] - J[5] * r[2]) + J[2] * (r[1] * J[7] - J[4] * r[2])) * id;
-        xt[1] = x[1] - (J[0] * (r[1] * J[8] - J[5] * r[2]) - r[0] * m1 + J[2] * (J[3] * r[2] - r[1] * J[6])) * id;
-        xt[2] = x[2] - (J[0] * (J[4] * r[2] - r[1] * J[7]) - J[1] * (J[3] * r[2] - r[1] * J[6]) + r[0] * m2) * id;
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+            xt[q] = x[q] - (double)(Ji[q * 3 + 0] * rf[0] + Ji[q * 3 + 1] * rf[1] + Ji[q * 3 + 2] * rf[2]);
         refine_residual(R, inv_M2, inv_pcn, g, xt, rt);
         if (!(isfinite(rt[0]) && isfinite(rt[1]) && isfinite(rt[2])) ||
             !(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2] < r[0] * r[0] + r[1] * r[1] + r[2] * r[2]))
@@ -239,33 +232,40 @@ __device__ __forceinline__ void return_residual_f(const ReturnConstF& R, const f
     }
 }
 
-__device__ __noinline__ int return_map_f32(const ReturnConstF& R, float x[3]) {
+__device__ __noinline__ int return_map_f32(const ReturnConstF& R, float x[3], float Jo[9]) {
     x[0] = 0.0f; x[1] = 0.0f; x[2] = 0.0f;
     float r[3], J[9];
     for (int it = 0;; it++) {
         return_residual_f<true>(R, x, r, J);
-        if (fmaxf(fabsf(r[0]), fmaxf(fabsf(r[1]), fabsf(r[2]))) <= R.tol) return 1;
+        if (fmaxf(fabsf(r[0]), fmaxf(fabsf(r[1]), fabsf(r[2]))) <= R.tol) {
+            for (int e = 0; e < 9; e++) Jo[e] = J[e];
+            return 1;
+        }
         if (it >= R.max_iter) return 0;
         const float m0 = J[4] * J[8] - J[5] * J[7];
         const float m1 = J[3] * J[8] - J[5] * J[6];
         const float m2 = J[3] * J[7] - J[4] * J[6];
         const float det = J[0] * m0 - J[1] * m1 + J[2] * m2;
         if (det == 0.0f || !isfinite(det)) return 0;
-        const float id = 1.0f / det;
+        const float id = __frcp_rn(det);
         float dx[3];
         dx[0] = (r[0] * m0 - J[1] * (r[1] * J[8] - J[5] * r[2]) + J[2] * (r[1] * J[7] - J[4] * r[2])) * id;
         dx[1] = (J[0] * (r[1] * J[8] - J[5] * r[2]) - r[0] * m1 + J[2] * (J[3] * r[2] - r[1] * J[6])) * id;
         dx[2] = (J[0] * (J[4] * r[2] - r[1] * J[7]) - J[1] * (J[3] * r[2] - r[1] * J[6]) + r[0] * m2) * id;
         const float small = 2e-7f * R.scale;
-        if (fabsf(dx[0]) <= small && fabsf(dx[1]) <= small && fabsf(dx[2]) <= small) return 1;
-        const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (fabsf(dx[0]) <= small && fabsf(dx[1]) <= small && fabsf(dx[2]) <= small) {
+            for (int e = 0; e < 9; e++) Jo[e] = J[e];
+            return 1;
+        }
+        // backtracking on the squared 2-norm of the residual
+        const float rn2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
         float lam = 1.0f, xt[3], rt[3];
         bool accepted = false;
         for (int ls = 0; ls < 20; ls++) {
             for (int q = 0; q < 3; q++) xt[q] = x[q] - lam * dx[q];
             return_residual_f<false>(R, xt, rt, nullptr);
             if (isfinite(rt[0]) && isfinite(rt[1]) && isfinite(rt[2]) &&
-                sqrtf(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]) < rn) {
+                rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2] < rn2) {
                 accepted = true;
                 break;
             }
@@ -372,8 +372,10 @@ __device__ __forceinline__ bool material_trial(const Real L[9], const Real sn[6]
 
 // Plastic part: the visco-plastic return from the trial stress st (Eq. 42-46,
 // 70-76) and the radial scaling of its deviator; o.des is left to the caller.
+// Kept out of line: it runs for a minority of bonds, and as a call its
+// register needs do not constrain the bond pass around it.
 template <typename Real>
-__device__ __forceinline__ void material_return(const Real st[6], Real pc_n, const StepConst& k,
+__device__ __noinline__ void material_return(const Real st[6], Real pc_n, const StepConst& k,
                                                 double M, float Mf, BondStress<Real>& o,
                                                 MatTrace<Real>* trace = nullptr) {
     constexpr bool F64 = sizeof(Real) == 8;
@@ -388,6 +390,7 @@ __device__ __forceinline__ void material_return(const Real st[6], Real pc_n, con
     bool need64 = F64;
     bool warm = false;
     double x64[3] = {0.0, 0.0, 0.0};
+    float Jf64[9];   // the FP32 Jacobian at the FP32 root, for the refinement
     if constexpr (!F64) {
         // FP32 return first.  Near the critical-state apex (mean stress within
         // 5% of the preconsolidation pressure from zero, or tensile) or where
@@ -410,14 +413,16 @@ __device__ __forceinline__ void material_return(const Real st[6], Real pc_n, con
             R.inv_scale = 1.0f / scale;
             R.tol = fmaxf((float)k.tol, 2e-6f);
             R.max_iter = k.max_iter;
-            float x[3];
-            if (return_map_f32(R, x)) {
+            float x[3], Jf[9];
+            if (return_map_f32(R, x, Jf)) {
                 p_new = p_tr + x[0];
                 q_new = q_tr + x[1];
                 pc_new = pc_n + x[2];
                 o.nonconv = 0;
                 if (near_apex) {
                     need64 = warm = true;
+#pragma unroll
+                    for (int e = 0; e < 9; e++) Jf64[e] = Jf[e];
                     x64[0] = (double)p_tr + (double)x[0];
                     x64[1] = (double)q_tr + (double)x[1];
                     x64[2] = (double)pc_n + (double)x[2];
@@ -440,7 +445,7 @@ __device__ __forceinline__ void material_return(const Real st[6], Real pc_n, con
         if (scale < 1.0) scale = 1.0;
         R.inv_scale = 1.0 / scale;
         double x[3] = {x64[0], x64[1], x64[2]};
-        int ok = warm ? return_refine64(R, k.tol, k.max_iter, x) : 0;
+        int ok = warm ? return_refine64(R, k.tol, k.max_iter, x, Jf64) : 0;
         if (!ok) ok = return_map(R, k.tol, k.max_iter, x);
         o.nonconv = !ok;
         o.ret64 = 1;
@@ -540,6 +545,37 @@ __device__ __forceinline__ void masked_add9(float tst, float thr, const float4& 
           "+f"(N[7]), "+f"(N[8])
         : "f"(tst), "f"(m0.x), "f"(m0.y), "f"(m0.z), "f"(m0.w), "f"(m1.x), "f"(m1.y), "f"(m1.z),
           "f"(m1.w), "f"(m8), "f"(thr));
+}
+
+// Predicated sum of a sender's 6 + 9 adjoint terms (G in g0, g1.xy; Ab in
+// g1.zw, g2, g3.xyz) into G, A when tst <= thr.
+__device__ __forceinline__ void masked_add15(float tst, float thr, const float4& g0,
+                                             const float4& g1, const float4& g2,
+                                             const float4& g3, float (&G)[6], float (&A)[9]) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.f32 p, %15, %16;\n\t"
+        "@p add.f32 %0, %0, %17;\n\t"
+        "@p add.f32 %1, %1, %18;\n\t"
+        "@p add.f32 %2, %2, %19;\n\t"
+        "@p add.f32 %3, %3, %20;\n\t"
+        "@p add.f32 %4, %4, %21;\n\t"
+        "@p add.f32 %5, %5, %22;\n\t"
+        "@p add.f32 %6, %6, %23;\n\t"
+        "@p add.f32 %7, %7, %24;\n\t"
+        "@p add.f32 %8, %8, %25;\n\t"
+        "@p add.f32 %9, %9, %26;\n\t"
+        "@p add.f32 %10, %10, %27;\n\t"
+        "@p add.f32 %11, %11, %28;\n\t"
+        "@p add.f32 %12, %12, %29;\n\t"
+        "@p add.f32 %13, %13, %30;\n\t"
+        "@p add.f32 %14, %14, %31;\n\t"
+        "}"
+        : "+f"(G[0]), "+f"(G[1]), "+f"(G[2]), "+f"(G[3]), "+f"(G[4]), "+f"(G[5]),
+          "+f"(A[0]), "+f"(A[1]), "+f"(A[2]), "+f"(A[3]), "+f"(A[4]), "+f"(A[5]), "+f"(A[6]),
+          "+f"(A[7]), "+f"(A[8])
+        : "f"(tst), "f"(thr), "f"(g0.x), "f"(g0.y), "f"(g0.z), "f"(g0.w), "f"(g1.x), "f"(g1.y),
+          "f"(g1.z), "f"(g1.w), "f"(g2.x), "f"(g2.y), "f"(g2.z), "f"(g2.w), "f"(g3.x), "f"(g3.y),
+          "f"(g3.z));
 }
 
 // deterministic block sum: butterfly within warps, then warps in order

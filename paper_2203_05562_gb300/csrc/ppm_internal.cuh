@@ -11,6 +11,8 @@ namespace ppm {
 constexpr int kMaxRow = 256;          // hard cap of bonds per point (smem staging)
 constexpr int kDefaultMaxFamily = 192;
 constexpr int kWarpPointsPerBlock = 8;  // family / gather kernels: one warp per point
+constexpr int kAdjAccDoubles = 32;     // adjoint accumulators (gradient, state sums) ...
+constexpr int kAdjRedBlocks = 152;     // ... followed by 5 partial sums per reduction block
 constexpr int kLatBits = 10;          // packed lattice index: ix | iy << 10 | iz << 20
 constexpr int kLatMask = (1 << kLatBits) - 1;
 

@@ -446,7 +446,7 @@ AdjLayout adj_layout(const ppm_ctx* c, int n_steps, int every) {
     L.off_ctr = off; off += align_up(sizeof(DevCounters), 256);
     L.off_adj = off;
     off += adj_region_bytes(f64, n, cap);
-    L.off_acc = off; off += 256;
+    L.off_acc = off; off += align_up(sizeof(double) * (kAdjAccDoubles + 5 * kAdjRedBlocks), 256);
     L.total = off;
     (void)mixed;
     return L;
