@@ -86,6 +86,15 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     const int li = s.lat[i];
     const int ix = lat_x(li), iy = lat_y(li), iz = lat_z(li);
     const Real inv_dx = F64 ? (Real)k.inv_dx : (Real)k.inv_dxf;
+    // the point's state and column constants, issued before the family
+    // gathers so that their latencies overlap
+    Real sig_i[6];
+#pragma unroll
+    for (int c = 0; c < 6; c++) sig_i[c] = s.sig[c * n + i];
+    const Real pc_i = s.pc[i];
+    const Real eps_i = s.eps[i];
+    const ColumnConst cc = s.cols[s.colid[i]];
+    const Real Srs = F64 ? (Real)cc.Srs : (Real)cc.Srsf;
 
     // stage the family of i: bond vectors and relative velocities
     double pxi = 0, pyi = 0, pzi = 0;
@@ -123,12 +132,6 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     }
     __syncthreads();
 
-    Real sig_i[6];
-#pragma unroll
-    for (int c = 0; c < 6; c++) sig_i[c] = s.sig[c * n + i];
-    const Real pc_i = s.pc[i];
-    const ColumnConst cc = s.cols[s.colid[i]];
-    const Real Srs = F64 ? (Real)cc.Srs : (Real)cc.Srsf;
     const Real hf2 = (Real)k.hf2f;
     const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
 
@@ -140,6 +143,9 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 
     for (int t = threadIdx.x; t < nb; t += TPP) {
         const R4<Real> zj = s_z[t];
+        // the bond's reverse slot, loaded now so that its latency is hidden by the sums
+        int rb = -1;
+        if constexpr (MODEL != 2) rb = s.rev[r0 + t];
         // mixed-path test |z_k - z_j|^2 <= hf^2 as
         // |z_k|^2 - 2 z_k.z_j <= hf^2 - |z_j|^2 (threshold thj per bond)
         const Real mjx = (Real)-2 * zj.x, mjy = (Real)-2 * zj.y, mjz = (Real)-2 * zj.z;
@@ -205,7 +211,6 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 s.T[r0 + t] = (Real)0;
                 s.T[k.cap + r0 + t] = (Real)0;
                 s.T[2 * k.cap + r0 + t] = (Real)0;
-                const int rb = s.rev[r0 + t];
                 if (rb >= 0) {
                     s.Trev[rb] = (Real)0;
                     s.Trev[k.cap + rb] = (Real)0;
@@ -298,7 +303,6 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;
-            const int rb = s.rev[r0 + t];
             if (rb >= 0) {
                 s.Trev[rb] = T0;
                 s.Trev[k.cap + rb] = T1;
@@ -328,6 +332,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         const Real inv_w = w > (Real)0 ? (Real)1 / w : (Real)0;
         for (int t = threadIdx.x; t < nb; t += TPP) {
             const R4<Real> zt = s_z[t];
+            const int rb = s.rev[r0 + t];     // loaded before the member loop hides its latency
             double ptx = 0, pty = 0, ptz = 0;
             if constexpr (F64) { ptx = s_p[0][t]; pty = s_p[F64 ? 1 : 0][t]; ptz = s_p[F64 ? 2 : 0][t]; }
             Real N[9];
@@ -366,7 +371,6 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;
-            const int rb = s.rev[r0 + t];
             if (rb >= 0) {
                 s.Trev[rb] = T0;
                 s.Trev[k.cap + rb] = T1;
@@ -386,7 +390,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 #pragma unroll
             for (int c = 0; c < 6; c++) s.sig[c * n + i] = red[1 + c] * iw;
             s.pc[i] = red[7] * iw;
-            s.eps[i] = s.eps[i] + red[8] * iw;
+            s.eps[i] = eps_i + red[8] * iw;
         }
         s.tsum[i] = red[9];
         s.tsum[n + i] = red[10];

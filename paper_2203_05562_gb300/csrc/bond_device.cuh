@@ -578,7 +578,9 @@ __device__ __forceinline__ void masked_add15(float tst, float thr, const float4&
           "f"(g3.z));
 }
 
-// deterministic block sum: butterfly within warps, then warps in order
+// deterministic block sum: butterfly within warps, then warps in order.  The
+// butterfly leaves every lane with the same bits (each stage adds the same two
+// operands on both partners), so a one-warp block needs nothing more.
 template <int NV, typename T>
 __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sm)[NV]) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -586,6 +588,7 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sm)[NV]) {
     for (int e = 0; e < NV; e++)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], off);
+    if (blockDim.x == 32) return;
     if (lane == 0)
 #pragma unroll
         for (int e = 0; e < NV; e++) sm[w][e] = v[e];
