@@ -367,6 +367,15 @@ def main():
     # ---- adjoint: 40x40x80 column, 200 steps, checkpoints every 20 ----
     adj = None
     if not args.no_adjoint:
+        # warm-up: a two-step adjoint on a small column loads the adjoint's
+        # kernels (modules load lazily, on first launch; about 1.4 s here)
+        wcfg = pi.small_config(5, 5, 7, suction=50e3)
+        wsim = Simulation(wcfg, precision="mixed", use_graph=False, bond_tile=tile)
+        wsim.write("v", pi.initial_velocity(wcfg, std=1e-3, seed=1))
+        wsim.adjoint_forward(2, 1)
+        wsim.adjoint_reverse(np.zeros((3, wsim.n)))
+        torch.cuda.synchronize()
+        del wsim
         acfg = pi.config("adjoint_40x40x80")
         av0 = pi.initial_velocity(acfg)
         asim = Simulation(acfg, precision="mixed", use_graph=False, bond_tile=tile)
