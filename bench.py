@@ -241,6 +241,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--standard-steps", type=int, default=100)
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -403,6 +404,14 @@ def main():
     fp64_rate = fig64["bond_steps"] / (fig64["ms"] * 1e-3)
     del sim64
 
+    # ---- standard correspondence (model 1) on the same column ----
+    simS, figS = time_path(dict(cfg, model=1), "mixed", args.standard_steps, args.warmup, barrier)
+    standard = {"model": "standard correspondence (every sub-horizon is the family)",
+                "value": figS["bond_steps"] / (figS["ms"] * 1e-3), "unit": UNIT,
+                "steps": args.standard_steps, "ms_per_step": figS["ms"] / args.standard_steps,
+                "bond_tile": figS["status"]["bond_tile"]}
+    del simS
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     from paper_2203_05562_gb300 import Simulation
@@ -459,7 +468,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
-            "hbm": hbm,
+            "hbm": hbm, "standard_model": standard,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "large": large, "adjoint": adj,
             "clocks": clocks, "gpu_launches": fig["launches"],

@@ -141,6 +141,120 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     for (int e = 0; e < 12; e++) red[e] = (Real)0;
     unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
 
+    if constexpr (MODEL == 1) {
+        // standard correspondence (Sec. 2.1): every bond's sub-horizon is the
+        // whole family, so K~, A~, L, the updated stress and the force-state
+        // matrix belong to the point.  Each warp sums the family with its 32
+        // lanes (lane l takes members l, l + 32, ...) and a butterfly, which
+        // leaves the same bits in every lane of every warp whatever the tile;
+        // every thread then applies the point's result to its bonds.
+        Real Ks[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int q = (int)(threadIdx.x & 31); q < nb; q += 32) {
+            const R4<Real> zk = s_z[q];
+            const R4<Real> yk = s_y[q];
+            Ks[0] += zk.x * zk.x; Ks[1] += zk.y * zk.y; Ks[2] += zk.z * zk.z;
+            Ks[3] += zk.y * zk.z; Ks[4] += zk.x * zk.z; Ks[5] += zk.x * zk.y;
+            Ks[6] += yk.x * zk.x; Ks[7] += yk.x * zk.y; Ks[8] += yk.x * zk.z;
+            Ks[9] += yk.y * zk.x; Ks[10] += yk.y * zk.y; Ks[11] += yk.y * zk.z;
+            Ks[12] += yk.z * zk.x; Ks[13] += yk.z * zk.y; Ks[14] += yk.z * zk.z;
+        }
+#pragma unroll
+        for (int e = 0; e < 15; e++)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) Ks[e] += __shfl_xor_sync(0xffffffffu, Ks[e], off);
+        const Real K00 = Ks[0], K11 = Ks[1], K22 = Ks[2], K12 = Ks[3], K02 = Ks[4], K01 = Ks[5];
+        const Real A00 = Ks[6], A01 = Ks[7], A02 = Ks[8], A10 = Ks[9], A11 = Ks[10], A12 = Ks[11];
+        const Real A20 = Ks[12], A21 = Ks[13], A22 = Ks[14];
+        const int cnt = nb;
+        Real Kid[6];
+        bool active = cnt >= 3;
+        if constexpr (F64) {
+            const double Kd[6] = {K00, K11, K22, K12, K02, K01};
+            active = active && inverse_sym_fp64(Kd, Kid);
+        } else {
+            active = active && inverse_sym_mixed(K00, K11, K22, K12, K02, K01, Kid);
+        }
+        const Real varpi = (Real)cnt * inv_nb;              // Eq. 55 (= 1)
+        BondStress<Real> bs;
+        bs.plastic = 0; bs.nonconv = 0; bs.ret64 = 0;
+        Real SK[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (active) {
+            const Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
+                                (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
+                                (Real)Kid[4], (Real)Kid[3], (Real)Kid[2]};
+            if (with_dt) {
+                const Real A[9] = {A00, A01, A02, A10, A11, A12, A20, A21, A22};
+                Real L[9];
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
+                                        A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
+                Real st[6], des;
+                if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
+                    material_return<Real>(st, pc_i, k, cc.M, cc.Mf, bs);
+                    bs.des = des;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 6; c++) bs.sig[c] = st[c];
+                    bs.pc = pc_i;
+                    bs.des = des;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; c++) bs.sig[c] = sig_i[c];
+                bs.pc = pc_i;
+                bs.des = (Real)0;
+            }
+            const Real S[9] = {bs.sig[0] + Srs, bs.sig[5], bs.sig[4],
+                               bs.sig[5], bs.sig[1] + Srs, bs.sig[3],
+                               bs.sig[4], bs.sig[3], bs.sig[2] + Srs};
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    SK[r * 3 + c] = varpi * (S[r * 3 + 0] * Ki[0 * 3 + c] + S[r * 3 + 1] * Ki[1 * 3 + c] +
+                                             S[r * 3 + 2] * Ki[2 * 3 + c]);
+        }
+        for (int t = threadIdx.x; t < nb; t += TPP) {
+            const int rb = s.rev[r0 + t];
+            n_pairs += cnt;
+            if (!active) {
+                n_singular++;
+                s.T[r0 + t] = (Real)0;
+                s.T[k.cap + r0 + t] = (Real)0;
+                s.T[2 * k.cap + r0 + t] = (Real)0;
+                if (rb >= 0) {
+                    s.Trev[rb] = (Real)0;
+                    s.Trev[k.cap + rb] = (Real)0;
+                    s.Trev[2 * k.cap + rb] = (Real)0;
+                }
+                continue;
+            }
+            n_plastic += bs.plastic;
+            n_nonconv += bs.nonconv;
+            n_ret64 += bs.ret64;
+            const R4<Real> zj = s_z[t];
+            const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+            const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+            const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            s.T[r0 + t] = T0;
+            s.T[k.cap + r0 + t] = T1;
+            s.T[2 * k.cap + r0 + t] = T2;
+            if (rb >= 0) {
+                s.Trev[rb] = T0;
+                s.Trev[k.cap + rb] = T1;
+                s.Trev[2 * k.cap + rb] = T2;
+            }
+            red[9] += T0; red[10] += T1; red[11] += T2;
+            red[0] += varpi;
+#pragma unroll
+            for (int c = 0; c < 6; c++) red[1 + c] += varpi * bs.sig[c];
+            red[7] += varpi * bs.pc;
+            red[8] += varpi * bs.des;
+        }
+    } else {
     for (int t = threadIdx.x; t < nb; t += TPP) {
         const R4<Real> zj = s_z[t];
         // the bond's reverse slot, loaded now so that its latency is hidden by the sums
@@ -156,19 +270,16 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         Real A00 = 0, A01 = 0, A02 = 0, A10 = 0, A11 = 0, A12 = 0, A20 = 0, A21 = 0, A22 = 0;
         int cnt = 0;
         // sub-horizon of bond (i, j): k in H_i with |x_k - x_j| <= delta
-        // (Alg. 1 line 4); the standard model takes all of H_i
-        if constexpr (F64 || MODEL == 1) {
+        // (Alg. 1 line 4)
+        if constexpr (F64) {
 #pragma unroll 2
             for (int q = 0; q < nb; q++) {
                 const R4<Real> zk = s_z[q];
-                bool member = true;
-                if constexpr (MODEL != 1) {
-                    const double d0 = __dsub_rn(s_p[0][q], pjx);
-                    const double d1 = __dsub_rn(s_p[F64 ? 1 : 0][q], pjy);
-                    const double d2 = __dsub_rn(s_p[F64 ? 2 : 0][q], pjz);
-                    member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
-                                       __dmul_rn(d2, d2)) <= k.delta2;
-                }
+                const double d0 = __dsub_rn(s_p[0][q], pjx);
+                const double d1 = __dsub_rn(s_p[F64 ? 1 : 0][q], pjy);
+                const double d2 = __dsub_rn(s_p[F64 ? 2 : 0][q], pjz);
+                const bool member = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
+                                              __dmul_rn(d2, d2)) <= k.delta2;
                 if (member) {
                     const R4<Real> yk = s_y[q];
                     K00 += zk.x * zk.x; K11 += zk.y * zk.y; K22 += zk.z * zk.z;
@@ -321,6 +432,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         for (int c = 0; c < 6; c++) red[1 + c] += varpi * bs.sig[c];
         red[7] += varpi * bs.pc;
         red[8] += varpi * bs.des;
+    }
     }
     block_sum<12, Real>(red, s_red);
     const Real w = red[0];
