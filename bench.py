@@ -83,6 +83,62 @@ def algorithmic_bytes(nbonds: int, npoints: int, mixed: bool) -> float:
     return nbonds * (8 + 9 * R) + npoints * (20 + 55 * R + (24 if mixed else 0))
 
 
+def uniaxial_config(m: int) -> dict:
+    """The uniaxial compression test of Sec. 4.1, synthetic and in 3-D:
+    12,000 points (40 x 15 x 20, spacing 5 mm), K = 25 MPa, mu = 15 MPa,
+    skeleton density 2200 kg/m^3 with porosity 0.2, saturated at zero
+    suction, the elastic skeleton, horizon m spacings (+0.015 against ties),
+    u_x = 0.5 mm over 0.1 s applied by the end regions (a horizon thick) at
+    the dynamic time step of 3e-6 s, no gravity."""
+    return pi.small_config(40, 15, 20, dx=0.005, horizon_factor=m + 0.015, K=25e6, mu=15e6,
+                           rho=0.8 * 2200.0 + 0.2 * 1000.0, suction=0.0, elastic=1, init_stress=1,
+                           gravity=(0.0, 0.0, 0.0), bc=1, load_rate=0.5e-3 / 0.1, dt=3e-6,
+                           rebuild_every=0)
+
+
+def oscillation_scores(sxx, cfg, m: int) -> dict:
+    """Point-to-point oscillation of sigma_xx over the points at least a
+    horizon inside the loaded regions and the lateral faces: the mean of
+    |sigma_i - mean of its six lattice neighbours| over |mean sigma|, the
+    coefficient of variation, and the mean."""
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    g = np.asarray(sxx, np.float64).reshape(nz, ny, nx)
+    mx, my = 2 * m, m
+    def sh(dz, dy, dx):
+        return g[my + dz:nz - my + dz, my + dy:ny - my + dy, mx + dx:nx - mx + dx]
+    core = sh(0, 0, 0)
+    nbr = (sh(0, 0, -1) + sh(0, 0, 1) + sh(0, -1, 0) + sh(0, 1, 0) + sh(-1, 0, 0) + sh(1, 0, 0)) / 6
+    mean = float(core.mean())
+    return {"checkerboard": float(np.abs(core - nbr).mean() / abs(mean)),
+            "cv": float(core.std() / abs(mean)), "mean_sxx_Pa": mean}
+
+
+def uniaxial_compression(steps: int, tile: int):
+    """The three force states on the Sec. 4.1 test at m = 2 and 3."""
+    import torch
+    from paper_2203_05562_gb300 import Simulation
+    out = []
+    for m in (2, 3):
+        cfg = uniaxial_config(m)
+        for model in (1, 2, 0):
+            sim = Simulation(cfg, precision="mixed", model=model, bond_tile=tile)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
+            sim.step(steps)
+            ev1.record(sim.stream)
+            torch.cuda.synchronize()
+            st = sim.status()
+            sig = sim.read("sigma")
+            r = {"m": m, "model": model, "steps": steps, "ms": ev0.elapsed_time(ev1),
+                 "flags": st["flags"], "W_kin_over_W_int": st["W_kin"] / abs(st["W_int"])
+                 if st["W_int"] else None}
+            if np.isfinite(sig).all():
+                r.update(oscillation_scores(sig[0], cfg, m))
+            out.append(r)
+            del sim
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -242,6 +298,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--standard-steps", type=int, default=100)
+    ap.add_argument("--no-uniaxial", action="store_true")
+    ap.add_argument("--uniaxial-steps", type=int, default=33334,
+                    help="steps of the Sec. 4.1 test (0.1 s at dt = 3e-6 s)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -404,6 +463,12 @@ def main():
     fp64_rate = fig64["bond_steps"] / (fig64["ms"] * 1e-3)
     del sim64
 
+    # ---- the uniaxial compression test of Sec. 4.1 (NEXT-1 comparison) ----
+    uniaxial = None
+    if not args.no_uniaxial:
+        uniaxial = {"workload": "uniaxial_40x15x20 (Sec. 4.1, dynamic loading, elastic skeleton)",
+                    "runs": uniaxial_compression(args.uniaxial_steps, tile)}
+
     # ---- standard correspondence (model 1) on the same column ----
     simS, figS = time_path(dict(cfg, model=1), "mixed", args.standard_steps, args.warmup, barrier)
     standard = {"model": "standard correspondence (every sub-horizon is the family)",
@@ -468,7 +533,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
-            "hbm": hbm, "standard_model": standard,
+            "hbm": hbm, "standard_model": standard, "uniaxial_compression": uniaxial,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "large": large, "adjoint": adj,
             "clocks": clocks, "gpu_launches": fig["launches"],

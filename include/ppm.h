@@ -105,7 +105,20 @@ typedef struct {
                                     256, or 0 to time each on the first call's
                                     bond pass and keep the fastest (results
                                     are bitwise reproducible for a fixed tile) */
-    int32_t pad_;
+    int32_t bc;                  /* boundary conditions: 0 = base layer iz = 0
+                                    fixed (the column collapse); 1 = uniaxial
+                                    compression along x (Sec. 4.1): the
+                                    load_layers planes at ix = 0 are held in x
+                                    and those at ix = nx-1 move at v_x =
+                                    -load_rate; no fixed base.  lock_lateral
+                                    holds x and y in both                     */
+    double load_rate;            /* m/s, bc = 1 (>= 0)                          */
+    int32_t elastic;             /* 1: linear (hypo-)elastic skeleton, as in the
+                                    compression test of Sec. 4.1: the yield test
+                                    is switched off (0: critical-state model) */
+    int32_t load_layers;         /* bc = 1: lattice planes held / driven at each
+                                    x end; 0 = floor(horizon_factor), the
+                                    horizon's thickness                        */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */

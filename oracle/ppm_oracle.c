@@ -387,7 +387,7 @@ static int mu_forward(const ppmo_params* p, const double sig_n[6], double pc_n, 
     t->plastic = 0;
     t->converged = 1;
     t->floored = 0;
-    if (!(t->f_tr > 0.0) || dt == 0.0) {          /* elastic, Eq. 44 */
+    if (!(t->f_tr > 0.0) || dt == 0.0 || p->elastic) {   /* elastic, Eq. 44 */
         mat_to_sym(t->Str, t->sig_out);
         t->pc_out = pc_n;
         return 0;
@@ -659,6 +659,29 @@ static int is_base(const ppmo_params* p, int64_t id) {
     return (id / ((int64_t)p->nx * p->ny)) == 0;
 }
 
+/* Boundary conditions (R18; the loading of Sec. 4.1): returns 1 when
+ * velocity component c of point id is prescribed, with the value in *vbar.
+ * bc = 0: the base layer and, with lock_lateral, the x and y components
+ * are held at zero.  bc = 1: the load_layers lattice planes at the x = 0
+ * end are held in x and those at the other end move at v_x = -load_rate
+ * (lock_lateral still holds x, y); by default the loaded regions are a
+ * horizon thick (reading R28). */
+static int constrained(const ppmo_params* p, int64_t id, int c, double* vbar) {
+    *vbar = 0.0;
+    if (p->lock_lateral && c < 2) return 1;
+    if (p->bc == 0) return is_base(p, id);
+    if (c != 0) return 0;
+    const int64_t ix = id % p->nx;
+    int64_t nl = p->load_layers > 0 ? p->load_layers : (int64_t)p->horizon_factor;
+    if (nl < 1) nl = 1;
+    if (ix < nl) return 1;
+    if (ix >= p->nx - nl) {
+        *vbar = -p->load_rate;
+        return 1;
+    }
+    return 0;
+}
+
 static void current_positions(const ppmo_params* p, int64_t n, const double* u, double* x) {
     ppmo_reference_positions(p, x);
     for (int64_t k = 0; k < 3 * n; k++) x[k] += u[k];
@@ -715,8 +738,8 @@ int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* 
     for (int64_t i = 0; i < n; i++) {
         for (int c = 0; c < 3; c++) {
             s->u[c * n + i] = 0.0;
-            double vv = v0 ? v0[c * n + i] : 0.0;
-            if (is_base(p, i) || (p->lock_lateral && c < 2)) vv = 0.0;
+            double vv = v0 ? v0[c * n + i] : 0.0, vbar;
+            if (constrained(p, i, c, &vbar)) vv = vbar;
             s->v[c * n + i] = vv;
         }
         s->pc[i] = -p->pc0;        /* b1 = 0, b2 = 1: pbar_c = p_c (Eq. 45) */
@@ -735,8 +758,8 @@ int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* 
     double wk = 0.0;
     for (int64_t i = 0; i < n; i++)
         for (int c = 0; c < 3; c++) {
-            double a = s->fint[c * n + i] / m + p->gravity[c];      /* Eq. 62 */
-            if (is_base(p, i) || (p->lock_lateral && c < 2)) a = 0.0;
+            double a = s->fint[c * n + i] / m + p->gravity[c], vbar;      /* Eq. 62 */
+            if (constrained(p, i, c, &vbar)) a = 0.0;
             s->a[c * n + i] = a;
             wk += 0.5 * m * s->v[c * n + i] * s->v[c * n + i];
         }
@@ -766,8 +789,8 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
          * conditions; displacement, Eq. 64 (Alg. 2 lines 6-8) */
         for (int64_t i = 0; i < n; i++)
             for (int c = 0; c < 3; c++) {
-                double v = s->v[c * n + i] + 0.5 * dt * s->a[c * n + i];
-                if (is_base(p, i) || (p->lock_lateral && c < 2)) v = 0.0;
+                double v = s->v[c * n + i] + 0.5 * dt * s->a[c * n + i], vbar;
+                if (constrained(p, i, c, &vbar)) v = vbar;
                 vh[c * n + i] = v;
                 s->u[c * n + i] += dt * v;
             }
@@ -784,8 +807,9 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         double dWi = 0.0, dWe = 0.0, wk = 0.0;
         for (int64_t i = 0; i < n; i++)
             for (int c = 0; c < 3; c++) {
-                double a = s->fint[c * n + i] / m + p->gravity[c];
-                if (is_base(p, i) || (p->lock_lateral && c < 2)) a = 0.0;
+                double a = s->fint[c * n + i] / m + p->gravity[c], vbar;
+                const int fixed = constrained(p, i, c, &vbar);
+                if (fixed) a = 0.0;
                 s->a[c * n + i] = a;
                 double v = vh[c * n + i] + 0.5 * dt * a;
                 s->v[c * n + i] = v;
@@ -793,6 +817,12 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
                  * internal force; external work of gravity */
                 dWi += -0.5 * dt * vh[c * n + i] * (f_old[c * n + i] + s->fint[c * n + i]);
                 dWe += 0.5 * dt * vh[c * n + i] * (2.0 * m * p->gravity[c]);
+                /* a prescribed component moves under the reaction R = -(f + m g)
+                 * that cancels its acceleration; its work is external (zero
+                 * where the component is held) */
+                if (fixed)
+                    dWe += -0.5 * dt * vh[c * n + i] *
+                           (f_old[c * n + i] + s->fint[c * n + i] + 2.0 * m * p->gravity[c]);
                 wk += 0.5 * m * v * v;
             }
         s->W_int += dWi;
@@ -952,8 +982,9 @@ static void reverse_step(const ppmo_params* p, int64_t n, const double* u, const
         for (int c = 0; c < 3; c++) {
             size_t t = (size_t)c * n + i;
             double w = v[t] + h * a[t];
-            int fixed = is_base(p, i) || (p->lock_lateral && c < 2);
-            if (fixed) w = 0.0;
+            double vbar;
+            int fixed = constrained(p, i, c, &vbar);
+            if (fixed) w = vbar;
             vh[t] = w;
             x[t] += u[t] + dt * w;
             /* v' = vh + h a' ; a' = f/m + g (fixed components: a' = 0) */
@@ -1081,8 +1112,8 @@ static void reverse_step(const ppmo_params* p, int64_t n, const double* u, const
     for (int64_t i = 0; i < n; i++)
         for (int c = 0; c < 3; c++) {
             size_t t = (size_t)c * n + i;
-            double vht = vhb[t] + dt * u1b[t];
-            int fixed = is_base(p, i) || (p->lock_lateral && c < 2);
+            double vht = vhb[t] + dt * u1b[t], vbar;
+            int fixed = constrained(p, i, c, &vbar);
             ub[t] = u1b[t];
             vb[t] = fixed ? 0.0 : vht;
             ab[t] = fixed ? 0.0 : h * vht;
@@ -1103,7 +1134,8 @@ static void reverse_initial(const ppmo_params* p, int64_t n, const double* sig0,
     for (int64_t i = 0; i < n; i++)
         for (int c = 0; c < 3; c++) {
             size_t t = (size_t)c * n + i;
-            int fixed = is_base(p, i) || (p->lock_lateral && c < 2);
+            double vbar;
+            int fixed = constrained(p, i, c, &vbar);
             fb[t] = fixed ? 0.0 : ab[t] / m;
         }
     for (int64_t i = 0; i < n; i++) {

@@ -45,7 +45,17 @@ typedef struct {
     int32_t newton_max_iter;
     double newton_tol;
     int32_t lock_lateral;        /* 1: x,y motion suppressed (uniaxial strain) */
-    int32_t pad_;
+    int32_t bc;                  /* 0: base layer iz = 0 fixed (R18)          */
+                                 /* 1: uniaxial compression along x (Sec. 4.1):
+                                    the load_layers planes at ix = 0 held in x,
+                                    those at ix = nx-1 moved at v_x =
+                                    -load_rate; no fixed base                 */
+    double load_rate;            /* m/s, bc = 1                               */
+    int32_t elastic;             /* 1: linear (hypo-)elastic skeleton of Sec. 4.1,
+                                    the yield test switched off               */
+    int32_t load_layers;         /* bc = 1: lattice planes held / driven at each
+                                    x end; 0 = floor(horizon_factor), the
+                                    horizon's thickness                        */
 } ppmo_params;
 
 typedef struct {

@@ -192,7 +192,8 @@ __global__ void k_adj_pre(DevState<Real> s, AdjState<Real> a, StepConst k, int i
          t += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
         const size_t i = t - (size_t)c * n;
-        const bool fixed = lat_z(s.lat[i]) == 0 || (k.lock_lateral && c < 2);
+        Real vbar;
+        const bool fixed = prescribed(s, k, (size_t)i, c, vbar);
         const Real abt = initial ? a.ab[t] : a.ab[t] + h * a.vb[t];
         a.fb[t] = fixed ? (Real)0 : abt * inv_m;
         if (!initial) {
@@ -625,7 +626,8 @@ k_adj_post(DevState<Real> s, AdjState<Real> a, StepConst k) {
         const Real gy = c == 0 ? z[3] : (c == 1 ? z[4] : z[5]);
         const Real u1b = a.u1b[t] + gz - a.zsum[t];
         const Real vhb = a.vhb[t] + gy - a.ysum[t] + dt * u1b;
-        const bool fixed = lat_z(s.lat[i]) == 0 || (k.lock_lateral && c < 2);
+        Real vbar;
+        const bool fixed = prescribed(s, k, (size_t)i, c, vbar);
         a.ub[t] = u1b;
         a.vb[t] = fixed ? (Real)0 : vhb;
         a.ab[t] = fixed ? (Real)0 : h * vhb;

@@ -39,8 +39,8 @@ __global__ void k_predictor(DevState<Real> s, StepConst k) {
          t += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
         const size_t i = t - (size_t)c * n;
-        Real v = s.v[t] + hdt * s.a[t];
-        if (lat_z(s.lat[i]) == 0 || (k.lock_lateral && c < 2)) v = (Real)0;
+        Real v = s.v[t] + hdt * s.a[t], vbar;
+        if (prescribed(s, k, i, c, vbar)) v = vbar;
         s.vh[t] = v;
         if constexpr (sizeof(Real) == 8) {
             s.u[t] = s.u[t] + dt * v;
@@ -547,7 +547,8 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
         const int c = lane < 3 ? lane : 0;
         const size_t t = (size_t)c * n + i;
         const Real ts = s.tsum[t], fo = s.fint[t], vh = s.vh[t], v0 = s.v[t];
-        const bool base = lat_z(s.lat[i]) == 0;
+        Real vbar;
+        const bool fixed = prescribed(s, k, (size_t)i, c, vbar);
         // every load of the row T_(ji) (stored contiguously in Trev) first
         Real x[3][kIt];
 #pragma unroll
@@ -596,7 +597,7 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
             const Real fhat = ts - gathered;
             const Real f = fhat * dx2;                               // Eq. 49-50
             Real a = fhat * inv_rho_dx + g;                          // Eq. 62
-            if (base || (k.lock_lateral && c < 2)) a = (Real)0;
+            if (fixed) a = (Real)0;
             if (!isfinite(a)) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
             s.fint[t] = f;
             s.a[t] = a;
@@ -607,6 +608,9 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
                 s.v[t] = v;
                 dwi = -hdt * vh * (fo + f);                          // Eq. 66
                 dwe = dtr * m * vh * g;                              // Eq. 67
+                // a prescribed component moves under the reaction -(f + m g);
+                // its work is external (zero where the component is held)
+                if (fixed) dwe += -hdt * vh * (fo + f + (Real)2 * m * g);
                 wk = (Real)0.5 * m * v * v;                          // Eq. 68
             }
         }
@@ -702,7 +706,8 @@ __global__ void k_velocity_bc(DevState<Real> s, StepConst k) {
          t += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / n);
         const size_t i = t - (size_t)c * n;
-        if (lat_z(s.lat[i]) == 0 || (k.lock_lateral && c < 2)) s.v[t] = (Real)0;
+        Real vbar;
+        if (prescribed(s, k, i, c, vbar)) s.v[t] = vbar;
     }
 }
 

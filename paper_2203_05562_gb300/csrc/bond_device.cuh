@@ -367,7 +367,7 @@ __device__ __forceinline__ bool material_trial(const Real L[9], const Real sn[6]
         trace->p_tr = p_tr; trace->q_tr = q_tr;
         trace->plastic = 0; trace->floored = 0;
     }
-    return f_tr > (Real)0;
+    return f_tr > (Real)0 && !k.elastic;
 }
 
 // Plastic part: the visco-plastic return from the trial stress st (Eq. 42-46,

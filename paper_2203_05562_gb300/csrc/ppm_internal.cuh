@@ -52,6 +52,11 @@ struct StepConst {
     double dt, rho, K, mu, lk, eta, tol;
     double g[3];
     int visc_form, max_iter, model, lock_lateral;
+    int bc;                      // 0: fixed base layer; 1: uniaxial compression along x
+    double load_rate;            // m/s, bc = 1
+    float load_ratef;
+    int elastic;                 // 1: linear elastic skeleton, the yield test off
+    int load_layers;             // bc = 1: planes held / driven at each x end
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
@@ -95,6 +100,29 @@ struct DevState {
     int32_t* scanbuf;    // block sums of the scans
     int ncell_cap;
 };
+
+// Boundary conditions (the fixed base; the loading of Sec. 4.1): true when
+// velocity component c of point i is prescribed, with the value in vbar.
+// bc = 0: the base layer and, with lock_lateral, the x and y components are
+// held at zero.  bc = 1: the load_layers planes at the x = 0 end of the
+// point's column are held in x and those at the other end move at
+// v_x = -load_rate.
+template <typename Real>
+__device__ __forceinline__ bool prescribed(const DevState<Real>& s, const StepConst& k, size_t i,
+                                           int c, Real& vbar) {
+    vbar = (Real)0;
+    if (k.lock_lateral && c < 2) return true;
+    const int li = s.lat[i];
+    if (k.bc == 0) return lat_z(li) == 0;
+    if (c != 0) return false;
+    const int ix = lat_x(li);
+    if (ix < k.load_layers) return true;
+    if (ix >= s.cols[s.colid[i]].nx - k.load_layers) {
+        vbar = sizeof(Real) == 8 ? (Real)-k.load_rate : (Real)-k.load_ratef;
+        return true;
+    }
+    return false;
+}
 
 // adjoint arrays (adjoint.cu); Real as the forward path
 template <typename Real>

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <new>
+#include <cmath>
 #include <vector>
 
 #include "ppm_internal.cuh"
@@ -79,6 +80,10 @@ int check_params(const ppm_params* p) {
         return PPM_EINVAL;
     if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
         return PPM_EINVAL;
+    if ((p->bc != 0 && p->bc != 1) || !(p->load_rate >= 0) || !std::isfinite(p->load_rate))
+        return PPM_EINVAL;
+    if (p->elastic != 0 && p->elastic != 1) return PPM_EINVAL;
+    if (p->load_layers < 0) return PPM_EINVAL;
     return PPM_OK;
 }
 
@@ -677,6 +682,12 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.max_iter = p->newton_max_iter;
     k.model = p->model;
     k.lock_lateral = p->lock_lateral;
+    k.bc = p->bc;
+    k.load_rate = p->load_rate;
+    k.load_ratef = (float)p->load_rate;
+    k.elastic = p->elastic;
+    k.load_layers = p->load_layers > 0 ? p->load_layers : (int)p->horizon_factor;
+    if (k.load_layers < 1) k.load_layers = 1;
     k.npoints = (int)c->N;
     k.ncols = c->ncols;
     k.max_family = z.max_family;

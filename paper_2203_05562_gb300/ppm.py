@@ -38,7 +38,8 @@ class Params(C.Structure):
         ("rebuild_every", C.c_int32), ("init_stress", C.c_int32), ("visc_form", C.c_int32),
         ("newton_max_iter", C.c_int32), ("newton_tol", C.c_double),
         ("lock_lateral", C.c_int32), ("precision", C.c_int32), ("max_family", C.c_int32),
-        ("use_graph", C.c_int32), ("bond_tile", C.c_int32), ("pad_", C.c_int32),
+        ("use_graph", C.c_int32), ("bond_tile", C.c_int32), ("bc", C.c_int32),
+        ("load_rate", C.c_double), ("elastic", C.c_int32), ("load_layers", C.c_int32),
     ]
 
 

@@ -31,6 +31,10 @@ MATERIAL = dict(
     newton_max_iter=50, newton_tol=1e-10,
     lock_lateral=0,
     rebuild_every=1,
+    bc=0,                   # 0: fixed base layer; 1: uniaxial compression along x
+    load_rate=0.0,          # m/s, bc = 1
+    elastic=0,              # 1: linear elastic skeleton (no yield), as in Sec. 4.1
+    load_layers=0,          # bc = 1: planes held / driven at each end; 0: the horizon's thickness
 )
 
 #: The five workloads: (description, overrides).

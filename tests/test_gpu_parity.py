@@ -238,3 +238,25 @@ def test_mixed_ensemble_matches_per_column_oracle():
         run = oracle_run(cc, 12, v0[:, off:off + m])
         assert rel_l2(u[:, off:off + m], run.u) <= MIXED_TOL
         off += m
+
+
+@pytest.mark.parametrize("model,elastic", [(0, 0), (1, 0), (2, 0), (2, 1)])
+def test_uniaxial_loading_matches_oracle(model, elastic):
+    # the loading of Sec. 4.1: the end regions (a horizon thick) held in x and
+    # driven at -load_rate, no fixed base; suction 50 kPa so that the returns
+    # run too, or the elastic skeleton of that section
+    cfg = pi.small_config(10, 5, 6, suction=50e3, model=model, bc=1, load_rate=0.05,
+                          rebuild_every=3, elastic=elastic)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=21)
+    run = oracle_run(cfg, 10, v0)
+    assert (run.counters()["plastic"] > 0) == (elastic == 0)
+    sim = gpu_run(cfg, 10, "fp64", v0=v0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    st, ce = sim.status(), run.energies()
+    for key in ("W_int", "W_ext", "W_kin"):
+        scale = max(abs(ce["W_int"]), abs(ce["W_ext"]), ce["W_kin"])
+        assert abs(st[key] - ce[key]) <= FP64_TOL * scale, key
+    sim = gpu_run(cfg, 10, "mixed", v0=v0)
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["u"] <= MIXED_TOL and err["sigma"] <= MIXED_TOL, err
