@@ -113,8 +113,9 @@ def oscillation_scores(sxx, cfg, m: int) -> dict:
             "cv": float(core.std() / abs(mean)), "mean_sxx_Pa": mean}
 
 
-def uniaxial_compression(steps: int, tile: int):
-    """The three force states on the Sec. 4.1 test at m = 2 and 3."""
+def uniaxial_compression(steps: int, tile: int, early: int = 10000):
+    """The three force states on the Sec. 4.1 test at m = 2 and 3; the
+    oscillation scores after `early` steps (u_x = 0.15 mm) and at the end."""
     import torch
     from paper_2203_05562_gb300 import Simulation
     out = []
@@ -122,18 +123,22 @@ def uniaxial_compression(steps: int, tile: int):
         cfg = uniaxial_config(m)
         for model in (1, 2, 0):
             sim = Simulation(cfg, precision="mixed", model=model, bond_tile=tile)
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record(sim.stream)
-            sim.step(steps)
-            ev1.record(sim.stream)
-            torch.cuda.synchronize()
-            st = sim.status()
-            sig = sim.read("sigma")
-            r = {"m": m, "model": model, "steps": steps, "ms": ev0.elapsed_time(ev1),
-                 "flags": st["flags"], "W_kin_over_W_int": st["W_kin"] / abs(st["W_int"])
-                 if st["W_int"] else None}
-            if np.isfinite(sig).all():
-                r.update(oscillation_scores(sig[0], cfg, m))
+            r = {"m": m, "model": model, "steps": steps, "ms": 0.0}
+            for tag, upto in (("early", min(early, steps)), ("end", steps)):
+                done = 0 if tag == "early" else min(early, steps)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(sim.stream)
+                sim.step(upto - done)
+                ev1.record(sim.stream)
+                torch.cuda.synchronize()
+                r["ms"] += ev0.elapsed_time(ev1)
+                st = sim.status()
+                sig = sim.read("sigma")
+                snap = {"steps": upto, "flags": st["flags"],
+                        "W_kin_over_W_int": st["W_kin"] / abs(st["W_int"]) if st["W_int"] else None}
+                if np.isfinite(sig).all():
+                    snap.update(oscillation_scores(sig[0], cfg, m))
+                r[tag] = snap
             out.append(r)
             del sim
     return out
