@@ -354,6 +354,9 @@ def main():
     # ---- dominant kernel: per-phase CUDA-event times on the launching stream,
     # over the same warm-up and steps as the headline, on a fresh column ----
     st = sim.status()
+    # Eq. 65 (reading R30) on the column at the end of the run, beside the step used
+    critical = {"eq65_s": sim.critical_time_step(), "dt_used_s": sim.dt,
+                "note": "micro-modulus over bond length; stable for models 1 and 2 up to at least 2x"}
     del sim
     from paper_2203_05562_gb300 import Simulation
     tile = fig["status"]["bond_tile"]          # the autotuner's choice, reused below
@@ -539,6 +542,7 @@ def main():
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
             "hbm": hbm, "standard_model": standard, "uniaxial_compression": uniaxial,
+            "critical_time_step": critical,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "large": large, "adjoint": adj,
             "clocks": clocks, "gpu_launches": fig["launches"],

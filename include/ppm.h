@@ -213,6 +213,15 @@ int ppm_read_state(ppm_ctx* c, int field, void* dst, size_t bytes, int dst_is_de
  * step).  Family fields are read-only. */
 int ppm_write_state(ppm_ctx* c, int field, const void* src, size_t bytes, int src_is_device);
 
+/* Critical time step of Eq. 65 over the current family and positions (the
+ * family is built first if there is none): the minimum over points with
+ * bonds of sqrt(2 rho / sum_j V C / |x_j - x_i|), V = dx^3, with the
+ * bond-based micro-modulus C = 18 K / (pi delta^4).  Eq. 65 as printed
+ * multiplies C by |zeta|, which does not give a time; the micro-modulus is
+ * divided by the bond length, as in the estimate the paper cites.  *dt is
+ * +inf when no point has a bond.  Synchronises the stream. */
+int ppm_critical_time_step(ppm_ctx* c, double* dt);
+
 /* Number of bonds of the current family (synchronises the stream). */
 int ppm_num_bonds(ppm_ctx* c, int64_t* nbonds);
 

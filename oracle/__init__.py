@@ -98,6 +98,8 @@ def lib():
             L.ppmo_initial_stress.restype = None
             L.ppmo_initial_stress.argtypes = [pp, dp]
             L.ppmo_objective_gradient.argtypes = [pp, dp, C.c_int, C.c_int64, dp, dp]
+            L.ppmo_critical_time_step.restype = C.c_double
+            L.ppmo_critical_time_step.argtypes = [pp, C.POINTER(State)]
             L.ppmo_num_threads.restype = C.c_int
             L.ppmo_set_num_threads.argtypes = [C.c_int]
             L.ppmo_set_num_threads.restype = None
@@ -319,6 +321,10 @@ class Run:
     @property
     def nbonds(self) -> int:
         return int(self.s.nbonds)
+
+    def critical_time_step(self) -> float:
+        """Eq. 65 (reading R30) over the current family and positions."""
+        return float(lib().ppmo_critical_time_step(C.byref(self.p), C.byref(self.s)))
 
     @property
     def steps_done(self) -> int:

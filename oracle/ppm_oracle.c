@@ -1271,6 +1271,39 @@ int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps,
     return 0;
 }
 
+/* Critical time step of Eq. 65 in the current configuration.  Eq. 65 as
+ * printed divides by sum V C |zeta|, which is not a time squared; the
+ * estimate it cites divides the micro-modulus by the bond length (reading
+ * R30): dt_i = sqrt(2 rho / sum_j V C / |x_j - x_i|) over the family of i,
+ * with the bond-based micro-modulus C = 18 K / (pi delta^4) and the mixture
+ * density for (1 - phi) rho_s (R5).  Returns the minimum over the points
+ * that have bonds (INFINITY if none). */
+double ppmo_critical_time_step(const ppmo_params* p, const ppmo_state* s) {
+    const int64_t n = s->n;
+    double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!x) return NAN;
+    current_positions(p, n, s->u, x);
+    const double delta = p->horizon_factor * p->dx;
+    const double pi = 3.14159265358979323846;
+    const double C = 18.0 * p->K / (pi * delta * delta * delta * delta);
+    const double V = p->dx * p->dx * p->dx;
+    double best = INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        double sum = 0.0;
+        for (int64_t b = s->row_ptr[i]; b < s->row_ptr[i + 1]; b++) {
+            const int64_t j = s->col[b];
+            const double d0 = x[j] - x[i], d1 = x[n + j] - x[n + i], d2 = x[2 * n + j] - x[2 * n + i];
+            sum += 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        }
+        if (sum > 0.0) {
+            const double dt = sqrt(2.0 * p->rho / (V * C * sum));
+            if (dt < best) best = dt;
+        }
+    }
+    free(x);
+    return best;
+}
+
 int ppmo_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

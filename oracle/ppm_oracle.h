@@ -137,6 +137,10 @@ int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps,
                             double* J, double grad[4]);
 
 /* Threads used by the OpenMP loops (results do not depend on it). */
+/* Critical time step of Eq. 65 (reading R30) over the current family and
+ * positions of s; the minimum over points with bonds. */
+double ppmo_critical_time_step(const ppmo_params* p, const ppmo_state* s);
+
 int ppmo_num_threads(void);
 void ppmo_set_num_threads(int t);
 

@@ -8,6 +8,7 @@
 //   per-point fill and in-warp rank sort -> reverse index by bisection.
 // Points of different columns never bond: the cell key includes the column.
 #include <cuda_runtime.h>
+#include <cmath>
 
 #include "ppm_internal.cuh"
 
@@ -359,6 +360,38 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t* data, int n,
     }
 }
 
+// Critical time step of Eq. 65 (reading R30: micro-modulus over bond
+// length): one warp per point sums 1 / |x_j - x_i| over the family in FP64
+// (lane-strided, then a butterfly), dt_i = sqrt(2 rho / (V C sum)), and the
+// minimum over points goes to *out by an atomic min on the ordered bits,
+// exact and independent of the order.
+template <typename Real>
+__global__ void __launch_bounds__(kWarpPointsPerBlock * 32)
+k_critical_dt(DevState<Real> s, StepConst k, double VC, long long* out) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kWarpPointsPerBlock + (threadIdx.x >> 5);
+    if (i >= k.npoints) return;                     // the whole warp leaves together
+    const int li = s.lat[i];
+    const int r0 = s.row_ptr[i], r1 = s.row_ptr[i + 1];
+    const double xi = Geometry<Real>::pos(s, k, i, 0, li);
+    const double yi = Geometry<Real>::pos(s, k, i, 1, li);
+    const double zi = Geometry<Real>::pos(s, k, i, 2, li);
+    double acc = 0.0;
+    for (int b = r0 + lane; b < r1; b += 32) {
+        const int j = s.col[b];
+        const int lj = s.lat[j];
+        const double d0 = Geometry<Real>::pos(s, k, j, 0, lj) - xi;
+        const double d1 = Geometry<Real>::pos(s, k, j, 1, lj) - yi;
+        const double d2 = Geometry<Real>::pos(s, k, j, 2, lj) - zi;
+        acc += 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0 && acc > 0.0) atomicMin(out, ordered(sqrt(2.0 * k.rho / (VC * acc))));
+}
+
+__global__ void k_critical_dt_reset(long long* out) { *out = 0x7fffffffffffffffLL; }
+
 }  // namespace
 
 cudaError_t launch_exclusive_scan(int32_t* data, int n, int32_t* scanbuf, cudaStream_t st,
@@ -409,6 +442,24 @@ cudaError_t launch_family_build(const DevState<Real>& s, const StepConst& k, cud
     if (nlaunch) *nlaunch += 10;   // bbox_reset .. rev, scans counted above
     return cudaGetLastError();
 }
+
+template <typename Real>
+cudaError_t launch_critical_dt(const DevState<Real>& s, const StepConst& k, long long* out,
+                               cudaStream_t st) {
+    if (k.npoints <= 0) return cudaSuccess;
+    const double delta = std::sqrt(k.delta2);
+    const double C = 18.0 * k.K / (3.14159265358979323846 * delta * delta * delta * delta);
+    const double VC = k.dx * k.dx * k.dx * C;
+    const int wblocks = (k.npoints + kWarpPointsPerBlock - 1) / kWarpPointsPerBlock;
+    k_critical_dt_reset<<<1, 1, 0, st>>>(out);
+    k_critical_dt<Real><<<wblocks, kWarpPointsPerBlock * 32, 0, st>>>(s, k, VC, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_critical_dt<double>(const DevState<double>&, const StepConst&,
+                                                long long*, cudaStream_t);
+template cudaError_t launch_critical_dt<float>(const DevState<float>&, const StepConst&,
+                                               long long*, cudaStream_t);
 
 template cudaError_t launch_family_build<double>(const DevState<double>&, const StepConst&,
                                                  cudaStream_t, long long*);

@@ -139,6 +139,9 @@ struct AdjState {
 // ---- launchers (family.cu) ----
 // *nlaunch (if not null) is incremented by the number of kernels launched
 template <typename Real>
+cudaError_t launch_critical_dt(const DevState<Real>& s, const StepConst& k, long long* out,
+                               cudaStream_t st);
+template <typename Real>
 cudaError_t launch_family_build(const DevState<Real>& s, const StepConst& k, cudaStream_t st,
                                 long long* nlaunch);
 // exclusive scan of n int32 values in place (n <= 16M); scanbuf >= 8192 ints

@@ -203,6 +203,29 @@ int run_family(ppm_ctx* c, const DevState<Real>& s) {
 template <typename Real>
 int autotune_tile(ppm_ctx* c, const DevState<Real>& s);
 
+// Eq. 65 over the current family (built first if there is none); the result
+// comes back through the first slot of the family search's bounding-box
+// scratch, unused between family builds
+template <typename Real>
+int critical_dt(ppm_ctx* c, const DevState<Real>& s, double* out) {
+    if (!c->family_built) {
+        int rc = run_family<Real>(c, s);
+        if (rc) return rc;
+    }
+    CU(launch_critical_dt<Real>(s, c->k, s.bbox, c->stream));
+    c->launches += 2;
+    long long h = 0;
+    CU(cudaMemcpyAsync(&h, s.bbox, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h == 0x7fffffffffffffffLL) {
+        *out = INFINITY;
+    } else {
+        h ^= (h >> 63) & 0x7fffffffffffffffLL;     // back from the ordered encoding
+        memcpy(out, &h, sizeof(h));
+    }
+    return PPM_OK;
+}
+
 template <typename Real>
 int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
     CU(launch_apply_velocity_bc<Real>(s, c->k, c->stream));
@@ -774,6 +797,12 @@ int ppm_step_timed(ppm_ctx* c, int n_steps, double* ms) {
     if (!c || n_steps < 0 || !ms) return PPM_EINVAL;
     return c->p.precision == PPM_FP64 ? do_steps<double>(c, c->sd, n_steps, ms)
                                       : do_steps<float>(c, c->sf, n_steps, ms);
+}
+
+int ppm_critical_time_step(ppm_ctx* c, double* dt) {
+    if (!c || !dt) return PPM_EINVAL;
+    return c->p.precision == PPM_FP64 ? critical_dt<double>(c, c->sd, dt)
+                                      : critical_dt<float>(c, c->sf, dt);
 }
 
 int ppm_num_bonds(ppm_ctx* c, int64_t* nbonds) {

@@ -83,6 +83,7 @@ def library(build_if_missing: bool = True):
             L.ppm_read_state.argtypes = [vp, C.c_int, vp, C.c_size_t, C.c_int]
             L.ppm_write_state.argtypes = [vp, C.c_int, vp, C.c_size_t, C.c_int]
             L.ppm_num_bonds.argtypes = [vp, C.POINTER(C.c_int64)]
+            L.ppm_critical_time_step.argtypes = [vp, C.POINTER(C.c_double)]
             L.ppm_status.argtypes = [vp, C.POINTER(Counters)]
             L.ppm_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
             L.ppm_error_string.restype = C.c_char_p
@@ -254,6 +255,12 @@ class Simulation:
             _check(library().ppm_adjoint_reverse(self._ctx, C.c_void_p(a.ctypes.data), 0, grad),
                    "ppm_adjoint_reverse")
         return np.array([grad[q] for q in range(4)])
+
+    def critical_time_step(self) -> float:
+        """Eq. 65 over the current family and positions (ppm_critical_time_step)."""
+        dt = C.c_double(0.0)
+        _check(library().ppm_critical_time_step(self._ctx, C.byref(dt)), "ppm_critical_time_step")
+        return float(dt.value)
 
     def num_bonds(self) -> int:
         nb = C.c_int64(0)

@@ -260,3 +260,14 @@ def test_uniaxial_loading_matches_oracle(model, elastic):
     sim = gpu_run(cfg, 10, "mixed", v0=v0)
     err = state_errors(sim, run, norm=rel_l2)
     assert err["u"] <= MIXED_TOL and err["sigma"] <= MIXED_TOL, err
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_critical_time_step_matches_oracle(precision, tol):
+    # Eq. 65 (reading R30) over a deformed column's family, after some steps
+    cfg = pi.small_config(7, 6, 9, suction=30e3, rebuild_every=2)
+    v0 = pi.initial_velocity(cfg, std=1e-2, seed=17)
+    run = oracle_run(cfg, 6, v0)
+    sim = gpu_run(cfg, 6, precision, v0=v0)
+    got, want = sim.critical_time_step(), run.critical_time_step()
+    assert np.isfinite(want) and abs(got - want) <= tol * want, (got, want)
