@@ -53,6 +53,8 @@ extern "C" {
 #define PPM_STATUS_FAMILY_FULL    8u  /* bonds exceeded the workspace capacity      */
 #define PPM_STATUS_ROW_FULL      16u  /* a point had more than max_family bonds     */
 #define PPM_STATUS_UNSTABLE      32u  /* energy balance of Eq. 69 above 1e-2        */
+#define PPM_STATUS_HALTED        64u  /* halt_on_unstable: the steps after the one
+                                         whose Eq. 69 check failed did nothing   */
 
 /* precision of the path */
 #define PPM_FP64  0   /* everything in FP64                                     */
@@ -119,6 +121,12 @@ typedef struct {
     int32_t load_layers;         /* bc = 1: lattice planes held / driven at each
                                     x end; 0 = floor(horizon_factor), the
                                     horizon's thickness                        */
+    int32_t halt_on_unstable;    /* 1: the Eq. 69 check is a hard stop -- once a
+                                    step fails it, later steps change nothing
+                                    (PPM_STATUS_HALTED, halted_step); decided
+                                    on the device, so it also holds inside CUDA
+                                    graphs.  Not with the adjoint calls.      */
+    int32_t pad_;
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */
@@ -142,7 +150,8 @@ typedef struct {
                                     in PPM_FP64; in PPM_MIXED those near the
                                     apex or whose FP32 solve failed)           */
     int32_t bond_tile;           /* tile in use                                 */
-    int32_t pad2_;
+    int32_t halted_step;         /* PPM_STATUS_HALTED: the step whose energy
+                                    check failed (counted from 1), else 0     */
     uint32_t status;             /* PPM_STATUS_* bits                           */
     uint32_t pad_;
     double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */

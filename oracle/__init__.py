@@ -53,6 +53,7 @@ class Params(C.Structure):
         ("newton_max_iter", C.c_int32), ("newton_tol", C.c_double),
         ("lock_lateral", C.c_int32), ("bc", C.c_int32), ("load_rate", C.c_double),
         ("elastic", C.c_int32), ("load_layers", C.c_int32),
+        ("halt_on_unstable", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -66,7 +67,7 @@ class State(C.Structure):
         ("step", C.c_int64),
         ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double), ("W_kin0", C.c_double),
         ("n_plastic", C.c_int64), ("n_nonconv", C.c_int64), ("n_singular", C.c_int64),
-        ("n_overflow", C.c_int64),
+        ("n_overflow", C.c_int64), ("unstable", C.c_int64), ("halted_step", C.c_int64),
     ]
 
 
@@ -344,4 +345,4 @@ class Run:
     def counters(self):
         s = self.s
         return dict(plastic=s.n_plastic, nonconv=s.n_nonconv, singular=s.n_singular,
-                    overflow=s.n_overflow)
+                    overflow=s.n_overflow, unstable=s.unstable, halted_step=s.halted_step)

@@ -767,6 +767,8 @@ int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* 
     s->step = 0;
     s->W_int = 0.0; s->W_ext = 0.0; s->W_kin = wk; s->W_kin0 = wk;
     s->n_plastic = s->n_nonconv = s->n_singular = 0;
+    s->unstable = 0;
+    s->halted_step = 0;
     return 0;
 }
 
@@ -784,6 +786,10 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
     double* f_old = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     if (!x || !vh || !f_old) { free(x); free(vh); free(f_old); return -2; }
     for (int st = 0; st < n_steps; st++) {
+        if (p->halt_on_unstable && s->halted_step) {     /* the run has stopped */
+            s->step++;
+            continue;
+        }
         memcpy(f_old, s->fint, sizeof(double) * 3 * (size_t)n);
         /* predictor, Eq. 60-61 with beta1 = 1/2, beta2 = 0; boundary
          * conditions; displacement, Eq. 64 (Alg. 2 lines 6-8) */
@@ -829,6 +835,13 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         s->W_ext += dWe;
         s->W_kin = wk;
         s->step++;
+        /* the energy check of Eq. 69 (R20): diagnostic, or a hard stop */
+        const double bal = fabs(s->W_int + s->W_kin - s->W_ext - s->W_kin0);
+        const double mx = fmax(fmax(s->W_kin, fabs(s->W_int)), fmax(fabs(s->W_ext), s->W_kin0));
+        if (bal > 1e-2 * mx) {
+            s->unstable = 1;
+            if (p->halt_on_unstable && !s->halted_step) s->halted_step = s->step;
+        }
     }
     free(x); free(vh); free(f_old);
     return 0;

@@ -56,6 +56,9 @@ typedef struct {
     int32_t load_layers;         /* bc = 1: lattice planes held / driven at each
                                     x end; 0 = floor(horizon_factor), the
                                     horizon's thickness                        */
+    int32_t halt_on_unstable;    /* 1: once a step fails the Eq. 69 check, later
+                                    steps change nothing                      */
+    int32_t pad_;
 } ppmo_params;
 
 typedef struct {
@@ -73,6 +76,8 @@ typedef struct {
     int64_t step;
     double W_int, W_ext, W_kin, W_kin0;
     int64_t n_plastic, n_nonconv, n_singular, n_overflow;
+    int64_t unstable;            /* 1 once a step failed the Eq. 69 check (1e-2)  */
+    int64_t halted_step;         /* halt_on_unstable: that step (from 1), else 0  */
 } ppmo_state;
 
 /* Eq. (15) replaced by the van Genuchten curve (see DESIGN readings). */

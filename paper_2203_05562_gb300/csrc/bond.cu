@@ -33,6 +33,7 @@ namespace {
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void k_predictor(DevState<Real> s, StepConst k) {
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;   // the run has stopped
     const size_t n = (size_t)k.npoints;
     const Real dt = (Real)k.dt, hdt = (Real)(0.5 * k.dt);
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 3 * n;
@@ -65,6 +66,9 @@ __global__ void __launch_bounds__(TPP, sizeof(Real) == 4 ? (640 / TPP) : (256 / 
 k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     constexpr bool F64 = sizeof(Real) == 8;
     constexpr int NW = TPP / 32;
+    // the run has stopped (set by the energy check between steps, so every
+    // thread of the block reads the same value)
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
     __shared__ R4<Real> s_z[kMaxRow];                         // zeta~_k, lattice units
     __shared__ R4<Real> s_y[kMaxRow];                         // Ydot_k, m/s
     __shared__ double s_p[F64 ? 3 : 1][F64 ? kMaxRow : 1];    // FP64: absolute x_k
@@ -531,6 +535,7 @@ __global__ void __launch_bounds__(kWarpPointsPerBlock * 32)
 k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     constexpr bool F64 = sizeof(Real) == 8;
     constexpr int kIt = kMaxRow / 32;
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;   // the run has stopped
     __shared__ Real s_e[kWarpPointsPerBlock][3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int i = blockIdx.x * kWarpPointsPerBlock + wib;       // one warp per point
@@ -634,7 +639,8 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
 
 __global__ void __launch_bounds__(1024)
 k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
-                const int32_t* row_ptr, int npoints) {
+                const int32_t* row_ptr, int npoints, int halt) {
+    if (halt && (ctr->status & PPM_STATUS_HALTED)) return;     // the run has stopped
     __shared__ double sm[3][1024];
     double t[3] = {0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
@@ -657,9 +663,17 @@ k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
             ctr->W_int += sm[0][0];
             ctr->W_ext += sm[1][0];
             ctr->W_kin = sm[2][0];
+            ctr->steps_done += 1;
             const double bal = fabs(ctr->W_int + ctr->W_kin - ctr->W_ext - ctr->W_kin0);
             const double mx = fmax(fmax(ctr->W_kin, fabs(ctr->W_int)), fmax(fabs(ctr->W_ext), ctr->W_kin0));
-            if (bal > 1e-2 * mx) atomicOr(&ctr->status, PPM_STATUS_UNSTABLE);   // Eq. 69
+            if (bal > 1e-2 * mx) {                                         // Eq. 69
+                atomicOr(&ctr->status, PPM_STATUS_UNSTABLE);
+                if (halt && !(ctr->status & PPM_STATUS_HALTED)) {
+                    // hard stop: the following steps' kernels find this bit and return
+                    atomicOr(&ctr->status, PPM_STATUS_HALTED);
+                    ctr->halted_step = (long long)ctr->steps_done;
+                }
+            }
         }
     }
 }
@@ -767,8 +781,8 @@ cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt
 }
 
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
-                                 const int32_t* row_ptr, int npoints, cudaStream_t st) {
-    k_energy_reduce<<<1, 1024, 0, st>>>(epart, nblocks, ctr, initial, row_ptr, npoints);
+                                 const int32_t* row_ptr, int npoints, int halt, cudaStream_t st) {
+    k_energy_reduce<<<1, 1024, 0, st>>>(epart, nblocks, ctr, initial, row_ptr, npoints, halt);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ struct DevCounters {
     unsigned int status, pad;
     int family_ok, pad2;
     double W_int, W_ext, W_kin, W_kin0;
+    unsigned long long steps_done;   // completed (not halted) steps
+    long long halted_step;           // the step whose energy check halted the run
 };
 
 // uniform cell grid of the family search (device-computed)
@@ -57,6 +59,7 @@ struct StepConst {
     float load_ratef;
     int elastic;                 // 1: linear elastic skeleton, the yield test off
     int load_layers;             // bc = 1: planes held / driven at each x end
+    int halt;                    // 1: the Eq. 69 check stops the run (kernels skip)
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
@@ -163,7 +166,7 @@ template <typename Real>
 cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt, int initial,
                           int gather_blocks, cudaStream_t st);
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
-                                 const int32_t* row_ptr, int npoints, cudaStream_t st);
+                                 const int32_t* row_ptr, int npoints, int halt, cudaStream_t st);
 
 // ---- launchers (adjoint.cu) ----
 // one reverse step from the restored start state (predictor already

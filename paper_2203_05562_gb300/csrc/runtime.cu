@@ -84,6 +84,7 @@ int check_params(const ppm_params* p) {
         return PPM_EINVAL;
     if (p->elastic != 0 && p->elastic != 1) return PPM_EINVAL;
     if (p->load_layers < 0) return PPM_EINVAL;
+    if (p->halt_on_unstable != 0 && p->halt_on_unstable != 1) return PPM_EINVAL;
     return PPM_OK;
 }
 
@@ -239,7 +240,8 @@ int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
     }
     CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
     CU(launch_gather<Real>(s, c->k, 0.0, 1, c->gather_blocks, c->stream));
-    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 1, s.row_ptr, c->k.npoints, c->stream));
+    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 1, s.row_ptr, c->k.npoints, c->k.halt,
+                            c->stream));
     c->launches += 4;
     return PPM_OK;
 }
@@ -258,7 +260,8 @@ int issue_step(ppm_ctx* c, const DevState<Real>& s, bool rebuild, cudaStream_t s
     CU(launch_bond<Real>(s, c->k, c->k.dt, 1, st));
     if (ev) CU(cudaEventRecord(ev[2], st));
     CU(launch_gather<Real>(s, c->k, c->k.dt, 0, c->gather_blocks, st));
-    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 0, s.row_ptr, c->k.npoints, st));
+    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 0, s.row_ptr, c->k.npoints, c->k.halt,
+                            st));
     if (ev) CU(cudaEventRecord(ev[3], st));
     return PPM_OK;
 }
@@ -709,6 +712,7 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.load_rate = p->load_rate;
     k.load_ratef = (float)p->load_rate;
     k.elastic = p->elastic;
+    k.halt = p->halt_on_unstable;
     k.load_layers = p->load_layers > 0 ? p->load_layers : (int)p->horizon_factor;
     if (k.load_layers < 1) k.load_layers = 1;
     k.npoints = (int)c->N;
@@ -866,6 +870,7 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     out->pairs = (int64_t)h.pairs;
     out->returns_fp64 = (int64_t)h.ret64;
     out->bond_tile = c->k.tile;
+    out->halted_step = (int32_t)h.halted_step;
     out->launches = c->launches;
     out->status = h.status;
     out->W_int = h.W_int;
@@ -901,7 +906,7 @@ int ppm_adjoint_workspace_size(const ppm_ctx* c, int n_steps, int ckpt_every, si
 
 int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, size_t bytes) {
     if (!c || n_steps < 0 || ckpt_every < 1 || !d_ws || ((uintptr_t)d_ws & 255u)) return PPM_EINVAL;
-    if (c->started || c->ncols != 1 || c->p.model == 2) return PPM_ESTATE;
+    if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable) return PPM_ESTATE;
     if (bytes < adj_layout(c, n_steps, ckpt_every).total) return PPM_ENOSPACE;
     c->adj_ws = (char*)d_ws;
     c->adj_bytes = bytes;

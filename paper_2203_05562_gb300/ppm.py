@@ -19,7 +19,8 @@ FP64, MIXED = 0, 1
 SUBHORIZON, STANDARD, SUBHORIZON_CONJUGATE = 0, 1, 2
 FIELD = dict(u=0, v=1, a=2, sigma=3, pc=4, eps_s=5, fint=6, row_ptr=7, col=8, rev=9, tforce=10)
 _NCOMP = dict(u=3, v=3, a=3, sigma=6, pc=1, eps_s=1, fint=3)
-STATUS_BITS = dict(nonconv=1, singular=2, nonfinite=4, family_full=8, row_full=16, unstable=32)
+STATUS_BITS = dict(nonconv=1, singular=2, nonfinite=4, family_full=8, row_full=16, unstable=32,
+                   halted=64)
 
 
 class PPMError(RuntimeError):
@@ -40,6 +41,7 @@ class Params(C.Structure):
         ("lock_lateral", C.c_int32), ("precision", C.c_int32), ("max_family", C.c_int32),
         ("use_graph", C.c_int32), ("bond_tile", C.c_int32), ("bc", C.c_int32),
         ("load_rate", C.c_double), ("elastic", C.c_int32), ("load_layers", C.c_int32),
+        ("halt_on_unstable", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -52,7 +54,7 @@ class Counters(C.Structure):
     _fields_ = [("steps", C.c_int64), ("nbonds", C.c_int64), ("bond_steps", C.c_int64),
                 ("plastic", C.c_int64), ("nonconv", C.c_int64), ("singular", C.c_int64),
                 ("rebuilds", C.c_int64), ("pairs", C.c_int64), ("launches", C.c_int64),
-                ("returns_fp64", C.c_int64), ("bond_tile", C.c_int32), ("pad2_", C.c_int32),
+                ("returns_fp64", C.c_int64), ("bond_tile", C.c_int32), ("halted_step", C.c_int32),
                 ("status", C.c_uint32), ("pad_", C.c_uint32),
                 ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double),
                 ("W_kin0", C.c_double)]

@@ -35,6 +35,7 @@ MATERIAL = dict(
     load_rate=0.0,          # m/s, bc = 1
     elastic=0,              # 1: linear elastic skeleton (no yield), as in Sec. 4.1
     load_layers=0,          # bc = 1: planes held / driven at each end; 0: the horizon's thickness
+    halt_on_unstable=0,     # 1: the Eq. 69 energy check stops the run
 )
 
 #: The five workloads: (description, overrides).

@@ -271,3 +271,23 @@ def test_critical_time_step_matches_oracle(precision, tol):
     sim = gpu_run(cfg, 6, precision, v0=v0)
     got, want = sim.critical_time_step(), run.critical_time_step()
     assert np.isfinite(want) and abs(got - want) <= tol * want, (got, want)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_hard_stop_on_the_energy_check_matches_oracle(use_graph):
+    # the Eq. 69 check as a hard stop, decided on the device (so also inside
+    # CUDA graphs): the printed Eq. 51 force state under compression fails it
+    cfg = pi.small_config(12, 4, 4, suction=0.0, model=0, bc=1, load_rate=0.05,
+                          gravity=(0.0, 0.0, 0.0), elastic=1, init_stress=1, rebuild_every=0,
+                          halt_on_unstable=1)
+    run = oracle_run(cfg, 300, np.zeros((3, pi.num_points(cfg))))
+    h = run.counters()["halted_step"]
+    assert 0 < h < 300
+    sim = gpu_run(cfg, 300, "fp64", v0=np.zeros((3, pi.num_points(cfg))), use_graph=use_graph)
+    st = sim.status()
+    assert "halted" in st["flags"] and st["halted_step"] == h
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    u = sim.read("u")
+    sim.step(10)
+    assert np.array_equal(sim.read("u"), u)

@@ -73,3 +73,29 @@ def test_the_elastic_skeleton_never_yields():
         run.step(200)
         counts[elastic] = run.counters()["plastic"]
     assert counts[0] > 0 and counts[1] == 0
+
+
+def test_the_energy_check_as_a_hard_stop():
+    # halt_on_unstable: the run stops at the first step whose Eq. 69 balance
+    # fails, and later steps change nothing (the printed Eq. 51 force state
+    # under the compression fails it within a few hundred steps)
+    cfg = dict(loaded_column(0), halt_on_unstable=1)
+    n = pi.num_points(cfg)
+    run = oracle.Run(cfg, np.zeros((3, n)))
+    run.step(300)
+    h = run.counters()["halted_step"]
+    assert 0 < h < 300
+    frozen = run.u.copy(), run.v.copy(), run.sig.copy()
+    run.step(20)
+    assert all(np.array_equal(a, b) for a, b in zip(frozen, (run.u, run.v, run.sig)))
+    # the same run without the stop, one step at a time: the balance first fails at h
+    free = oracle.Run(dict(cfg, halt_on_unstable=0), np.zeros((3, n)))
+    first = None
+    for step in range(1, h + 1):
+        free.step(1)
+        e = free.energies()
+        bal = abs(e["W_int"] + e["W_kin"] - e["W_ext"] - e["W_kin0"])
+        if first is None and bal > 1e-2 * max(e["W_kin"], abs(e["W_int"]), abs(e["W_ext"]), e["W_kin0"]):
+            first = step
+    assert first == h
+    assert np.array_equal(free.u, frozen[0])
