@@ -49,7 +49,7 @@ extern "C" {
 /* device status bits (ppm_counters.status) */
 #define PPM_STATUS_NONCONV        1u  /* a return-map Newton solve did not converge */
 #define PPM_STATUS_SINGULAR       2u  /* a bond had a degenerate shape tensor       */
-#define PPM_STATUS_NONFINITE      4u  /* a non-finite acceleration appeared         */
+#define PPM_STATUS_NONFINITE      4u  /* a non-finite acceleration or velocity      */
 #define PPM_STATUS_FAMILY_FULL    8u  /* bonds exceeded the workspace capacity      */
 #define PPM_STATUS_ROW_FULL      16u  /* a point had more than max_family bonds     */
 #define PPM_STATUS_UNSTABLE      32u  /* energy balance of Eq. 69 above 1e-2        */

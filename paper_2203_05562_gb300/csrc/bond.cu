@@ -603,13 +603,17 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
             const Real f = fhat * dx2;                               // Eq. 49-50
             Real a = fhat * inv_rho_dx + g;                          // Eq. 62
             if (fixed) a = (Real)0;
-            if (!isfinite(a)) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
+            bool bad = !isfinite(a);
             s.fint[t] = f;
             s.a[t] = a;
             if (initial) {
+                bad = bad || !isfinite(v0);
                 wk = (Real)0.5 * m * v0 * v0;
             } else {
                 const Real v = vh + hdt * a;                         // Eq. 63
+                // a point whose position stopped being finite leaves every
+                // family and keeps a finite acceleration: its velocity tells
+                bad = bad || !isfinite(v);
                 s.v[t] = v;
                 dwi = -hdt * vh * (fo + f);                          // Eq. 66
                 dwe = dtr * m * vh * g;                              // Eq. 67
@@ -618,6 +622,7 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
                 if (fixed) dwe += -hdt * vh * (fo + f + (Real)2 * m * g);
                 wk = (Real)0.5 * m * v * v;                          // Eq. 68
             }
+            if (bad) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
         }
     }
     // energies of the point: lanes 0..2 hold the three components

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ppm_internal.cuh"
 
 using namespace ppm;
@@ -48,6 +50,16 @@ struct ppm_ctx {
 namespace {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// NVTX range over a host-side scope (phases of a step, graph launches, the
+// family, adjoint and Eq. 65 calls), for timeline profilers; header-only
+// NVTX costs a few nanoseconds when no tool is attached
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // Offsets of every buffer in the caller's workspace.
 struct Layout {
@@ -196,6 +208,7 @@ size_t workspace_bytes(const ppm_params* p, int ncols, const Sizes& z) {
 
 template <typename Real>
 int run_family(ppm_ctx* c, const DevState<Real>& s) {
+    Range r("ppm family search");
     CU(launch_family_build<Real>(s, c->k, c->stream, &c->launches));
     c->family_built = true;
     return PPM_OK;
@@ -229,6 +242,7 @@ int critical_dt(ppm_ctx* c, const DevState<Real>& s, double* out) {
 
 template <typename Real>
 int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
+    Range r("ppm initial pass");
     CU(launch_apply_velocity_bc<Real>(s, c->k, c->stream));
     if (!c->family_built) {
         int rc = run_family<Real>(c, s);
@@ -253,15 +267,27 @@ template <typename Real>
 int issue_step(ppm_ctx* c, const DevState<Real>& s, bool rebuild, cudaStream_t st,
                cudaEvent_t* ev, long long* nlaunch) {
     if (ev) CU(cudaEventRecord(ev[0], st));
-    CU(launch_predictor<Real>(s, c->k, st));
-    if (rebuild) CU(launch_family_build<Real>(s, c->k, st, nlaunch));
+    {
+        Range r("ppm predictor");
+        CU(launch_predictor<Real>(s, c->k, st));
+    }
+    if (rebuild) {
+        Range r("ppm family search");
+        CU(launch_family_build<Real>(s, c->k, st, nlaunch));
+    }
     *nlaunch += 4;   // predictor, bond, gather, energy reduction
     if (ev) CU(cudaEventRecord(ev[1], st));
-    CU(launch_bond<Real>(s, c->k, c->k.dt, 1, st));
+    {
+        Range r("ppm bond pass");
+        CU(launch_bond<Real>(s, c->k, c->k.dt, 1, st));
+    }
     if (ev) CU(cudaEventRecord(ev[2], st));
-    CU(launch_gather<Real>(s, c->k, c->k.dt, 0, c->gather_blocks, st));
-    CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 0, s.row_ptr, c->k.npoints, c->k.halt,
-                            st));
+    {
+        Range r("ppm gather and energy");
+        CU(launch_gather<Real>(s, c->k, c->k.dt, 0, c->gather_blocks, st));
+        CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 0, s.row_ptr, c->k.npoints,
+                                c->k.halt, st));
+    }
     if (ev) CU(cudaEventRecord(ev[3], st));
     return PPM_OK;
 }
@@ -347,7 +373,10 @@ int do_steps(ppm_ctx* c, const DevState<Real>& s, int n_steps, double* phase_ms)
                 if (rc) return rc;
                 c->segment_len = R;
             }
-            CU(cudaGraphLaunch(c->g_segment, c->stream));
+            {
+                Range r("ppm rebuild period (graph)");
+                CU(cudaGraphLaunch(c->g_segment, c->stream));
+            }
             c->launches += c->launches_segment;
             c->step += R;
             t += R - 1;
@@ -367,7 +396,10 @@ int do_steps(ppm_ctx* c, const DevState<Real>& s, int n_steps, double* phase_ms)
                 int rc = capture_step<Real>(c, s, rebuild, g);
                 if (rc) return rc;
             }
-            CU(cudaGraphLaunch(*g, c->stream));
+            {
+                Range r(rebuild ? "ppm step with family search (graph)" : "ppm step (graph)");
+                CU(cudaGraphLaunch(*g, c->stream));
+            }
             c->launches += rebuild ? c->launches_rebuild : c->launches_plain;
         } else {
             int rc = issue_step<Real>(c, s, rebuild, c->stream, nullptr, &c->launches);
@@ -790,6 +822,7 @@ int ppm_build_families(ppm_ctx* c) {
 
 int ppm_step(ppm_ctx* c, int n_steps) {
     if (!c || n_steps < 0) return PPM_EINVAL;
+    Range r("ppm_step");
     return c->p.precision == PPM_FP64 ? do_steps<double>(c, c->sd, n_steps, nullptr)
                                       : do_steps<float>(c, c->sf, n_steps, nullptr);
 }
@@ -805,6 +838,7 @@ int ppm_step_timed(ppm_ctx* c, int n_steps, double* ms) {
 
 int ppm_critical_time_step(ppm_ctx* c, double* dt) {
     if (!c || !dt) return PPM_EINVAL;
+    Range r("ppm_critical_time_step");
     return c->p.precision == PPM_FP64 ? critical_dt<double>(c, c->sd, dt)
                                       : critical_dt<float>(c, c->sf, dt);
 }
@@ -908,6 +942,7 @@ int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, siz
     if (!c || n_steps < 0 || ckpt_every < 1 || !d_ws || ((uintptr_t)d_ws & 255u)) return PPM_EINVAL;
     if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable) return PPM_ESTATE;
     if (bytes < adj_layout(c, n_steps, ckpt_every).total) return PPM_ENOSPACE;
+    Range r("ppm_adjoint_forward");
     c->adj_ws = (char*)d_ws;
     c->adj_bytes = bytes;
     c->adj_steps = n_steps;
@@ -921,6 +956,7 @@ int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, siz
 int ppm_adjoint_reverse(ppm_ctx* c, const double* dJ_du, int src_is_device, double grad[4]) {
     if (!c || !dJ_du || !grad) return PPM_EINVAL;
     if (!c->adj_ready) return PPM_ESTATE;
+    Range r("ppm_adjoint_reverse");
     const AdjLayout L = adj_layout(c, c->adj_steps, c->adj_every);
     const double* d_src = dJ_du;
     if (!src_is_device) {
