@@ -126,7 +126,17 @@ typedef struct {
                                     (PPM_STATUS_HALTED, halted_step); decided
                                     on the device, so it also holds inside CUDA
                                     graphs.  Not with the adjoint calls.      */
-    int32_t pad_;
+    int32_t contact;             /* 1: the column rests on a rigid flat substrate
+                                    (Sec. 4.2, Eq. 91-93) instead of a fixed base
+                                    layer: the plane z = -contact_cutoff * dx;
+                                    a point at distance d < delta_c is pushed
+                                    up by C_s dx^2 (delta_c - d) / delta_c and
+                                    held by Coulomb friction mu_f on its
+                                    tangential velocity.  Not with the adjoint
+                                    calls.                                      */
+    double contact_modulus;      /* C_s (Pa), contact = 1                      */
+    double friction;             /* mu_f, contact = 1                          */
+    double contact_cutoff;       /* delta_c / dx, contact = 1                  */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */

@@ -669,7 +669,7 @@ static int is_base(const ppmo_params* p, int64_t id) {
 static int constrained(const ppmo_params* p, int64_t id, int c, double* vbar) {
     *vbar = 0.0;
     if (p->lock_lateral && c < 2) return 1;
-    if (p->bc == 0) return is_base(p, id);
+    if (p->bc == 0) return !p->contact && is_base(p, id);
     if (c != 0) return 0;
     const int64_t ix = id % p->nx;
     int64_t nl = p->load_layers > 0 ? p->load_layers : (int64_t)p->horizon_factor;
@@ -680,6 +680,39 @@ static int constrained(const ppmo_params* p, int64_t id, int c, double* vbar) {
         return 1;
     }
     return 0;
+}
+
+/* Contact with a rigid flat substrate (Sec. 4.2, Eq. 91-93; readings
+ * R31-R33): the substrate is the plane z = -delta_c below the bottom layer;
+ * each point's virtual bond goes to its projection on the plane.  At a
+ * distance d < delta_c the normal force is C_s dx^2 (delta_c - d) / delta_c
+ * (the contact modulus on the point's tributary area), and Coulomb friction
+ * opposes the tangential velocity the point would have at the end of the
+ * half step without it, |F_t| <= mu_f F_n, limited so that it never
+ * reverses that velocity.  The forces are added to f (x: positions, w: the
+ * velocity the step starts the half step from, hdt: half the step). */
+static void add_contact(const ppmo_params* p, int64_t n, const double* x, const double* w,
+                        double hdt, double m, double* f) {
+    const double dc = p->contact_cutoff * p->dx;
+    const double zs = -dc;
+    for (int64_t i = 0; i < n; i++) {
+        const double d = x[2 * n + i] - zs;
+        if (!(d < dc)) continue;
+        const double Fn = p->contact_modulus * p->dx * p->dx * (dc - d) / dc;
+        f[2 * n + i] += Fn;
+        if (p->friction > 0.0 && hdt > 0.0) {
+            double vt[2], nrm = 0.0;
+            for (int c = 0; c < 2; c++) {
+                vt[c] = w[c * n + i] + hdt * (f[c * n + i] / m + p->gravity[c]);
+                nrm += vt[c] * vt[c];
+            }
+            nrm = sqrt(nrm);
+            if (nrm > 0.0) {
+                const double Ft = fmin(p->friction * Fn, m * nrm / hdt);
+                for (int c = 0; c < 2; c++) f[c * n + i] -= Ft * vt[c] / nrm;
+            }
+        }
+    }
 }
 
 static void current_positions(const ppmo_params* p, int64_t n, const double* u, double* x) {
@@ -755,6 +788,7 @@ int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* 
     if (rc < 0) { free(x); return rc; }
     bond_pass(p, n, x, s->v, 0.0, s->row_ptr, s->col, s->rev, s->cap, s->sig, s->pc,
               s->eps_s, 0, s->tforce, s->fint, NULL);
+    if (p->contact) add_contact(p, n, x, s->v, 0.5 * ppmo_time_step(p), m, s->fint);
     double wk = 0.0;
     for (int64_t i = 0; i < n; i++)
         for (int c = 0; c < 3; c++) {
@@ -809,6 +843,7 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         s->n_plastic += pcnt.plastic;
         s->n_nonconv += pcnt.nonconv;
         s->n_singular += pcnt.singular;
+        if (p->contact) add_contact(p, n, x, vh, 0.5 * dt, m, s->fint);
         /* acceleration and velocity corrector, Eq. 62-63 */
         double dWi = 0.0, dWe = 0.0, wk = 0.0;
         for (int64_t i = 0; i < n; i++)
@@ -1196,7 +1231,8 @@ static int is_top(const ppmo_params* p, int64_t id) {
 
 int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps, int64_t cap,
                             double* J, double grad[4]) {
-    if (!params_ok(p) || p->model == 2 || n_steps < 0) return -1;
+    if (!params_ok(p) || p->model == 2 || n_steps < 0 || p->contact || p->halt_on_unstable)
+        return -1;
     const int64_t n = (int64_t)p->nx * p->ny * p->nz;
     ppmo_state s;
     memset(&s, 0, sizeof(s));

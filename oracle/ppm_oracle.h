@@ -58,7 +58,12 @@ typedef struct {
                                     horizon's thickness                        */
     int32_t halt_on_unstable;    /* 1: once a step fails the Eq. 69 check, later
                                     steps change nothing                      */
-    int32_t pad_;
+    int32_t contact;             /* 1: a rigid flat substrate at z = -delta_c
+                                    (Sec. 4.2, Eq. 91-93, readings R31-R33)
+                                    instead of the fixed base layer           */
+    double contact_modulus;      /* C_s (Pa)                                   */
+    double friction;             /* mu_f                                       */
+    double contact_cutoff;       /* delta_c / dx                               */
 } ppmo_params;
 
 typedef struct {

@@ -596,12 +596,53 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
                 }
             }
         }
+        // contact with the rigid substrate (Sec. 4.2, Eq. 91-93; readings
+        // R31-R33): the plane z = -delta_c below the bottom layer; normal
+        // force C_s dx^2 (delta_c - d) / delta_c at a distance d < delta_c,
+        // Coulomb friction on the tangential velocity the point would have
+        // after the half step without it, never reversing that velocity
+        Real fcon = (Real)0;
+        if (k.contact) {
+            const Real tsx = __shfl_sync(0xffffffffu, ts, 0), tsy = __shfl_sync(0xffffffffu, ts, 1);
+            if (lane < 3) {
+                const int li = s.lat[i];
+                Real z;
+                if constexpr (F64) z = __dadd_rn(__dmul_rn((double)lat_z(li), k.dx), (double)s.u[2 * n + i]);
+                else z = (float)lat_z(li) * k.dxf + s.u[2 * n + i];
+                const Real dc = F64 ? (Real)k.contact_dc : (Real)k.contact_dcf;
+                const Real d = z + dc;
+                if (d < dc) {
+                    const Real Fn = F64 ? (Real)(k.contact_modulus * k.dx * k.dx) * (dc - d) / dc
+                                        : (Real)k.contact_kf * (dc - d) / dc;
+                    if (c == 2) {
+                        fcon = Fn;
+                    } else if (k.friction > 0.0) {
+                        const Real hdc = F64 ? (Real)(0.5 * k.dt) : (Real)k.hdtf;
+                        const Real* w = initial ? s.v : s.vh;
+                        const Real gx = F64 ? (Real)k.g[0] : (Real)k.gf[0];
+                        const Real gy = F64 ? (Real)k.g[1] : (Real)k.gf[1];
+                        const Real vtx = w[i] + hdc * ((tsx - (sum[0] + cmp[0])) * dx2 / m + gx);
+                        const Real vty = w[n + i] + hdc * ((tsy - (sum[1] + cmp[1])) * dx2 / m + gy);
+                        const Real nrm = sqrt(vtx * vtx + vty * vty);
+                        if (nrm > (Real)0) {
+                            const Real mu = F64 ? (Real)k.friction : (Real)k.frictionf;
+                            const Real Ft = fmin(mu * Fn, m * nrm / hdc);
+                            fcon = -Ft * (c == 0 ? vtx : vty) / nrm;
+                        }
+                    }
+                }
+            }
+        }
         if (lane < 3) {
             const Real g = F64 ? (Real)k.g[c] : (Real)k.gf[c];
             const Real gathered = c == 0 ? sum[0] + cmp[0] : (c == 1 ? sum[1] + cmp[1] : sum[2] + cmp[2]);
             const Real fhat = ts - gathered;
-            const Real f = fhat * dx2;                               // Eq. 49-50
+            Real f = fhat * dx2;                                     // Eq. 49-50
             Real a = fhat * inv_rho_dx + g;                          // Eq. 62
+            if (k.contact) {
+                f += fcon;                                           // Eq. 93
+                a = f / m + g;
+            }
             if (fixed) a = (Real)0;
             bool bad = !isfinite(a);
             s.fint[t] = f;

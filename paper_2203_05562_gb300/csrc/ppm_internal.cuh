@@ -60,6 +60,9 @@ struct StepConst {
     int elastic;                 // 1: linear elastic skeleton, the yield test off
     int load_layers;             // bc = 1: planes held / driven at each x end
     int halt;                    // 1: the Eq. 69 check stops the run (kernels skip)
+    int contact;                 // 1: rigid flat substrate at z = -delta_c (no fixed base)
+    double contact_modulus, friction, contact_dc;   // C_s (Pa), mu_f, delta_c (m)
+    float contact_kf, frictionf, contact_dcf;        // C_s dx^2, mu_f, delta_c in FP32
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
@@ -106,8 +109,8 @@ struct DevState {
 
 // Boundary conditions (the fixed base; the loading of Sec. 4.1): true when
 // velocity component c of point i is prescribed, with the value in vbar.
-// bc = 0: the base layer and, with lock_lateral, the x and y components are
-// held at zero.  bc = 1: the load_layers planes at the x = 0 end of the
+// bc = 0: the base layer (unless the substrate carries the column) and, with
+// lock_lateral, the x and y components are held at zero.  bc = 1: the load_layers planes at the x = 0 end of the
 // point's column are held in x and those at the other end move at
 // v_x = -load_rate.
 template <typename Real>
@@ -116,7 +119,7 @@ __device__ __forceinline__ bool prescribed(const DevState<Real>& s, const StepCo
     vbar = (Real)0;
     if (k.lock_lateral && c < 2) return true;
     const int li = s.lat[i];
-    if (k.bc == 0) return lat_z(li) == 0;
+    if (k.bc == 0) return !k.contact && lat_z(li) == 0;
     if (c != 0) return false;
     const int ix = lat_x(li);
     if (ix < k.load_layers) return true;

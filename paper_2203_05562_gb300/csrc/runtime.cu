@@ -97,6 +97,10 @@ int check_params(const ppm_params* p) {
     if (p->elastic != 0 && p->elastic != 1) return PPM_EINVAL;
     if (p->load_layers < 0) return PPM_EINVAL;
     if (p->halt_on_unstable != 0 && p->halt_on_unstable != 1) return PPM_EINVAL;
+    if (p->contact != 0 && p->contact != 1) return PPM_EINVAL;
+    if (p->contact && (!(p->contact_modulus >= 0) || !(p->friction >= 0) || !(p->contact_cutoff > 0) ||
+                       !std::isfinite(p->contact_modulus) || !std::isfinite(p->friction)))
+        return PPM_EINVAL;
     return PPM_OK;
 }
 
@@ -745,6 +749,13 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.load_ratef = (float)p->load_rate;
     k.elastic = p->elastic;
     k.halt = p->halt_on_unstable;
+    k.contact = p->contact;
+    k.contact_modulus = p->contact_modulus;
+    k.friction = p->friction;
+    k.contact_dc = p->contact_cutoff * p->dx;
+    k.contact_kf = (float)(p->contact_modulus * p->dx * p->dx);
+    k.frictionf = (float)p->friction;
+    k.contact_dcf = (float)(p->contact_cutoff * p->dx);
     k.load_layers = p->load_layers > 0 ? p->load_layers : (int)p->horizon_factor;
     if (k.load_layers < 1) k.load_layers = 1;
     k.npoints = (int)c->N;
@@ -940,7 +951,8 @@ int ppm_adjoint_workspace_size(const ppm_ctx* c, int n_steps, int ckpt_every, si
 
 int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, size_t bytes) {
     if (!c || n_steps < 0 || ckpt_every < 1 || !d_ws || ((uintptr_t)d_ws & 255u)) return PPM_EINVAL;
-    if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable) return PPM_ESTATE;
+    if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable || c->p.contact)
+        return PPM_ESTATE;
     if (bytes < adj_layout(c, n_steps, ckpt_every).total) return PPM_ENOSPACE;
     Range r("ppm_adjoint_forward");
     c->adj_ws = (char*)d_ws;

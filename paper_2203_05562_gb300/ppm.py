@@ -41,7 +41,8 @@ class Params(C.Structure):
         ("lock_lateral", C.c_int32), ("precision", C.c_int32), ("max_family", C.c_int32),
         ("use_graph", C.c_int32), ("bond_tile", C.c_int32), ("bc", C.c_int32),
         ("load_rate", C.c_double), ("elastic", C.c_int32), ("load_layers", C.c_int32),
-        ("halt_on_unstable", C.c_int32), ("pad_", C.c_int32),
+        ("halt_on_unstable", C.c_int32), ("contact", C.c_int32),
+        ("contact_modulus", C.c_double), ("friction", C.c_double), ("contact_cutoff", C.c_double),
     ]
 
 

@@ -36,6 +36,10 @@ MATERIAL = dict(
     elastic=0,              # 1: linear elastic skeleton (no yield), as in Sec. 4.1
     load_layers=0,          # bc = 1: planes held / driven at each end; 0: the horizon's thickness
     halt_on_unstable=0,     # 1: the Eq. 69 energy check stops the run
+    contact=0,              # 1: rigid flat substrate (Sec. 4.2) instead of the fixed base
+    contact_modulus=4e6,    # C_s, Pa (Sec. 4.2)
+    friction=0.25,          # mu_f (Sec. 4.2)
+    contact_cutoff=0.8,     # delta_c / dx (Sec. 4.2)
 )
 
 #: The five workloads: (description, overrides).

@@ -291,3 +291,35 @@ def test_hard_stop_on_the_energy_check_matches_oracle(use_graph):
     u = sim.read("u")
     sim.step(10)
     assert np.array_equal(sim.read("u"), u)
+
+
+def test_substrate_contact_sliding_slab_matches_oracle():
+    # Sec. 4.2: a one-layer slab sliding on the rigid substrate under friction
+    cfg = pi.small_config(6, 6, 1, suction=0.0, elastic=1, init_stress=1, contact=1,
+                          friction=0.25, rebuild_every=0, model=1)
+    n = pi.num_points(cfg)
+    v0 = np.zeros((3, n)); v0[0] = 0.1; v0[1] = 0.03
+    run = oracle_run(cfg, 400, v0)
+    for precision, tol, norm in (("fp64", FP64_TOL, rel_inf), ("mixed", MIXED_TOL, rel_l2)):
+        sim = gpu_run(cfg, 400, precision, v0=v0)
+        err = state_errors(sim, run, norm=norm)
+        assert err["u"] <= tol and err["v"] <= tol, (precision, err)
+
+
+@pytest.mark.parametrize("model", [0, 2])
+def test_column_on_the_substrate_matches_oracle(model):
+    # a plastic column resting on the substrate instead of a fixed base
+    cfg = pi.small_config(6, 5, 8, suction=50e3, contact=1, model=model, rebuild_every=2)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=23)
+    run = oracle_run(cfg, 12, v0)
+    assert run.counters()["plastic"] > 0
+    sim = gpu_run(cfg, 12, "fp64", v0=v0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    st, ce = sim.status(), run.energies()
+    for key in ("W_int", "W_ext", "W_kin"):
+        scale = max(abs(ce["W_int"]), abs(ce["W_ext"]), ce["W_kin"])
+        assert abs(st[key] - ce[key]) <= FP64_TOL * scale, key
+    sim = gpu_run(cfg, 12, "mixed", v0=v0)
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["u"] <= MIXED_TOL, err
