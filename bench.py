@@ -144,6 +144,83 @@ def uniaxial_compression(steps: int, tile: int, early: int = 10000):
     return out
 
 
+def runout_config(aspect: float, friction: float, suction: float) -> dict:
+    """The soil column collapse of Sec. 4.2, synthetic and in 3-D: a square
+    column 0.1 m wide (40 points at 2.5 mm) and 0.1 / aspect high resting on
+    the rigid substrate (C_s = 4 MPa, delta_c = 0.8 dx, friction mu_f),
+    released from the K0 geostatic state at a constant suction, with the
+    preconsolidation pressure 1.25 x the initial mean effective stress at the
+    base (the geostatic part plus S_r s: over-consolidation ratio 1.25
+    there), the power-conjugate sub-horizon force state, the family rebuilt
+    every 50 steps."""
+    dx, nx = 0.0025, 40
+    nz = int(round(0.1 / aspect / dx))
+    m = pi.MATERIAL
+    nu = (3 * m["K"] - 2 * m["mu"]) / (2 * (3 * m["K"] + m["mu"]))
+    k0 = nu / (1 - nu)
+    p_base = (1 + 2 * k0) / 3 * m["rho"] * -m["gravity"][2] * (nz - 1) * dx
+    n_vg = m["vg_n"]
+    s_r = (1 + (m["vg_alpha"] * suction) ** n_vg) ** -(1 - 1 / n_vg)
+    return pi.small_config(nx, nx, nz, dx=dx, suction=suction, model=2, contact=1,
+                           friction=friction, pc0=1.25 * (p_base + s_r * suction),
+                           rebuild_every=50, energy_tol=5e-2)
+
+
+def runout_shape(sim, cfg) -> dict:
+    """Run-out (largest horizontal distance from the column's axis over the
+    initial half-width) and deposit height (over the initial height)."""
+    nx, ny, nz, dx = cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"]
+    i = np.arange(nx * ny * nz)
+    x = np.stack([i % nx, i // nx % ny, i // (nx * ny)]) * dx + sim.read("u").astype(np.float64)
+    c = (cfg["nx"] - 1) * cfg["dx"] / 2
+    return {"runout": float(np.maximum(np.abs(x[0] - c), np.abs(x[1] - c)).max() / c),
+            "height": float(x[2].max() / ((cfg["nz"] - 1) * cfg["dx"]))}
+
+
+def collapse_runout(tile: int) -> list:
+    """Sec. 4.2.1-4.2.3 on the substrate: the dry column at aspect 2 on a
+    smooth, an intermediate and a rough substrate (mu_f = 0, 0.25, 0.5), at
+    suctions 25 and 50 kPa (mu_f = 0.25), and at aspect 1, each to the end
+    time of the paper's snapshots for that aspect."""
+    import torch
+    from paper_2203_05562_gb300 import Simulation
+    runs = [(2.0, 0.0, 0.0), (2.0, 0.25, 0.0), (2.0, 0.5, 0.0),
+            (2.0, 0.25, 25e3), (2.0, 0.25, 50e3), (1.0, 0.25, 0.0)]
+    t_end = {2.0: 0.25, 1.0: 0.4}
+    out = []
+    for aspect, friction, suction in runs:
+        cfg = runout_config(aspect, friction, suction)
+        sim = Simulation(cfg, precision="mixed", bond_tile=tile)
+        steps = int(round(t_end[aspect] / sim.dt / 50)) * 50
+        r = {"aspect": aspect, "friction": friction, "suction_Pa": suction,
+             "points": sim.n, "steps": steps, "t_end_s": steps * sim.dt, "snapshots": []}
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, done = 0.0, 0
+        for q in (1, 2, 3, 4):
+            upto = steps * q // 4 // 50 * 50
+            ev0.record(sim.stream)
+            sim.step(upto - done)
+            ev1.record(sim.stream)
+            torch.cuda.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            done = upto
+            st = sim.status()
+            r["snapshots"].append(dict(runout_shape(sim, cfg), t_s=done * sim.dt, flags=st["flags"],
+                                       unstable_step=st["unstable_step"], W_kin=st["W_kin"],
+                                       eq69_residual_over_max=eq69_ratio(st)))
+        st = sim.status()
+        r.update(ms_per_step=ms / steps, bond_steps_per_s=st["bond_steps"] / (ms * 1e-3))
+        out.append(r)
+        del sim
+    return out
+
+
+def eq69_ratio(st) -> float:
+    """|W_int + W_kin - W_ext - W_kin0| over the largest of the four terms."""
+    bal = abs(st["W_int"] + st["W_kin"] - st["W_ext"] - st["W_kin0"])
+    return bal / max(st["W_kin"], abs(st["W_int"]), abs(st["W_ext"]), st["W_kin0"])
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -304,6 +381,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--standard-steps", type=int, default=100)
     ap.add_argument("--no-uniaxial", action="store_true")
+    ap.add_argument("--runout", action="store_true",
+                    help="also run the column-collapse run-out study of Sec. 4.2 (about 4 min)")
     ap.add_argument("--uniaxial-steps", type=int, default=33334,
                     help="steps of the Sec. 4.1 test (0.1 s at dt = 3e-6 s)")
     ap.add_argument("--no-ensemble", action="store_true")
@@ -459,11 +538,17 @@ def main():
         g = asim.adjoint_reverse(dJ)
         torch.cuda.synchronize()
         tc = time.perf_counter()
+        # the reverse call leaves the context at the final state: repeat it
+        # warm (the first call's time varies between boxes by about 1.3 s)
+        g2 = asim.adjoint_reverse(dJ)
+        torch.cuda.synchronize()
+        td = time.perf_counter()
         adj = {"workload": "adjoint_40x40x80", "steps": acfg["steps"], "ckpt_every": acfg["ckpt_every"],
                "objective": float((u[0:2, -nxy:] ** 2).sum()),
                "grad": {"M": g[0], "eta": g[1], "suction": g[2], "pc0": g[3]},
-               "forward_s": tb - ta, "reverse_s": tc - tb,
-               "reverse_over_forward": (tc - tb) / (tb - ta)}
+               "repeat_bitwise_equal": bool(np.array_equal(np.asarray(g), np.asarray(g2))),
+               "forward_s": tb - ta, "reverse_s": td - tc, "reverse_first_call_s": tc - tb,
+               "reverse_over_forward": (td - tc) / (tb - ta)}
         del asim
 
     # ---- FP64 path on the same column (fewer steps: FP64 is ~1/64 rate) ----
@@ -476,6 +561,12 @@ def main():
     if not args.no_uniaxial:
         uniaxial = {"workload": "uniaxial_40x15x20 (Sec. 4.1, dynamic loading, elastic skeleton)",
                     "runs": uniaxial_compression(args.uniaxial_steps, tile)}
+
+    # ---- run-out of the column collapse on the substrate (Sec. 4.2, opt-in) ----
+    runout = None
+    if args.runout:
+        runout = {"workload": "collapse on the substrate, 40 x 40 x 0.1/(aspect dx), dx 2.5 mm",
+                  "runs": collapse_runout(tile)}
 
     # ---- standard correspondence (model 1) on the same column ----
     simS, figS = time_path(dict(cfg, model=1), "mixed", args.standard_steps, args.warmup, barrier)
@@ -542,11 +633,13 @@ def main():
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
             "hbm": hbm, "standard_model": standard, "uniaxial_compression": uniaxial,
+            "collapse_runout": runout,
             "critical_time_step": critical,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "large": large, "adjoint": adj,
             "clocks": clocks, "gpu_launches": fig["launches"],
-            "status": {k: st[k] for k in ("plastic", "nonconv", "singular", "flags")},
+            "status": dict({k: st[k] for k in ("plastic", "nonconv", "singular", "flags", "unstable_step")},
+                           eq69_residual_over_max_at_end=eq69_ratio(st)),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

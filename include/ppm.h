@@ -137,6 +137,8 @@ typedef struct {
     double contact_modulus;      /* C_s (Pa), contact = 1                      */
     double friction;             /* mu_f, contact = 1                          */
     double contact_cutoff;       /* delta_c / dx, contact = 1                  */
+    double energy_tol;           /* the tolerance of the Eq. 69 check (> 0), or
+                                    0 for 1e-2; the paper gives its order only */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */
@@ -163,7 +165,8 @@ typedef struct {
     int32_t halted_step;         /* PPM_STATUS_HALTED: the step whose energy
                                     check failed (counted from 1), else 0     */
     uint32_t status;             /* PPM_STATUS_* bits                           */
-    uint32_t pad_;
+    int32_t unstable_step;       /* PPM_STATUS_UNSTABLE: the first step that
+                                    failed the Eq. 69 check (from 1), else 0  */
     double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */
 } ppm_counters;
 

@@ -55,6 +55,7 @@ class Params(C.Structure):
         ("elastic", C.c_int32), ("load_layers", C.c_int32),
         ("halt_on_unstable", C.c_int32), ("contact", C.c_int32),
         ("contact_modulus", C.c_double), ("friction", C.c_double), ("contact_cutoff", C.c_double),
+        ("energy_tol", C.c_double),
     ]
 
 
@@ -69,6 +70,7 @@ class State(C.Structure):
         ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double), ("W_kin0", C.c_double),
         ("n_plastic", C.c_int64), ("n_nonconv", C.c_int64), ("n_singular", C.c_int64),
         ("n_overflow", C.c_int64), ("unstable", C.c_int64), ("halted_step", C.c_int64),
+        ("unstable_step", C.c_int64),
     ]
 
 
@@ -346,4 +348,5 @@ class Run:
     def counters(self):
         s = self.s
         return dict(plastic=s.n_plastic, nonconv=s.n_nonconv, singular=s.n_singular,
-                    overflow=s.n_overflow, unstable=s.unstable, halted_step=s.halted_step)
+                    overflow=s.n_overflow, unstable=s.unstable, halted_step=s.halted_step,
+                    unstable_step=s.unstable_step)

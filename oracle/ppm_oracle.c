@@ -141,6 +141,7 @@ static int params_ok(const ppmo_params* p) {
     if (p->b1 != 0.0 || p->b2 != 1.0) return 0;
     if (p->model < 0 || p->model > 2) return 0;
     if (p->newton_max_iter < 1 || !(p->newton_tol > 0)) return 0;
+    if (!(p->energy_tol >= 0) || !isfinite(p->energy_tol)) return 0;
     return 1;
 }
 
@@ -803,6 +804,7 @@ int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* 
     s->n_plastic = s->n_nonconv = s->n_singular = 0;
     s->unstable = 0;
     s->halted_step = 0;
+    s->unstable_step = 0;
     return 0;
 }
 
@@ -873,7 +875,8 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         /* the energy check of Eq. 69 (R20): diagnostic, or a hard stop */
         const double bal = fabs(s->W_int + s->W_kin - s->W_ext - s->W_kin0);
         const double mx = fmax(fmax(s->W_kin, fabs(s->W_int)), fmax(fabs(s->W_ext), s->W_kin0));
-        if (bal > 1e-2 * mx) {
+        if (bal > (p->energy_tol > 0 ? p->energy_tol : 1e-2) * mx) {
+            if (!s->unstable) s->unstable_step = s->step;
             s->unstable = 1;
             if (p->halt_on_unstable && !s->halted_step) s->halted_step = s->step;
         }

@@ -64,6 +64,7 @@ typedef struct {
     double contact_modulus;      /* C_s (Pa)                                   */
     double friction;             /* mu_f                                       */
     double contact_cutoff;       /* delta_c / dx                               */
+    double energy_tol;           /* tolerance of the Eq. 69 check; 0 = 1e-2    */
 } ppmo_params;
 
 typedef struct {
@@ -81,8 +82,9 @@ typedef struct {
     int64_t step;
     double W_int, W_ext, W_kin, W_kin0;
     int64_t n_plastic, n_nonconv, n_singular, n_overflow;
-    int64_t unstable;            /* 1 once a step failed the Eq. 69 check (1e-2)  */
+    int64_t unstable;            /* 1 once a step failed the Eq. 69 check         */
     int64_t halted_step;         /* halt_on_unstable: that step (from 1), else 0  */
+    int64_t unstable_step;       /* the first step that failed it (from 1), else 0 */
 } ppmo_state;
 
 /* Eq. (15) replaced by the van Genuchten curve (see DESIGN readings). */

@@ -685,7 +685,7 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
 
 __global__ void __launch_bounds__(1024)
 k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
-                const int32_t* row_ptr, int npoints, int halt) {
+                const int32_t* row_ptr, int npoints, int halt, double tol) {
     if (halt && (ctr->status & PPM_STATUS_HALTED)) return;     // the run has stopped
     __shared__ double sm[3][1024];
     double t[3] = {0.0, 0.0, 0.0};
@@ -712,7 +712,8 @@ k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
             ctr->steps_done += 1;
             const double bal = fabs(ctr->W_int + ctr->W_kin - ctr->W_ext - ctr->W_kin0);
             const double mx = fmax(fmax(ctr->W_kin, fabs(ctr->W_int)), fmax(fabs(ctr->W_ext), ctr->W_kin0));
-            if (bal > 1e-2 * mx) {                                         // Eq. 69
+            if (bal > tol * mx) {                                          // Eq. 69
+                if (!(ctr->status & PPM_STATUS_UNSTABLE)) ctr->unstable_step = (long long)ctr->steps_done;
                 atomicOr(&ctr->status, PPM_STATUS_UNSTABLE);
                 if (halt && !(ctr->status & PPM_STATUS_HALTED)) {
                     // hard stop: the following steps' kernels find this bit and return
@@ -827,8 +828,9 @@ cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt
 }
 
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
-                                 const int32_t* row_ptr, int npoints, int halt, cudaStream_t st) {
-    k_energy_reduce<<<1, 1024, 0, st>>>(epart, nblocks, ctr, initial, row_ptr, npoints, halt);
+                                 const int32_t* row_ptr, int npoints, int halt, double tol,
+                                 cudaStream_t st) {
+    k_energy_reduce<<<1, 1024, 0, st>>>(epart, nblocks, ctr, initial, row_ptr, npoints, halt, tol);
     return cudaGetLastError();
 }
 

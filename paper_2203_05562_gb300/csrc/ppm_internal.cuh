@@ -37,6 +37,7 @@ struct DevCounters {
     double W_int, W_ext, W_kin, W_kin0;
     unsigned long long steps_done;   // completed (not halted) steps
     long long halted_step;           // the step whose energy check halted the run
+    long long unstable_step;         // the first step that failed the energy check
 };
 
 // uniform cell grid of the family search (device-computed)
@@ -60,6 +61,7 @@ struct StepConst {
     int elastic;                 // 1: linear elastic skeleton, the yield test off
     int load_layers;             // bc = 1: planes held / driven at each x end
     int halt;                    // 1: the Eq. 69 check stops the run (kernels skip)
+    double energy_tol;           // the Eq. 69 tolerance (resolved: > 0)
     int contact;                 // 1: rigid flat substrate at z = -delta_c (no fixed base)
     double contact_modulus, friction, contact_dc;   // C_s (Pa), mu_f, delta_c (m)
     float contact_kf, frictionf, contact_dcf;        // C_s dx^2, mu_f, delta_c in FP32
@@ -169,7 +171,8 @@ template <typename Real>
 cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt, int initial,
                           int gather_blocks, cudaStream_t st);
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
-                                 const int32_t* row_ptr, int npoints, int halt, cudaStream_t st);
+                                 const int32_t* row_ptr, int npoints, int halt, double tol,
+                                 cudaStream_t st);
 
 // ---- launchers (adjoint.cu) ----
 // one reverse step from the restored start state (predictor already

@@ -98,6 +98,7 @@ int check_params(const ppm_params* p) {
     if (p->load_layers < 0) return PPM_EINVAL;
     if (p->halt_on_unstable != 0 && p->halt_on_unstable != 1) return PPM_EINVAL;
     if (p->contact != 0 && p->contact != 1) return PPM_EINVAL;
+    if (!(p->energy_tol >= 0) || !std::isfinite(p->energy_tol)) return PPM_EINVAL;
     if (p->contact && (!(p->contact_modulus >= 0) || !(p->friction >= 0) || !(p->contact_cutoff > 0) ||
                        !std::isfinite(p->contact_modulus) || !std::isfinite(p->friction)))
         return PPM_EINVAL;
@@ -259,7 +260,7 @@ int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
     CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
     CU(launch_gather<Real>(s, c->k, 0.0, 1, c->gather_blocks, c->stream));
     CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 1, s.row_ptr, c->k.npoints, c->k.halt,
-                            c->stream));
+                            c->k.energy_tol, c->stream));
     c->launches += 4;
     return PPM_OK;
 }
@@ -290,7 +291,7 @@ int issue_step(ppm_ctx* c, const DevState<Real>& s, bool rebuild, cudaStream_t s
         Range r("ppm gather and energy");
         CU(launch_gather<Real>(s, c->k, c->k.dt, 0, c->gather_blocks, st));
         CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 0, s.row_ptr, c->k.npoints,
-                                c->k.halt, st));
+                                c->k.halt, c->k.energy_tol, st));
     }
     if (ev) CU(cudaEventRecord(ev[3], st));
     return PPM_OK;
@@ -749,6 +750,7 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.load_ratef = (float)p->load_rate;
     k.elastic = p->elastic;
     k.halt = p->halt_on_unstable;
+    k.energy_tol = p->energy_tol > 0 ? p->energy_tol : 1e-2;
     k.contact = p->contact;
     k.contact_modulus = p->contact_modulus;
     k.friction = p->friction;
@@ -916,6 +918,7 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     out->returns_fp64 = (int64_t)h.ret64;
     out->bond_tile = c->k.tile;
     out->halted_step = (int32_t)h.halted_step;
+    out->unstable_step = (int32_t)h.unstable_step;
     out->launches = c->launches;
     out->status = h.status;
     out->W_int = h.W_int;

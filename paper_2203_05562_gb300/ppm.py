@@ -43,6 +43,7 @@ class Params(C.Structure):
         ("load_rate", C.c_double), ("elastic", C.c_int32), ("load_layers", C.c_int32),
         ("halt_on_unstable", C.c_int32), ("contact", C.c_int32),
         ("contact_modulus", C.c_double), ("friction", C.c_double), ("contact_cutoff", C.c_double),
+        ("energy_tol", C.c_double),
     ]
 
 
@@ -56,7 +57,7 @@ class Counters(C.Structure):
                 ("plastic", C.c_int64), ("nonconv", C.c_int64), ("singular", C.c_int64),
                 ("rebuilds", C.c_int64), ("pairs", C.c_int64), ("launches", C.c_int64),
                 ("returns_fp64", C.c_int64), ("bond_tile", C.c_int32), ("halted_step", C.c_int32),
-                ("status", C.c_uint32), ("pad_", C.c_uint32),
+                ("status", C.c_uint32), ("unstable_step", C.c_int32),
                 ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double),
                 ("W_kin0", C.c_double)]
 

@@ -40,6 +40,7 @@ MATERIAL = dict(
     contact_modulus=4e6,    # C_s, Pa (Sec. 4.2)
     friction=0.25,          # mu_f (Sec. 4.2)
     contact_cutoff=0.8,     # delta_c / dx (Sec. 4.2)
+    energy_tol=0.0,         # tolerance of the Eq. 69 energy check; 0: 1e-2
 )
 
 #: The five workloads: (description, overrides).
