@@ -144,9 +144,10 @@ def uniaxial_compression(steps: int, tile: int, early: int = 10000):
     return out
 
 
-def runout_config(aspect: float, friction: float, suction: float) -> dict:
-    """The soil column collapse of Sec. 4.2, synthetic and in 3-D: a square
-    column 0.1 m wide (40 points at 2.5 mm) and 0.1 / aspect high resting on
+def runout_config(aspect: float, friction: float, suction: float, plane_strain: bool = True) -> dict:
+    """The soil column collapse of Sec. 4.2, synthetic: in plane strain (the
+    paper's setting; a slab 13 planes thick, periodic in y) or as a square
+    3-D column; 0.1 m wide (40 points at 2.5 mm) and 0.1 / aspect high resting on
     the rigid substrate (C_s = 4 MPa, delta_c = 0.8 dx, friction mu_f),
     released from the K0 geostatic state at a constant suction, with the
     preconsolidation pressure 1.25 x the initial mean effective stress at the
@@ -161,32 +162,34 @@ def runout_config(aspect: float, friction: float, suction: float) -> dict:
     p_base = (1 + 2 * k0) / 3 * m["rho"] * -m["gravity"][2] * (nz - 1) * dx
     n_vg = m["vg_n"]
     s_r = (1 + (m["vg_alpha"] * suction) ** n_vg) ** -(1 - 1 / n_vg)
-    return pi.small_config(nx, nx, nz, dx=dx, suction=suction, model=2, contact=1,
-                           friction=friction, pc0=1.25 * (p_base + s_r * suction),
-                           rebuild_every=50, energy_tol=5e-2)
+    return pi.small_config(nx, 13 if plane_strain else nx, nz, dx=dx, suction=suction, model=2,
+                           contact=1, friction=friction, pc0=1.25 * (p_base + s_r * suction),
+                           rebuild_every=50, energy_tol=5e-2, plane_strain=int(plane_strain))
 
 
 def runout_shape(sim, cfg) -> dict:
     """Run-out (largest horizontal distance from the column's axis over the
-    initial half-width) and deposit height (over the initial height)."""
+    initial half-width; along x in plane strain) and deposit height (over
+    the initial height)."""
     nx, ny, nz, dx = cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"]
     i = np.arange(nx * ny * nz)
     x = np.stack([i % nx, i // nx % ny, i // (nx * ny)]) * dx + sim.read("u").astype(np.float64)
     c = (cfg["nx"] - 1) * cfg["dx"] / 2
-    return {"runout": float(np.maximum(np.abs(x[0] - c), np.abs(x[1] - c)).max() / c),
+    reach = np.abs(x[0] - c) if cfg["plane_strain"] else np.maximum(np.abs(x[0] - c), np.abs(x[1] - c))
+    return {"runout": float(reach.max() / c),
             "height": float(x[2].max() / ((cfg["nz"] - 1) * cfg["dx"]))}
 
 
 def collapse_runout(tile: int) -> list:
-    """Sec. 4.2.1-4.2.3 on the substrate: the dry column at aspect 2 on a
-    smooth, an intermediate and a rough substrate (mu_f = 0, 0.25, 0.5), at
-    suctions 25 and 50 kPa (mu_f = 0.25), and at aspect 1, each to the end
-    time of the paper's snapshots for that aspect."""
+    """Sec. 4.2.1-4.2.3 in plane strain on the substrate: the dry column at
+    aspect 2 on a smooth, an intermediate and a rough substrate (mu_f = 0,
+    0.25, 0.5), at suctions 25 and 50 kPa (mu_f = 0.25), and at aspects 1
+    and 0.5, each to the end time of the paper's snapshots for that aspect."""
     import torch
     from paper_2203_05562_gb300 import Simulation
     runs = [(2.0, 0.0, 0.0), (2.0, 0.25, 0.0), (2.0, 0.5, 0.0),
-            (2.0, 0.25, 25e3), (2.0, 0.25, 50e3), (1.0, 0.25, 0.0)]
-    t_end = {2.0: 0.25, 1.0: 0.4}
+            (2.0, 0.25, 25e3), (2.0, 0.25, 50e3), (1.0, 0.25, 0.0), (0.5, 0.25, 0.0)]
+    t_end = {2.0: 0.25, 1.0: 0.4, 0.5: 0.5}
     out = []
     for aspect, friction, suction in runs:
         cfg = runout_config(aspect, friction, suction)
@@ -565,7 +568,7 @@ def main():
     # ---- run-out of the column collapse on the substrate (Sec. 4.2, opt-in) ----
     runout = None
     if args.runout:
-        runout = {"workload": "collapse on the substrate, 40 x 40 x 0.1/(aspect dx), dx 2.5 mm",
+        runout = {"workload": "plane-strain collapse on the substrate, 40 x 13 (periodic) x 0.1/(aspect dx), dx 2.5 mm",
                   "runs": collapse_runout(tile)}
 
     # ---- standard correspondence (model 1) on the same column ----

@@ -139,6 +139,14 @@ typedef struct {
     double contact_cutoff;       /* delta_c / dx, contact = 1                  */
     double energy_tol;           /* the tolerance of the Eq. 69 check (> 0), or
                                     0 for 1e-2; the paper gives its order only */
+    int32_t plane_strain;        /* 1: plane strain in the x-z plane, the setting
+                                    of the paper's experiments (Sec. 4): y is
+                                    periodic with period ny * dx, which must
+                                    exceed 4 delta, bond vectors take the
+                                    nearest periodic image, and v_y is held at
+                                    zero, so a y-invariant start stays
+                                    y-invariant.  Single columns only; not
+                                    with the adjoint calls                     */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */

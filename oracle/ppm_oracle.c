@@ -142,6 +142,8 @@ static int params_ok(const ppmo_params* p) {
     if (p->model < 0 || p->model > 2) return 0;
     if (p->newton_max_iter < 1 || !(p->newton_tol > 0)) return 0;
     if (!(p->energy_tol >= 0) || !isfinite(p->energy_tol)) return 0;
+    if (p->plane_strain != 0 && p->plane_strain != 1) return 0;
+    if (p->plane_strain && !((double)p->ny > 4.0 * p->horizon_factor)) return 0;
     return 1;
 }
 
@@ -161,16 +163,36 @@ void ppmo_reference_positions(const ppmo_params* p, double* X0) {
     }
 }
 
-/* squared distance between points a and b of a 3n component-major array */
-static double dist2(const double* x, int64_t n, int64_t a, int64_t b) {
-    double d0 = x[0 * n + b] - x[0 * n + a];
-    double d1 = x[1 * n + b] - x[1 * n + a];
-    double d2 = x[2 * n + b] - x[2 * n + a];
+/* x_b - x_a, component c.  Under plane strain (reading R35) y is periodic
+ * with period L = ny dx and the image of b is chosen by the lattice offset
+ * so that |iy_b - iy_a| <= ny / 2: the image's y is x_b + s L, s = -1, 0, 1. */
+static double rel(const ppmo_params* p, int64_t n, const double* x, int64_t a, int64_t b, int c) {
+    if (c != 1 || !p || !p->plane_strain) return x[c * n + b] - x[c * n + a];
+    const int64_t dl = (b / p->nx) % p->ny - (a / p->nx) % p->ny;
+    const double L = (double)p->ny * p->dx;
+    double xb = x[n + b];
+    if (2 * dl > p->ny) xb = xb + -L;
+    else if (2 * dl < -p->ny) xb = xb + L;
+    return xb - x[n + a];
+}
+
+/* squared distance from a to b with the images of rel() */
+static double dist2p(const ppmo_params* p, const double* x, int64_t n, int64_t a, int64_t b) {
+    const double d0 = rel(p, n, x, a, b, 0), d1 = rel(p, n, x, a, b, 1), d2 = rel(p, n, x, a, b, 2);
     return (d0 * d0 + d1 * d1) + d2 * d2;
 }
 
+static int64_t family_impl(const ppmo_params* p, int64_t n, const double* x, const int32_t* group,
+                           double delta, int64_t cap, int32_t* row_ptr, int32_t* col, int32_t* rev);
+
 int64_t ppmo_family(int64_t n, const double* x, const int32_t* group, double delta,
                     int64_t cap, int32_t* row_ptr, int32_t* col, int32_t* rev) {
+    return family_impl(NULL, n, x, group, delta, cap, row_ptr, col, rev);
+}
+
+/* Eq. 1 by brute force: H_i = {j != i : |x_j - x_i| <= delta}, ascending j */
+static int64_t family_impl(const ppmo_params* p, int64_t n, const double* x, const int32_t* group,
+                           double delta, int64_t cap, int32_t* row_ptr, int32_t* col, int32_t* rev) {
     const double d2max = delta * delta;
     int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
     if (!cnt) return -2;
@@ -180,7 +202,7 @@ int64_t ppmo_family(int64_t n, const double* x, const int32_t* group, double del
         for (int64_t j = 0; j < n; j++) {
             if (j == i) continue;
             if (group && group[j] != group[i]) continue;
-            if (dist2(x, n, i, j) <= d2max) c++;
+            if (dist2p(p, x, n, i, j) <= d2max) c++;
         }
         cnt[i + 1] = c;
     }
@@ -195,7 +217,7 @@ int64_t ppmo_family(int64_t n, const double* x, const int32_t* group, double del
         for (int64_t j = 0; j < n; j++) {
             if (j == i) continue;
             if (group && group[j] != group[i]) continue;
-            if (dist2(x, n, i, j) <= d2max) col[pos++] = (int32_t)j;
+            if (dist2p(p, x, n, i, j) <= d2max) col[pos++] = (int32_t)j;
         }
     }
     /* rev[b]: position of bond (j, i) in row j, found by bisection */
@@ -444,11 +466,11 @@ static void subhorizon(const ppmo_params* p, int64_t n, const double* x, const d
     memset(s, 0, sizeof(*s));
     for (int64_t b2 = row_ptr[i]; b2 < row_ptr[i + 1]; b2++) {
         int64_t k = col[b2];
-            int member = (p->model == 1) || (dist2(x, n, j, k) <= d2max);
+            int member = (p->model == 1) || (dist2p(p, x, n, j, k) <= d2max);
         if (!member) continue;
         double zeta[3], ydot[3];
         for (int c = 0; c < 3; c++) {
-            zeta[c] = x[c * n + k] - x[c * n + i];
+            zeta[c] = rel(p, n, x, i, k, c);
             ydot[c] = vel[c * n + k] - vel[c * n + i];
         }
         for (int r = 0; r < 3; r++)
@@ -501,7 +523,7 @@ int ppmo_full_horizon_L(const ppmo_params* p, int64_t n, const double* x, const 
             int64_t k = col[b];
             double zeta[3], ydot[3];
             for (int c = 0; c < 3; c++) {
-                zeta[c] = x[c * n + k] - x[c * n + i];
+                zeta[c] = rel(p, n, x, i, k, c);
                 ydot[c] = vel[c * n + k] - vel[c * n + i];
             }
             for (int r = 0; r < 3; r++)
@@ -586,9 +608,9 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
                  * over H_s); the row is normalised by sum(varpi) below */
                 for (int64_t b2 = row_ptr[i]; b2 < row_ptr[i + 1]; b2++) {
                     int64_t k = col[b2];
-                    if (!(dist2(x, n, j, k) <= d2max)) continue;
+                    if (!(dist2p(p, x, n, j, k) <= d2max)) continue;
                     double zk[3];
-                    for (int c = 0; c < 3; c++) zk[c] = x[c * n + k] - x[c * n + i];
+                    for (int c = 0; c < 3; c++) zk[c] = rel(p, n, x, i, k, c);
                     for (int r = 0; r < 3; r++) {
                         double t = 0.0;
                         for (int c = 0; c < 3; c++) t += SK[r][c] * zk[c];
@@ -598,7 +620,7 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
             } else {
                 /* Eq. 31-32, 51: the force state on the bond itself */
                 double zj[3];
-                for (int c = 0; c < 3; c++) zj[c] = x[c * n + j] - x[c * n + i];
+                for (int c = 0; c < 3; c++) zj[c] = rel(p, n, x, i, j, c);
                 for (int r = 0; r < 3; r++) {
                     double t = 0.0;
                     for (int c = 0; c < 3; c++) t += SK[r][c] * zj[c];
@@ -670,6 +692,7 @@ static int is_base(const ppmo_params* p, int64_t id) {
 static int constrained(const ppmo_params* p, int64_t id, int c, double* vbar) {
     *vbar = 0.0;
     if (p->lock_lateral && c < 2) return 1;
+    if (p->plane_strain && c == 1) return 1;
     if (p->bc == 0) return !p->contact && is_base(p, id);
     if (c != 0) return 0;
     const int64_t ix = id % p->nx;
@@ -726,7 +749,7 @@ static int rebuild(const ppmo_params* p, ppmo_state* s, const double* x) {
     int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->cap > 0 ? s->cap : 1));
     int32_t* rv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->cap > 0 ? s->cap : 1));
     if (!rp || !cl || !rv) { free(rp); free(cl); free(rv); return -2; }
-    int64_t B = ppmo_family(s->n, x, NULL, p->horizon_factor * p->dx, s->cap, rp, cl, rv);
+    int64_t B = family_impl(p, s->n, x, NULL, p->horizon_factor * p->dx, s->cap, rp, cl, rv);
     if (B < 0) {                      /* keep the previous family */
         s->n_overflow++;
         free(rp); free(cl); free(rv);
@@ -1084,7 +1107,7 @@ static void reverse_step(const ppmo_params* p, int64_t n, const double* u, const
             sym_to_mat(t.sig_out, Sh);
             for (int c = 0; c < 3; c++) Sh[c][c] += Srs;
             for (int c = 0; c < 3; c++) {
-                zj[c] = x[c * n + j] - x[c * n + i];
+                zj[c] = rel(p, n, x, i, j, c);
                 Tb[c] = V * V * (fb[c * n + i] - fb[c * n + j]);   /* Eq. 49 reversed */
             }
             for (int r = 0; r < 3; r++) {
@@ -1128,10 +1151,10 @@ static void reverse_step(const ppmo_params* p, int64_t n, const double* u, const
             /* K = V sum zeta zeta^T, A = V sum Ydot zeta^T over the sub-horizon */
             for (int64_t b2 = r0; b2 < r1; b2++) {
                 const int64_t k = F->col[b2];
-                if (!((p->model == 1) || (dist2(x, n, j, k) <= d2max))) continue;
+                if (!((p->model == 1) || (dist2p(p, x, n, j, k) <= d2max))) continue;
                 double zk[3], yk[3], zb[3], yb[3];
                 for (int c = 0; c < 3; c++) {
-                    zk[c] = x[c * n + k] - x[c * n + i];
+                    zk[c] = rel(p, n, x, i, k, c);
                     yk[c] = vh[c * n + k] - vh[c * n + i];
                 }
                 for (int r = 0; r < 3; r++) {
@@ -1201,7 +1224,7 @@ static void reverse_initial(const ppmo_params* p, int64_t n, const double* sig0,
             const double varpi = (double)ss.count / (double)nb;
             double zj[3], g[3], Tb[3];
             for (int c = 0; c < 3; c++) {
-                zj[c] = x[c * n + j] - x[c * n + i];
+                zj[c] = rel(p, n, x, i, j, c);
                 Tb[c] = V * V * (fb[c * n + i] - fb[c * n + j]);
             }
             for (int r = 0; r < 3; r++) {
@@ -1234,7 +1257,8 @@ static int is_top(const ppmo_params* p, int64_t id) {
 
 int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps, int64_t cap,
                             double* J, double grad[4]) {
-    if (!params_ok(p) || p->model == 2 || n_steps < 0 || p->contact || p->halt_on_unstable)
+    if (!params_ok(p) || p->model == 2 || n_steps < 0 || p->contact || p->halt_on_unstable ||
+        p->plane_strain)
         return -1;
     const int64_t n = (int64_t)p->nx * p->ny * p->nz;
     ppmo_state s;
@@ -1344,7 +1368,8 @@ double ppmo_critical_time_step(const ppmo_params* p, const ppmo_state* s) {
         double sum = 0.0;
         for (int64_t b = s->row_ptr[i]; b < s->row_ptr[i + 1]; b++) {
             const int64_t j = s->col[b];
-            const double d0 = x[j] - x[i], d1 = x[n + j] - x[n + i], d2 = x[2 * n + j] - x[2 * n + i];
+            const double d0 = rel(p, n, x, i, j, 0), d1 = rel(p, n, x, i, j, 1),
+                         d2 = rel(p, n, x, i, j, 2);
             sum += 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         }
         if (sum > 0.0) {

@@ -65,6 +65,9 @@ typedef struct {
     double friction;             /* mu_f                                       */
     double contact_cutoff;       /* delta_c / dx                               */
     double energy_tol;           /* tolerance of the Eq. 69 check; 0 = 1e-2    */
+    int32_t plane_strain;        /* 1: plane strain in x-z (reading R35): y is
+                                    periodic with period ny dx (ny dx > 4 delta)
+                                    and v_y is held at zero                   */
 } ppmo_params;
 
 typedef struct {

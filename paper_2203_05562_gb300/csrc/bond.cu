@@ -115,7 +115,9 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         R4<Real> z, y;
         if constexpr (F64) {
             const double px = __dadd_rn(__dmul_rn((double)lat_x(lj), k.dx), (double)s.u[j]);
-            const double py = __dadd_rn(__dmul_rn((double)lat_y(lj), k.dx), (double)s.u[n + j]);
+            double py = __dadd_rn(__dmul_rn((double)lat_y(lj), k.dx), (double)s.u[n + j]);
+            const int sh = image_shift(k, lj, li);     // plane strain: nearest image
+            if (sh) py = __dadd_rn(py, (double)sh * k.pbc_L);
             const double pz = __dadd_rn(__dmul_rn((double)lat_z(lj), k.dx), (double)s.u[2 * n + j]);
             s_p[0][t] = px; s_p[F64 ? 1 : 0][t] = py; s_p[F64 ? 2 : 0][t] = pz;
             z.x = (Real)((px - pxi) * k.inv_dx);
@@ -123,7 +125,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             z.z = (Real)((pz - pzi) * k.inv_dx);
         } else {
             z.x = (Real)(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
-            z.y = (Real)(lat_y(lj) - iy) + (s.u[n + j] - uyi) * inv_dx;
+            z.y = (Real)(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) + (s.u[n + j] - uyi) * inv_dx;
             z.z = (Real)(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
         }
         z.w = z.x * z.x + z.y * z.y + z.z * z.z;

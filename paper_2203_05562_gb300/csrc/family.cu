@@ -38,10 +38,17 @@ struct Geometry<double> {
     static __device__ __forceinline__ bool within(const DevState<double>& s, const StepConst& k,
                                                   int i, int li, int j, int lj) {
         double d0 = __dsub_rn(pos(s, k, j, 0, lj), pos(s, k, i, 0, li));
-        double d1 = __dsub_rn(pos(s, k, j, 1, lj), pos(s, k, i, 1, li));
+        double d1 = __dsub_rn(image_y(s, k, j, lj, li), pos(s, k, i, 1, li));
         double d2 = __dsub_rn(pos(s, k, j, 2, lj), pos(s, k, i, 2, li));
         double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
         return r2 <= k.delta2;
+    }
+    // y of the image of j nearest to i (plane strain), y_j + s L
+    static __device__ __forceinline__ double image_y(const DevState<double>& s, const StepConst& k,
+                                                     int j, int lj, int li) {
+        const double y = pos(s, k, j, 1, lj);
+        const int sh = image_shift(k, lj, li);
+        return sh ? __dadd_rn(y, (double)sh * k.pbc_L) : y;
     }
 };
 
@@ -60,9 +67,14 @@ struct Geometry<float> {
         const float inv = (float)k.inv_dx;
         const size_t n = (size_t)k.npoints;
         float z0 = (float)(lat_x(lj) - lat_x(li)) + (s.u[j] - s.u[i]) * inv;
-        float z1 = (float)(lat_y(lj) - lat_y(li)) + (s.u[n + j] - s.u[n + i]) * inv;
+        float z1 = (float)(lat_y(lj) - lat_y(li) + image_shift(k, lj, li) * k.pbc_ny) +
+                   (s.u[n + j] - s.u[n + i]) * inv;
         float z2 = (float)(lat_z(lj) - lat_z(li)) + (s.u[2 * n + j] - s.u[2 * n + i]) * inv;
         return z0 * z0 + z1 * z1 + z2 * z2 <= k.hf2f;
+    }
+    static __device__ __forceinline__ double image_y(const DevState<float>& s, const StepConst& k,
+                                                     int j, int lj, int li) {
+        return pos(s, k, j, 1, lj) + (double)image_shift(k, lj, li) * k.pbc_L;
     }
 };
 
@@ -112,7 +124,7 @@ __global__ void k_bbox(DevState<Real> s, StepConst k) {
 // cell edge >= delta, grown while the grid would exceed the cell capacity;
 // a single cell per column if nothing fits (non-finite positions)
 __global__ void k_grid_setup(const long long* bbox, CellGrid* g, double delta, int ncols,
-                             int ncell_cap) {
+                             int ncell_cap, int periodic_y) {
     double lo[3], ext[3];
     for (int c = 0; c < 3; c++) {
         double a = unordered(bbox[c]), b = unordered(bbox[3 + c]);
@@ -126,7 +138,9 @@ __global__ void k_grid_setup(const long long* bbox, CellGrid* g, double delta, i
     for (int it = 0; it < 400 && !fits; it++) {
         double tot = (double)ncols;
         for (int c = 0; c < 3; c++) {
-            d[c] = (int)fmin(ext[c] / h, 1e9) + 3;
+            // periodic y (plane strain): one cell spans the period and the
+            // images are taken per pair
+            d[c] = (c == 1 && periodic_y) ? 1 : (int)fmin(ext[c] / h, 1e9) + 3;
             tot *= (double)d[c];
         }
         fits = tot <= (double)ncell_cap;
@@ -381,7 +395,7 @@ k_critical_dt(DevState<Real> s, StepConst k, double VC, long long* out) {
         const int j = s.col[b];
         const int lj = s.lat[j];
         const double d0 = Geometry<Real>::pos(s, k, j, 0, lj) - xi;
-        const double d1 = Geometry<Real>::pos(s, k, j, 1, lj) - yi;
+        const double d1 = Geometry<Real>::image_y(s, k, j, lj, li) - yi;
         const double d2 = Geometry<Real>::pos(s, k, j, 2, lj) - zi;
         acc += 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     }
@@ -421,7 +435,7 @@ cudaError_t launch_family_build(const DevState<Real>& s, const StepConst& k, cud
     const double delta = sqrt(k.delta2);
     k_bbox_reset<<<1, 32, 0, st>>>(s.bbox, &s.ctr->rebuilds);
     k_bbox<Real><<<min(pblocks, 4096), tpb, 0, st>>>(s, k);
-    k_grid_setup<<<1, 1, 0, st>>>(s.bbox, s.grid, delta, k.ncols, s.ncell_cap);
+    k_grid_setup<<<1, 1, 0, st>>>(s.bbox, s.grid, delta, k.ncols, s.ncell_cap, k.pbc_ny != 0);
     cudaMemsetAsync(s.cellcnt, 0, sizeof(int32_t) * (size_t)(s.ncell_cap + 1), st);
     cudaMemsetAsync(s.cellfill, 0, sizeof(int32_t) * (size_t)s.ncell_cap, st);
     k_cell_count<Real><<<pblocks, tpb, 0, st>>>(s, k);

@@ -62,6 +62,8 @@ struct StepConst {
     int load_layers;             // bc = 1: planes held / driven at each x end
     int halt;                    // 1: the Eq. 69 check stops the run (kernels skip)
     double energy_tol;           // the Eq. 69 tolerance (resolved: > 0)
+    int pbc_ny;                  // plane strain: the y period in lattice planes, else 0
+    double pbc_L;                // plane strain: the y period ny * dx (m)
     int contact;                 // 1: rigid flat substrate at z = -delta_c (no fixed base)
     double contact_modulus, friction, contact_dc;   // C_s (Pa), mu_f, delta_c (m)
     float contact_kf, frictionf, contact_dcf;        // C_s dx^2, mu_f, delta_c in FP32
@@ -71,6 +73,14 @@ struct StepConst {
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;
     float gf[3];
 };
+
+// plane strain: the periodic image of point j (lattice index lj) nearest to
+// point i (li) in y, as a multiple of the period: -1, 0 or 1
+__host__ __device__ __forceinline__ int image_shift(const StepConst& k, int lj, int li) {
+    if (!k.pbc_ny) return 0;
+    const int dl = lat_y(lj) - lat_y(li);
+    return 2 * dl > k.pbc_ny ? -1 : (2 * dl < -k.pbc_ny ? 1 : 0);
+}
 
 // device pointers of one context (Real = double for FP64, float for mixed)
 template <typename Real>
@@ -112,7 +122,8 @@ struct DevState {
 // Boundary conditions (the fixed base; the loading of Sec. 4.1): true when
 // velocity component c of point i is prescribed, with the value in vbar.
 // bc = 0: the base layer (unless the substrate carries the column) and, with
-// lock_lateral, the x and y components are held at zero.  bc = 1: the load_layers planes at the x = 0 end of the
+// lock_lateral, the x and y components are held at zero; under plane strain
+// the y component is held at zero.  bc = 1: the load_layers planes at the x = 0 end of the
 // point's column are held in x and those at the other end move at
 // v_x = -load_rate.
 template <typename Real>
@@ -120,6 +131,7 @@ __device__ __forceinline__ bool prescribed(const DevState<Real>& s, const StepCo
                                            int c, Real& vbar) {
     vbar = (Real)0;
     if (k.lock_lateral && c < 2) return true;
+    if (k.pbc_ny && c == 1) return true;          // plane strain
     const int li = s.lat[i];
     if (k.bc == 0) return !k.contact && lat_z(li) == 0;
     if (c != 0) return false;

@@ -99,6 +99,7 @@ int check_params(const ppm_params* p) {
     if (p->halt_on_unstable != 0 && p->halt_on_unstable != 1) return PPM_EINVAL;
     if (p->contact != 0 && p->contact != 1) return PPM_EINVAL;
     if (!(p->energy_tol >= 0) || !std::isfinite(p->energy_tol)) return PPM_EINVAL;
+    if (p->plane_strain != 0 && p->plane_strain != 1) return PPM_EINVAL;
     if (p->contact && (!(p->contact_modulus >= 0) || !(p->friction >= 0) || !(p->contact_cutoff > 0) ||
                        !std::isfinite(p->contact_modulus) || !std::isfinite(p->friction)))
         return PPM_EINVAL;
@@ -111,6 +112,7 @@ int collect_columns(const ppm_params* p, int n_columns, const ppm_column* cols,
     int64_t off = 0;
     const int nc = n_columns > 0 ? n_columns : 1;
     if (n_columns > 0 && !cols) return PPM_EINVAL;
+    if (p->plane_strain && n_columns > 1) return PPM_EINVAL;      // one periodic slab
     for (int c = 0; c < nc; c++) {
         int nx = n_columns > 0 ? cols[c].nx : p->nx;
         int ny = n_columns > 0 ? cols[c].ny : p->ny;
@@ -120,6 +122,9 @@ int collect_columns(const ppm_params* p, int n_columns, const ppm_column* cols,
         if (nx < 1 || ny < 1 || nz < 1 || nx > kLatMask + 1 || ny > kLatMask + 1 ||
             nz > kLatMask + 1 || s < 0 || !(M > 0))
             return PPM_EINVAL;
+        // plane strain: the y period must exceed 4 delta, so that the nearest
+        // images of two members of one family are each other's nearest
+        if (p->plane_strain && !((double)ny > 4.0 * p->horizon_factor)) return PPM_EINVAL;
         ColumnConst cc;
         cc.M = M;
         cc.Srs = saturation(s, p->vg_alpha, p->vg_n) * s;
@@ -751,6 +756,8 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.elastic = p->elastic;
     k.halt = p->halt_on_unstable;
     k.energy_tol = p->energy_tol > 0 ? p->energy_tol : 1e-2;
+    k.pbc_ny = p->plane_strain ? c->cols[0].ny : 0;
+    k.pbc_L = (double)k.pbc_ny * p->dx;
     k.contact = p->contact;
     k.contact_modulus = p->contact_modulus;
     k.friction = p->friction;
@@ -954,7 +961,8 @@ int ppm_adjoint_workspace_size(const ppm_ctx* c, int n_steps, int ckpt_every, si
 
 int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, size_t bytes) {
     if (!c || n_steps < 0 || ckpt_every < 1 || !d_ws || ((uintptr_t)d_ws & 255u)) return PPM_EINVAL;
-    if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable || c->p.contact)
+    if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable || c->p.contact ||
+        c->p.plane_strain)
         return PPM_ESTATE;
     if (bytes < adj_layout(c, n_steps, ckpt_every).total) return PPM_ENOSPACE;
     Range r("ppm_adjoint_forward");

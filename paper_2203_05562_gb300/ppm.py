@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("load_rate", C.c_double), ("elastic", C.c_int32), ("load_layers", C.c_int32),
         ("halt_on_unstable", C.c_int32), ("contact", C.c_int32),
         ("contact_modulus", C.c_double), ("friction", C.c_double), ("contact_cutoff", C.c_double),
-        ("energy_tol", C.c_double),
+        ("energy_tol", C.c_double), ("plane_strain", C.c_int32),
     ]
 
 

@@ -41,6 +41,7 @@ MATERIAL = dict(
     friction=0.25,          # mu_f (Sec. 4.2)
     contact_cutoff=0.8,     # delta_c / dx (Sec. 4.2)
     energy_tol=0.0,         # tolerance of the Eq. 69 energy check; 0: 1e-2
+    plane_strain=0,         # 1: plane strain in x-z, y periodic (ny dx > 4 delta), v_y = 0
 )
 
 #: The five workloads: (description, overrides).
