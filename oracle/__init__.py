@@ -99,6 +99,7 @@ def lib():
             L.ppmo_init.argtypes = [pp, dp, C.POINTER(State)]
             L.ppmo_step.argtypes = [pp, C.POINTER(State), C.c_int]
             L.ppmo_init_with_stress.argtypes = [pp, dp, dp, C.POINTER(State)]
+            L.ppmo_init_state.argtypes = [pp, dp, dp, dp, C.POINTER(State)]
             L.ppmo_initial_stress.restype = None
             L.ppmo_initial_stress.argtypes = [pp, dp]
             L.ppmo_objective_gradient.argtypes = [pp, dp, C.c_int, C.c_int64, dp, dp]
@@ -286,7 +287,7 @@ class Run:
     views in the oracle's component-major layout."""
 
     def __init__(self, cfg: dict, v0: np.ndarray | None = None, cap_per_point: int = 256,
-                 sig0: np.ndarray | None = None):
+                 sig0: np.ndarray | None = None, u0: np.ndarray | None = None):
         self.cfg = dict(cfg)
         self.p = make_params(self.cfg)
         n = self.p.nx * self.p.ny * self.p.nz
@@ -312,8 +313,11 @@ class Run:
         self._v0 = v0a
         s0 = None if sig0 is None else np.ascontiguousarray(sig0, np.float64).reshape(6 * n)
         self._sig0 = s0
-        rc = lib().ppmo_init_with_stress(C.byref(self.p), _d(v0a) if v0a is not None else None,
-                                         _d(s0) if s0 is not None else None, C.byref(s))
+        u0a = None if u0 is None else np.ascontiguousarray(u0, np.float64).reshape(3 * n)
+        self._u0 = u0a
+        rc = lib().ppmo_init_state(C.byref(self.p), _d(u0a) if u0a is not None else None,
+                                   _d(v0a) if v0a is not None else None,
+                                   _d(s0) if s0 is not None else None, C.byref(s))
         if rc != 0:
             raise RuntimeError(f"ppmo_init failed ({rc})")
 

@@ -651,6 +651,23 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
             fint[c * n + i] = V * V * s;
         }
     }
+    /* Eq. 91 between material points of the soil (reading R36): a pair
+     * closer than delta_c (always family members, delta_c < delta) pushes
+     * each of its points from the other by C_s dx^2 (delta_c - r) / delta_c
+     * along the line joining them; coincident points get nothing */
+    if (p->contact) {
+        const double dc = p->contact_cutoff * p->dx;
+        const double kc = p->contact_modulus * p->dx * p->dx / dc;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
+                double d[3];
+                for (int c = 0; c < 3; c++) d[c] = rel(p, n, x, i, col[b], c);
+                const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (r > 0.0 && r < dc)
+                    for (int c = 0; c < 3; c++) fint[c * n + i] -= kc * (dc - r) * d[c] / r;
+            }
+    }
     if (cnt_out) {
         cnt_out->plastic = plastic;
         cnt_out->nonconv = nonconv;
@@ -788,13 +805,18 @@ void ppmo_initial_stress(const ppmo_params* p, double* sig) {
 
 int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* sig0,
                           ppmo_state* s) {
+    return ppmo_init_state(p, NULL, v0, sig0, s);
+}
+
+int ppmo_init_state(const ppmo_params* p, const double* u0, const double* v0, const double* sig0,
+                    ppmo_state* s) {
     if (!params_ok(p)) return -1;
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
     if (s->n != n) return -1;
     const double V = p->dx * p->dx * p->dx, m = p->rho * V;
     for (int64_t i = 0; i < n; i++) {
         for (int c = 0; c < 3; c++) {
-            s->u[c * n + i] = 0.0;
+            s->u[c * n + i] = u0 ? u0[c * n + i] : 0.0;
             double vv = v0 ? v0[c * n + i] : 0.0, vbar;
             if (constrained(p, i, c, &vbar)) vv = vbar;
             s->v[c * n + i] = vv;

@@ -139,6 +139,9 @@ int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s);
  * geostatic state of ppmo_initial_stress). */
 int ppmo_init_with_stress(const ppmo_params* p, const double* v0, const double* sig0,
                           ppmo_state* s);
+/* The same from an initial displacement u0 (3n; NULL: zero). */
+int ppmo_init_state(const ppmo_params* p, const double* u0, const double* v0, const double* sig0,
+                    ppmo_state* s);
 /* Initial effective stress of the column (6n), O(n). */
 void ppmo_initial_stress(const ppmo_params* p, double* sig);
 /* Alg. 2, lines 5-13: n_steps explicit central-difference steps. */

@@ -228,23 +228,27 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             n_pairs += cnt;
             if (!active) {
                 n_singular++;
-                s.T[r0 + t] = (Real)0;
-                s.T[k.cap + r0 + t] = (Real)0;
-                s.T[2 * k.cap + r0 + t] = (Real)0;
+                Real C0 = (Real)0, C1 = (Real)0, C2 = (Real)0;
+                pair_contact(k, s_z[t], C0, C1, C2);
+                s.T[r0 + t] = C0;
+                s.T[k.cap + r0 + t] = C1;
+                s.T[2 * k.cap + r0 + t] = C2;
                 if (rb >= 0) {
-                    s.Trev[rb] = (Real)0;
-                    s.Trev[k.cap + rb] = (Real)0;
-                    s.Trev[2 * k.cap + rb] = (Real)0;
+                    s.Trev[rb] = C0;
+                    s.Trev[k.cap + rb] = C1;
+                    s.Trev[2 * k.cap + rb] = C2;
                 }
+                red[9] += C0; red[10] += C1; red[11] += C2;
                 continue;
             }
             n_plastic += bs.plastic;
             n_nonconv += bs.nonconv;
             n_ret64 += bs.ret64;
             const R4<Real> zj = s_z[t];
-            const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
-            const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
-            const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+            Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+            Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            pair_contact(k, zj, T0, T1, T2);
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;
@@ -325,14 +329,17 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         if (!active) {
             n_singular++;
             if constexpr (MODEL != 2) {
-                s.T[r0 + t] = (Real)0;
-                s.T[k.cap + r0 + t] = (Real)0;
-                s.T[2 * k.cap + r0 + t] = (Real)0;
+                Real C0 = (Real)0, C1 = (Real)0, C2 = (Real)0;
+                pair_contact(k, zj, C0, C1, C2);
+                s.T[r0 + t] = C0;
+                s.T[k.cap + r0 + t] = C1;
+                s.T[2 * k.cap + r0 + t] = C2;
                 if (rb >= 0) {
-                    s.Trev[rb] = (Real)0;
-                    s.Trev[k.cap + rb] = (Real)0;
-                    s.Trev[2 * k.cap + rb] = (Real)0;
+                    s.Trev[rb] = C0;
+                    s.Trev[k.cap + rb] = C1;
+                    s.Trev[2 * k.cap + rb] = C2;
                 }
+                red[9] += C0; red[10] += C1; red[11] += C2;
             } else {
 #pragma unroll
                 for (int e = 0; e < 9; e++) s_M[t][e] = (Real)0;
@@ -414,9 +421,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                                          S[r * 3 + 2] * Ki[2 * 3 + c]);
         if constexpr (MODEL != 2) {
             // force state on the bond itself (Eq. 31-32, 51)
-            const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
-            const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
-            const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+            Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+            Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            pair_contact(k, zj, T0, T1, T2);
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;
@@ -483,9 +491,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 #pragma unroll
                 for (int e = 0; e < 9; e++) N[e] = Nf[e];
             }
-            const Real T0 = (N[0] * zt.x + N[1] * zt.y + N[2] * zt.z) * inv_w;
-            const Real T1 = (N[3] * zt.x + N[4] * zt.y + N[5] * zt.z) * inv_w;
-            const Real T2 = (N[6] * zt.x + N[7] * zt.y + N[8] * zt.z) * inv_w;
+            Real T0 = (N[0] * zt.x + N[1] * zt.y + N[2] * zt.z) * inv_w;
+            Real T1 = (N[3] * zt.x + N[4] * zt.y + N[5] * zt.z) * inv_w;
+            Real T2 = (N[6] * zt.x + N[7] * zt.y + N[8] * zt.z) * inv_w;
+            pair_contact(k, zt, T0, T1, T2);
             s.T[r0 + t] = T0;
             s.T[k.cap + r0 + t] = T1;
             s.T[2 * k.cap + r0 + t] = T2;

@@ -67,12 +67,33 @@ struct StepConst {
     int contact;                 // 1: rigid flat substrate at z = -delta_c (no fixed base)
     double contact_modulus, friction, contact_dc;   // C_s (Pa), mu_f, delta_c (m)
     float contact_kf, frictionf, contact_dcf;        // C_s dx^2, mu_f, delta_c in FP32
+    double pair_dc, pair_kappa;  // between points: delta_c / dx and C_s / (2 delta_c / dx)
+    float pair_dcf, pair_kappaf; // the same in FP32
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;
     float gf[3];
 };
+
+// Short-range repulsion between two material points closer than delta_c
+// (Eq. 91 between points of the soil; reading R36), added to the force
+// state of bond (i, j) in lattice units, z = (zeta / dx, |zeta / dx|^2): the
+// opposite term sits in bond (j, i), so each point of the pair is pushed
+// from the other by C_s dx^2 (delta_c - r) / delta_c.  Coincident points
+// (no direction) get nothing.
+template <typename Real, typename V4>
+__device__ __forceinline__ void pair_contact(const StepConst& k, const V4& z, Real& T0, Real& T1, Real& T2) {
+    constexpr bool F64 = sizeof(Real) == 8;
+    const Real dc = F64 ? (Real)k.pair_dc : (Real)k.pair_dcf;
+    if (k.contact && z.w < dc * dc && z.w > (Real)0) {
+        const Real kap = F64 ? (Real)k.pair_kappa : (Real)k.pair_kappaf;
+        const Real a = kap * (dc / sqrt(z.w) - (Real)1);
+        T0 -= a * z.x;
+        T1 -= a * z.y;
+        T2 -= a * z.z;
+    }
+}
 
 // plane strain: the periodic image of point j (lattice index lj) nearest to
 // point i (li) in y, as a multiple of the period: -1, 0 or 1

@@ -757,6 +757,10 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.halt = p->halt_on_unstable;
     k.energy_tol = p->energy_tol > 0 ? p->energy_tol : 1e-2;
     k.pbc_ny = p->plane_strain ? c->cols[0].ny : 0;
+    k.pair_dc = p->contact_cutoff;
+    k.pair_kappa = p->contact ? p->contact_modulus / (2.0 * p->contact_cutoff) : 0.0;
+    k.pair_dcf = (float)k.pair_dc;
+    k.pair_kappaf = (float)k.pair_kappa;
     k.pbc_L = (double)k.pbc_ny * p->dx;
     k.contact = p->contact;
     k.contact_modulus = p->contact_modulus;

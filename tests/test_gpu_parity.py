@@ -323,3 +323,22 @@ def test_column_on_the_substrate_matches_oracle(model):
     sim = gpu_run(cfg, 12, "mixed", v0=v0)
     err = state_errors(sim, run, norm=rel_l2)
     assert err["u"] <= MIXED_TOL, err
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_points_closer_than_the_cutoff_match_oracle(model):
+    # Eq. 91 between points of the soil (reading R36): a point starting at
+    # 0.4 dx of its x-neighbour in a column on the substrate
+    cfg = pi.small_config(6, 5, 8, suction=50e3, contact=1, model=model, rebuild_every=2)
+    n = pi.num_points(cfg)
+    u0 = np.zeros((3, n))
+    u0[0, 2 + 6 * 2 + 30 * 4] = 0.6 * cfg["dx"]
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=29)
+    run = oracle.Run(cfg, v0, u0=u0)
+    run.step(12)
+    sim = gpu_run(cfg, 12, "fp64", v0=v0, u=u0)
+    err = state_errors(sim, run)
+    assert max(err.values()) <= FP64_TOL, err
+    sim = gpu_run(cfg, 12, "mixed", v0=v0, u=u0)
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["u"] <= MIXED_TOL, err

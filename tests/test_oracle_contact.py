@@ -71,3 +71,25 @@ def test_the_adjoint_rejects_contact():
     cfg = slab(0.25)
     with pytest.raises(RuntimeError):
         oracle.objective_gradient(cfg, np.zeros((3, pi.num_points(cfg))), 2)
+
+
+def test_two_points_closer_than_the_cutoff_repel_each_other():
+    # Eq. 91 between points of the soil (reading R36): in a stress-free block
+    # (no force state) with one point moved to 0.5 dx of its x-neighbour, the
+    # internal force is the pair's repulsion and nothing else
+    cfg = pi.small_config(4, 4, 4, suction=0.0, elastic=1, init_stress=1, contact=1,
+                          rebuild_every=0, model=1)
+    n = pi.num_points(cfg)
+    dx, dc = cfg["dx"], cfg["contact_cutoff"] * cfg["dx"]
+    x = oracle.reference_positions(cfg)
+    a, b = 1 + 4 + 16, 2 + 4 + 16                  # (1, 1, 1) and (2, 1, 1)
+    x[0, a] += 0.5 * dx
+    rp, col, rev = oracle.family(x, cfg["horizon_factor"] * dx)
+    sig = np.zeros((6, n))
+    f = oracle.internal_force(cfg, x, sig, rp, col, rev)
+    F = cfg["contact_modulus"] * dx * dx * (dc - 0.5 * dx) / dc
+    want = np.zeros((3, n))
+    want[0, a], want[0, b] = -F, F
+    assert np.allclose(f, want, rtol=0, atol=1e-12 * F)
+    f0 = oracle.internal_force(dict(cfg, contact=0), x, sig, rp, col, rev)
+    assert np.all(f0 == 0.0)

@@ -14,7 +14,8 @@ so the residual of Eq. 69 is, identically,
 
 Every force must be booked in W_int or W_ext for this to hold: the bond
 forces, gravity, the reaction of a prescribed component (reading R20), the
-substrate's normal and friction forces (Eq. 93).  A dropped term, a wrong
+substrate's normal and friction forces and the repulsion between soil points
+closer than delta_c (Eq. 91-93).  A dropped term, a wrong
 half or a force booked at the wrong velocity breaks it, which makes it an
 exact check on all of them at once.  It also says what the check of Eq. 69
 measures: the mass-weighted frequency content of the motion against dt, so
@@ -42,6 +43,9 @@ CASES = {
     # a slab sliding on the substrate until friction stops it
     "sliding": dict(nx=6, ny=6, nz=1, suction=0.0, elastic=1, init_stress=1, contact=1,
                     friction=0.25, rebuild_every=0, model=1),
+    # two points of the column starting closer than delta_c (reading R36)
+    "pair": dict(nx=5, ny=5, nz=6, suction=20e3, model=2, contact=1, friction=0.25,
+                 rebuild_every=2),
 }
 
 
@@ -63,7 +67,11 @@ def test_the_eq69_residual_is_dt2_over_8_times_the_change_of_sum_m_a2(case):
         v0 = np.zeros((3, n)); v0[0] = 0.1; v0[1] = 0.03
     else:
         v0 = pi.initial_velocity(cfg, std=1e-3, seed=11)
-    run = oracle.Run(cfg, v0)
+    u0 = None
+    if case == "pair":
+        u0 = np.zeros((3, n))
+        u0[0, 2 + 5 * 2 + 25 * 3] = 0.6 * cfg["dx"]    # (2, 2, 3) to 0.4 dx of (3, 2, 3)
+    run = oracle.Run(cfg, v0, u0=u0)
     m = cfg["rho"] * cfg["dx"] ** 3
     a0_sq = m * float((run.a ** 2).sum())
     steps = 400 if case == "sliding" else 60
@@ -73,6 +81,11 @@ def test_the_eq69_residual_is_dt2_over_8_times_the_change_of_sum_m_a2(case):
         resid, pred, scale = residual_and_identity(run, cfg, a0_sq)
         assert abs(resid - pred) <= 1e-10 * max(scale, abs(pred)), (run.steps_done, resid, pred)
         nonzero += abs(resid) > 1e-6 * scale
+    if case == "pair":
+        # the pair was pushed apart
+        x = oracle.reference_positions(cfg) + run.u
+        i, j = 2 + 5 * 2 + 25 * 3, 3 + 5 * 2 + 25 * 3
+        assert np.linalg.norm(x[:, j] - x[:, i]) > 0.5 * cfg["dx"]
     # the identity is not met trivially (the sliding slab's accelerations are
     # small beside its kinetic energy; there the friction work, which is as
     # large as that energy, is what the identity checks)
