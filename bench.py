@@ -83,17 +83,19 @@ def algorithmic_bytes(nbonds: int, npoints: int, mixed: bool) -> float:
     return nbonds * (8 + 9 * R) + npoints * (20 + 55 * R + (24 if mixed else 0))
 
 
-def uniaxial_config(m: int) -> dict:
-    """The uniaxial compression test of Sec. 4.1, synthetic and in 3-D:
-    12,000 points (40 x 15 x 20, spacing 5 mm), K = 25 MPa, mu = 15 MPa,
+def uniaxial_config(m: int, plane_strain: bool = False) -> dict:
+    """The uniaxial compression test of Sec. 4.1, synthetic: in 3-D,
+    12,000 points (40 x 15 x 20, spacing 5 mm), or in plane strain (the
+    paper's setting) 40 x 13 x 20 with y periodic; K = 25 MPa, mu = 15 MPa,
     skeleton density 2200 kg/m^3 with porosity 0.2, saturated at zero
     suction, the elastic skeleton, horizon m spacings (+0.015 against ties),
     u_x = 0.5 mm over 0.1 s applied by the end regions (a horizon thick) at
     the dynamic time step of 3e-6 s, no gravity."""
-    return pi.small_config(40, 15, 20, dx=0.005, horizon_factor=m + 0.015, K=25e6, mu=15e6,
-                           rho=0.8 * 2200.0 + 0.2 * 1000.0, suction=0.0, elastic=1, init_stress=1,
-                           gravity=(0.0, 0.0, 0.0), bc=1, load_rate=0.5e-3 / 0.1, dt=3e-6,
-                           rebuild_every=0)
+    return pi.small_config(40, 13 if plane_strain else 15, 20, dx=0.005, horizon_factor=m + 0.015,
+                           K=25e6, mu=15e6, rho=0.8 * 2200.0 + 0.2 * 1000.0, suction=0.0,
+                           elastic=1, init_stress=1, gravity=(0.0, 0.0, 0.0), bc=1,
+                           load_rate=0.5e-3 / 0.1, dt=3e-6, rebuild_every=0,
+                           plane_strain=int(plane_strain))
 
 
 def oscillation_scores(sxx, cfg, m: int) -> dict:
@@ -113,15 +115,16 @@ def oscillation_scores(sxx, cfg, m: int) -> dict:
             "cv": float(core.std() / abs(mean)), "mean_sxx_Pa": mean}
 
 
-def uniaxial_compression(steps: int, tile: int, early: int = 10000):
-    """The three force states on the Sec. 4.1 test at m = 2 and 3; the
-    oscillation scores after `early` steps (u_x = 0.15 mm) and at the end."""
+def uniaxial_compression(steps: int, tile: int, early: int = 10000, plane_strain: bool = False):
+    """The three force states (in plane strain the two that conserve
+    energy) on the Sec. 4.1 test at m = 2 and 3; the oscillation scores
+    after `early` steps (u_x = 0.15 mm) and at the end."""
     import torch
     from paper_2203_05562_gb300 import Simulation
     out = []
     for m in (2, 3):
-        cfg = uniaxial_config(m)
-        for model in (1, 2, 0):
+        cfg = uniaxial_config(m, plane_strain)
+        for model in ((1, 2) if plane_strain else (1, 2, 0)):
             sim = Simulation(cfg, precision="mixed", model=model, bond_tile=tile)
             r = {"m": m, "model": model, "steps": steps, "ms": 0.0}
             for tag, upto in (("early", min(early, steps)), ("end", steps)):
@@ -563,7 +566,10 @@ def main():
     uniaxial = None
     if not args.no_uniaxial:
         uniaxial = {"workload": "uniaxial_40x15x20 (Sec. 4.1, dynamic loading, elastic skeleton)",
-                    "runs": uniaxial_compression(args.uniaxial_steps, tile)}
+                    "runs": uniaxial_compression(args.uniaxial_steps, tile),
+                    "plane_strain": {"workload": "uniaxial_40x13x20, y periodic",
+                                     "runs": uniaxial_compression(args.uniaxial_steps, tile,
+                                                                  plane_strain=True)}}
 
     # ---- run-out of the column collapse on the substrate (Sec. 4.2, opt-in) ----
     runout = None
