@@ -56,6 +56,8 @@ class Params(C.Structure):
         ("halt_on_unstable", C.c_int32), ("contact", C.c_int32),
         ("contact_modulus", C.c_double), ("friction", C.c_double), ("contact_cutoff", C.c_double),
         ("energy_tol", C.c_double), ("plane_strain", C.c_int32),
+        ("coupled", C.c_int32), ("porosity", C.c_double), ("rho_s", C.c_double),
+        ("rho_w", C.c_double), ("wr_a1", C.c_double), ("wr_a2", C.c_double), ("wr_n", C.c_double),
     ]
 
 
@@ -70,7 +72,7 @@ class State(C.Structure):
         ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double), ("W_kin0", C.c_double),
         ("n_plastic", C.c_int64), ("n_nonconv", C.c_int64), ("n_singular", C.c_int64),
         ("n_overflow", C.c_int64), ("unstable", C.c_int64), ("halted_step", C.c_int64),
-        ("unstable_step", C.c_int64),
+        ("unstable_step", C.c_int64), ("J", C.c_void_p),
     ]
 
 
@@ -103,6 +105,11 @@ def lib():
             L.ppmo_initial_stress.restype = None
             L.ppmo_initial_stress.argtypes = [pp, dp]
             L.ppmo_objective_gradient.argtypes = [pp, dp, C.c_int, C.c_int64, dp, dp]
+            for name in ("ppmo_coupled_saturation", "ppmo_coupled_density"):
+                getattr(L, name).restype = C.c_double
+                getattr(L, name).argtypes = [pp, C.c_double, C.c_double]
+            L.ppmo_coupled_porosity.restype = C.c_double
+            L.ppmo_coupled_porosity.argtypes = [pp, C.c_double]
             L.ppmo_critical_time_step.restype = C.c_double
             L.ppmo_critical_time_step.argtypes = [pp, C.POINTER(State)]
             L.ppmo_num_threads.restype = C.c_int
@@ -138,6 +145,21 @@ def make_params(cfg: dict) -> Params:
 def saturation(suction, alpha, n):
     """van Genuchten S_r standing in for the garbled Eq. 15."""
     return lib().ppmo_saturation(suction, alpha, n)
+
+
+def coupled_saturation(cfg, J, suction):
+    """Eq. 15 as read (R37): S_r at volume ratio J and suction."""
+    return lib().ppmo_coupled_saturation(C.byref(make_params(cfg)), float(J), float(suction))
+
+
+def coupled_porosity(cfg, J):
+    """Eq. 16: porosity at volume ratio J."""
+    return lib().ppmo_coupled_porosity(C.byref(make_params(cfg)), float(J))
+
+
+def coupled_density(cfg, J, suction):
+    """Eq. 48 per current volume: rho_s (1 - phi) + rho_w S_r phi."""
+    return lib().ppmo_coupled_density(C.byref(make_params(cfg)), float(J), float(suction))
 
 
 def time_step(cfg) -> float:
@@ -304,9 +326,10 @@ class Run:
         self.row_ptr = np.zeros(n + 1, np.int32)
         self.col = np.zeros(cap, np.int32)
         self.rev = np.zeros(cap, np.int32)
+        self.J = np.ones(n)
         s = State()
         s.n, s.cap = n, cap
-        for name in ("u", "v", "a", "sig", "pc", "eps_s", "fint", "tforce", "row_ptr", "col", "rev"):
+        for name in ("u", "v", "a", "sig", "pc", "eps_s", "fint", "tforce", "row_ptr", "col", "rev", "J"):
             setattr(s, name, getattr(self, name).ctypes.data)
         self.s = s
         v0a = None if v0 is None else np.ascontiguousarray(v0, np.float64).reshape(3 * n)

@@ -127,9 +127,39 @@ double ppmo_saturation(double suction, double alpha, double n) {
     return pow(1.0 + pow(alpha * suction, n), -(1.0 - 1.0 / n));
 }
 
+/* Eq. 15 with the exponent -(n - 1)/n (as printed, S_r >= 1) and the
+ * porosity in it the initial one, so that J / (1 - phi_0) - 1 is the void
+ * ratio e; p_w = -s.  A point with no voids left is saturated. */
+double ppmo_coupled_saturation(const ppmo_params* p, double J, double suction) {
+    const double e = J / (1.0 - p->porosity) - 1.0;
+    if (!(suction > 0.0) || !(e > 0.0)) return 1.0;
+    const double alpha = p->wr_a1 * pow(e, p->wr_a2) * J;
+    return pow(1.0 + pow(alpha * suction, p->wr_n), -(p->wr_n - 1.0) / p->wr_n);
+}
+
+/* Eq. 16: phi = 1 - (1 - phi_0) / J */
+double ppmo_coupled_porosity(const ppmo_params* p, double J) {
+    return 1.0 - (1.0 - p->porosity) / J;
+}
+
+/* Eq. 48 per current volume: rho_s (1 - phi) + rho_w S_r phi */
+double ppmo_coupled_density(const ppmo_params* p, double J, double suction) {
+    const double phi = ppmo_coupled_porosity(p, J);
+    return p->rho_s * (1.0 - phi) + p->rho_w * ppmo_coupled_saturation(p, J, suction) * phi;
+}
+
+/* the mixture density and S_r s at the start (J = 1) */
+static double rho_start(const ppmo_params* p) {
+    return p->coupled ? ppmo_coupled_density(p, 1.0, p->suction) : p->rho;
+}
+static double srs_at(const ppmo_params* p, double J) {
+    if (p->coupled) return ppmo_coupled_saturation(p, J, p->suction) * p->suction;
+    return ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
+}
+
 double ppmo_time_step(const ppmo_params* p) {
     if (p->dt > 0.0) return p->dt;
-    double cp = sqrt((p->K + 4.0 * p->mu / 3.0) / p->rho);
+    double cp = sqrt((p->K + 4.0 * p->mu / 3.0) / rho_start(p));
     return 0.3 * p->dx / cp;
 }
 
@@ -144,6 +174,10 @@ static int params_ok(const ppmo_params* p) {
     if (!(p->energy_tol >= 0) || !isfinite(p->energy_tol)) return 0;
     if (p->plane_strain != 0 && p->plane_strain != 1) return 0;
     if (p->plane_strain && !((double)p->ny > 4.0 * p->horizon_factor)) return 0;
+    if (p->coupled != 0 && p->coupled != 1) return 0;
+    if (p->coupled && (!(p->porosity > 0.0 && p->porosity < 1.0) || !(p->rho_s > 0) ||
+                       !(p->rho_w >= 0) || !(p->wr_a1 > 0) || !(p->wr_a2 >= 0) || !(p->wr_n > 1)))
+        return 0;
     return 1;
 }
 
@@ -558,10 +592,10 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
                       double dt, const int32_t* row_ptr, const int32_t* col,
                       const int32_t* rev, int64_t cap, double* sig, double* pc,
                       double* eps_s, int update, double* T, double* fint,
-                      pass_counts* cnt_out) {
+                      pass_counts* cnt_out, const double* J, double* Jnew) {
     const double V = p->dx * p->dx * p->dx;
     const double omega = 1.0;
-    const double Srs = ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
+    const double Srs = srs_at(p, 1.0);
     const double delta = p->horizon_factor * p->dx;
     const double d2max = delta * delta;
     int64_t plastic = 0, nonconv = 0, singular = 0;
@@ -571,7 +605,9 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
         double sig_i[6];
         for (int c = 0; c < 6; c++) sig_i[c] = sig[c * n + i];
         double pc_i = pc[i];
-        double w = 0.0, acc_sig[6] = {0}, acc_pc = 0.0, acc_es = 0.0;
+        double w = 0.0, acc_sig[6] = {0}, acc_pc = 0.0, acc_es = 0.0, acc_ev = 0.0;
+        /* coupled mode: S_r of the point's volume at the start of the step */
+        const double Srs_i = (p->coupled && J) ? srs_at(p, J[i]) : Srs;
         for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++)
             for (int c = 0; c < 3; c++) T[c * cap + b] = 0.0;
         for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
@@ -596,11 +632,13 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
                 ppmo_material_update(p, sig_i, pc_i, Lf, dt, sig_b, &pc_b, &des, &fl);
                 if (fl & 1) plastic++;
                 if (fl & 2) nonconv++;
+                /* the bond's volumetric strain increment (reading R37) */
+                acc_ev += varpi * dt * (L[0][0] + L[1][1] + L[2][2]);
             }
             /* total stress sigma_bar - S_r p_w 1 with p_w = -s (Eq. 32) */
             double St[3][3], SK[3][3];
             sym_to_mat(sig_b, St);
-            for (int c = 0; c < 3; c++) St[c][c] += Srs;
+            for (int c = 0; c < 3; c++) St[c][c] += Srs_i;
             matmul3(St, Ki, SK);
             if (p->model == 2) {
                 /* power-conjugate form: the force state of this sub-horizon
@@ -640,15 +678,20 @@ static void bond_pass(const ppmo_params* p, int64_t n, const double* x, const do
             pc[i] = acc_pc / w;
             eps_s[i] += acc_es / w;
         }
+        /* J_{n+1} = J_n exp(varpi-mean of dt tr L_b) (reading R37) */
+        if (Jnew) Jnew[i] = (update && w > 0.0) ? J[i] * exp(acc_ev / w) : J[i];
     }
-    /* pairwise nodal force, Eq. 49-50: f_i = V^2 sum_j (T_(ij) - T_(ji)) */
+    /* pairwise nodal force, Eq. 49-50: f_i = V_i sum_j (T_(ij) - T_(ji)) V_j,
+     * with V = J dx^3 in the coupled mode (J at the start of the step) */
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         for (int c = 0; c < 3; c++) {
             double s = 0.0;
-            for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++)
-                s += T[c * cap + b] - T[c * cap + rev[b]];
-            fint[c * n + i] = V * V * s;
+            for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; b++) {
+                const double Vj = (p->coupled && J) ? J[col[b]] : 1.0;
+                s += (T[c * cap + b] - T[c * cap + rev[b]]) * Vj;
+            }
+            fint[c * n + i] = V * V * s * ((p->coupled && J) ? J[i] : 1.0);
         }
     }
     /* Eq. 91 between material points of the soil (reading R36): a pair
@@ -686,7 +729,7 @@ int ppmo_internal_force(const ppmo_params* p, int64_t n, const double* x, const 
     if (!T || !sg || !pcs || !es) { free(T); free(sg); free(pcs); free(es); return -2; }
     memcpy(sg, sig, sizeof(double) * 6 * (size_t)n);
     double* vel = (double*)calloc(3 * (size_t)n, sizeof(double));
-    bond_pass(p, n, x, vel, 0.0, row_ptr, col, rev, B, sg, pcs, es, 0, T, f, NULL);
+    bond_pass(p, n, x, vel, 0.0, row_ptr, col, rev, B, sg, pcs, es, 0, T, f, NULL, NULL, NULL);
     free(vel); free(T); free(sg); free(pcs); free(es);
     return 0;
 }
@@ -732,8 +775,16 @@ static int constrained(const ppmo_params* p, int64_t id, int c, double* vbar) {
  * half step without it, |F_t| <= mu_f F_n, limited so that it never
  * reverses that velocity.  The forces are added to f (x: positions, w: the
  * velocity the step starts the half step from, hdt: half the step). */
+/* point masses (Eq. 48): rho dx^3, or in the coupled mode the mixture
+ * density of the volume ratio J times J dx^3 */
+static void point_masses(const ppmo_params* p, int64_t n, const double* J, double* mass) {
+    const double V = p->dx * p->dx * p->dx;
+    for (int64_t i = 0; i < n; i++)
+        mass[i] = p->coupled ? ppmo_coupled_density(p, J[i], p->suction) * J[i] * V : p->rho * V;
+}
+
 static void add_contact(const ppmo_params* p, int64_t n, const double* x, const double* w,
-                        double hdt, double m, double* f) {
+                        double hdt, const double* mass, double* f) {
     const double dc = p->contact_cutoff * p->dx;
     const double zs = -dc;
     for (int64_t i = 0; i < n; i++) {
@@ -744,12 +795,12 @@ static void add_contact(const ppmo_params* p, int64_t n, const double* x, const 
         if (p->friction > 0.0 && hdt > 0.0) {
             double vt[2], nrm = 0.0;
             for (int c = 0; c < 2; c++) {
-                vt[c] = w[c * n + i] + hdt * (f[c * n + i] / m + p->gravity[c]);
+                vt[c] = w[c * n + i] + hdt * (f[c * n + i] / mass[i] + p->gravity[c]);
                 nrm += vt[c] * vt[c];
             }
             nrm = sqrt(nrm);
             if (nrm > 0.0) {
-                const double Ft = fmin(p->friction * Fn, m * nrm / hdt);
+                const double Ft = fmin(p->friction * Fn, mass[i] * nrm / hdt);
                 for (int c = 0; c < 2; c++) f[c * n + i] -= Ft * vt[c] / nrm;
             }
         }
@@ -786,7 +837,7 @@ static int rebuild(const ppmo_params* p, ppmo_state* s, const double* x) {
  * init_stress = 1.  sig is 6n. */
 void ppmo_initial_stress(const ppmo_params* p, double* sig) {
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
-    const double Srs = ppmo_saturation(p->suction, p->vg_alpha, p->vg_n) * p->suction;
+    const double Srs = srs_at(p, 1.0);
     const double nu = (3.0 * p->K - 2.0 * p->mu) / (2.0 * (3.0 * p->K + p->mu));
     const double K0 = nu / (1.0 - nu);
     const double gmag = -p->gravity[2];
@@ -795,7 +846,7 @@ void ppmo_initial_stress(const ppmo_params* p, double* sig) {
         for (int c = 0; c < 6; c++) sig[c * n + i] = 0.0;
         if (p->init_stress == 0) {
             double d = (double)(p->nz - 1 - iz) * p->dx;
-            double szz = -p->rho * gmag * d;
+            double szz = -rho_start(p) * gmag * d;
             sig[0 * n + i] = K0 * szz - Srs;
             sig[1 * n + i] = K0 * szz - Srs;
             sig[2 * n + i] = szz - Srs;
@@ -813,7 +864,6 @@ int ppmo_init_state(const ppmo_params* p, const double* u0, const double* v0, co
     if (!params_ok(p)) return -1;
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
     if (s->n != n) return -1;
-    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
     for (int64_t i = 0; i < n; i++) {
         for (int c = 0; c < 3; c++) {
             s->u[c * n + i] = u0 ? u0[c * n + i] : 0.0;
@@ -832,18 +882,22 @@ int ppmo_init_state(const ppmo_params* p, const double* u0, const double* v0, co
     s->n_overflow = 0;
     int rc = rebuild(p, s, x);
     if (rc < 0) { free(x); return rc; }
+    for (int64_t i = 0; i < n; i++) s->J[i] = 1.0;
+    double* mass = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!mass) { free(x); return -2; }
+    point_masses(p, n, s->J, mass);
     bond_pass(p, n, x, s->v, 0.0, s->row_ptr, s->col, s->rev, s->cap, s->sig, s->pc,
-              s->eps_s, 0, s->tforce, s->fint, NULL);
-    if (p->contact) add_contact(p, n, x, s->v, 0.5 * ppmo_time_step(p), m, s->fint);
+              s->eps_s, 0, s->tforce, s->fint, NULL, s->J, NULL);
+    if (p->contact) add_contact(p, n, x, s->v, 0.5 * ppmo_time_step(p), mass, s->fint);
     double wk = 0.0;
     for (int64_t i = 0; i < n; i++)
         for (int c = 0; c < 3; c++) {
-            double a = s->fint[c * n + i] / m + p->gravity[c], vbar;      /* Eq. 62 */
+            double a = s->fint[c * n + i] / mass[i] + p->gravity[c], vbar;      /* Eq. 62 */
             if (constrained(p, i, c, &vbar)) a = 0.0;
             s->a[c * n + i] = a;
-            wk += 0.5 * m * s->v[c * n + i] * s->v[c * n + i];
+            wk += 0.5 * mass[i] * s->v[c * n + i] * s->v[c * n + i];
         }
-    free(x);
+    free(x); free(mass);
     s->step = 0;
     s->W_int = 0.0; s->W_ext = 0.0; s->W_kin = wk; s->W_kin0 = wk;
     s->n_plastic = s->n_nonconv = s->n_singular = 0;
@@ -861,17 +915,23 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
     if (!params_ok(p)) return -1;
     const int64_t n = s->n;
     const double dt = ppmo_time_step(p);
-    const double V = p->dx * p->dx * p->dx, m = p->rho * V;
     double* x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     double* vh = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     double* f_old = (double*)malloc(sizeof(double) * 3 * (size_t)n);
-    if (!x || !vh || !f_old) { free(x); free(vh); free(f_old); return -2; }
+    double* mass = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Jnew = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!x || !vh || !f_old || !mass || !Jnew) {
+        free(x); free(vh); free(f_old); free(mass); free(Jnew);
+        return -2;
+    }
     for (int st = 0; st < n_steps; st++) {
         if (p->halt_on_unstable && s->halted_step) {     /* the run has stopped */
             s->step++;
             continue;
         }
         memcpy(f_old, s->fint, sizeof(double) * 3 * (size_t)n);
+        /* masses of the volumes at the start of the step (Eq. 48) */
+        point_masses(p, n, s->J, mass);
         /* predictor, Eq. 60-61 with beta1 = 1/2, beta2 = 0; boundary
          * conditions; displacement, Eq. 64 (Alg. 2 lines 6-8) */
         for (int64_t i = 0; i < n; i++)
@@ -886,15 +946,16 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         /* internal force, Alg. 1 (Alg. 2 line 9) */
         pass_counts pcnt;
         bond_pass(p, n, x, vh, dt, s->row_ptr, s->col, s->rev, s->cap, s->sig, s->pc,
-                  s->eps_s, 1, s->tforce, s->fint, &pcnt);
+                  s->eps_s, 1, s->tforce, s->fint, &pcnt, s->J, Jnew);
         s->n_plastic += pcnt.plastic;
         s->n_nonconv += pcnt.nonconv;
         s->n_singular += pcnt.singular;
-        if (p->contact) add_contact(p, n, x, vh, 0.5 * dt, m, s->fint);
+        if (p->contact) add_contact(p, n, x, vh, 0.5 * dt, mass, s->fint);
         /* acceleration and velocity corrector, Eq. 62-63 */
         double dWi = 0.0, dWe = 0.0, wk = 0.0;
         for (int64_t i = 0; i < n; i++)
             for (int c = 0; c < 3; c++) {
+                const double m = mass[i];
                 double a = s->fint[c * n + i] / m + p->gravity[c], vbar;
                 const int fixed = constrained(p, i, c, &vbar);
                 if (fixed) a = 0.0;
@@ -917,6 +978,7 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         s->W_ext += dWe;
         s->W_kin = wk;
         s->step++;
+        if (p->coupled) memcpy(s->J, Jnew, sizeof(double) * (size_t)n);
         /* the energy check of Eq. 69 (R20): diagnostic, or a hard stop */
         const double bal = fabs(s->W_int + s->W_kin - s->W_ext - s->W_kin0);
         const double mx = fmax(fmax(s->W_kin, fabs(s->W_int)), fmax(fabs(s->W_ext), s->W_kin0));
@@ -926,7 +988,7 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
             if (p->halt_on_unstable && !s->halted_step) s->halted_step = s->step;
         }
     }
-    free(x); free(vh); free(f_old);
+    free(x); free(vh); free(f_old); free(mass); free(Jnew);
     return 0;
 }
 
@@ -1280,7 +1342,7 @@ static int is_top(const ppmo_params* p, int64_t id) {
 int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps, int64_t cap,
                             double* J, double grad[4]) {
     if (!params_ok(p) || p->model == 2 || n_steps < 0 || p->contact || p->halt_on_unstable ||
-        p->plane_strain)
+        p->plane_strain || p->coupled)
         return -1;
     const int64_t n = (int64_t)p->nx * p->ny * p->nz;
     ppmo_state s;
@@ -1298,6 +1360,7 @@ int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps,
     s.row_ptr = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
     s.col = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
     s.rev = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
+    s.J = (double*)calloc((size_t)n, sizeof(double));
     /* states before every step and the family each step used */
     const size_t N3 = 3 * (size_t)n, N6 = 6 * (size_t)n;
     double* hist = (double*)malloc(sizeof(double) * (N3 * 3 + N6 + (size_t)n) * ((size_t)n_steps + 1));
@@ -1365,7 +1428,7 @@ int ppmo_objective_gradient(const ppmo_params* p, const double* v0, int n_steps,
     free(fam0.row_ptr); free(fam0.col); free(fam0.rev);
     free(ub); free(vb); free(ab); free(sb); free(pcb);
     free(s.u); free(s.v); free(s.a); free(s.sig); free(s.pc); free(s.eps_s); free(s.fint);
-    free(s.tforce); free(s.row_ptr); free(s.col); free(s.rev);
+    free(s.tforce); free(s.row_ptr); free(s.col); free(s.rev); free(s.J);
     return 0;
 }
 
@@ -1395,7 +1458,7 @@ double ppmo_critical_time_step(const ppmo_params* p, const ppmo_state* s) {
             sum += 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         }
         if (sum > 0.0) {
-            const double dt = sqrt(2.0 * p->rho / (V * C * sum));
+            const double dt = sqrt(2.0 * rho_start(p) / (V * C * sum));
             if (dt < best) best = dt;
         }
     }

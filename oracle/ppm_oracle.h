@@ -68,6 +68,12 @@ typedef struct {
     int32_t plane_strain;        /* 1: plane strain in x-z (reading R35): y is
                                     periodic with period ny dx (ny dx > 4 delta)
                                     and v_y is held at zero                   */
+    int32_t coupled;             /* 1: deformation-dependent porosity, degree of
+                                    saturation, volume and mass (Eq. 15-16, 48-49;
+                                    reading R37); rho and vg_* are then unused */
+    double porosity;             /* phi_0, initial porosity                    */
+    double rho_s, rho_w;         /* solid and water densities (kg/m^3)         */
+    double wr_a1, wr_a2, wr_n;   /* Eq. 15: a1 (1/Pa), a2, n                   */
 } ppmo_params;
 
 typedef struct {
@@ -88,11 +94,19 @@ typedef struct {
     int64_t unstable;            /* 1 once a step failed the Eq. 69 check         */
     int64_t halted_step;         /* halt_on_unstable: that step (from 1), else 0  */
     int64_t unstable_step;       /* the first step that failed it (from 1), else 0 */
+    double *J;                   /* n: volume ratio (coupled = 1; else unused)   */
 } ppmo_state;
 
 /* Eq. (15) replaced by the van Genuchten curve (see DESIGN readings). */
 double ppmo_saturation(double suction, double alpha, double n);
-/* Time step used when p->dt <= 0: 0.3 dx / sqrt((K + 4 mu / 3) / rho). */
+/* Coupled mode (reading R37): S_r of Eq. 15 at volume ratio J and suction s,
+ * the porosity of Eq. 16 and the mixture density of Eq. 48 per current
+ * volume. */
+double ppmo_coupled_saturation(const ppmo_params* p, double J, double suction);
+double ppmo_coupled_porosity(const ppmo_params* p, double J);
+double ppmo_coupled_density(const ppmo_params* p, double J, double suction);
+/* Time step used when p->dt <= 0: 0.3 dx / sqrt((K + 4 mu / 3) / rho), rho
+ * the initial mixture density in the coupled mode. */
 double ppmo_time_step(const ppmo_params* p);
 
 /* Eq. (1): brute-force family search.  x is 3n component-major.  group may

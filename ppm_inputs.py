@@ -42,6 +42,10 @@ MATERIAL = dict(
     contact_cutoff=0.8,     # delta_c / dx (Sec. 4.2)
     energy_tol=0.0,         # tolerance of the Eq. 69 energy check; 0: 1e-2
     plane_strain=0,         # 1: plane strain in x-z, y periodic (ny dx > 4 delta), v_y = 0
+    coupled=0,              # 1: J-dependent porosity, S_r, volume and mass (Eq. 15-16, 48-49)
+    porosity=0.2,           # phi_0 (Sec. 4.2)
+    rho_s=2200.0, rho_w=1000.0,   # kg/m^3 (Sec. 4.2)
+    wr_a1=0.038, wr_a2=3.49, wr_n=1.25,      # Eq. 15 (Sec. 4.2; a1 read per Pa)
 )
 
 #: The five workloads: (description, overrides).
