@@ -79,6 +79,7 @@ extern "C" {
 #define PPM_FIELD_COL      8   /* int32, bonds (ascending within a row)      */
 #define PPM_FIELD_REV      9   /* int32, bonds: index of bond (j,i), -1 none */
 #define PPM_FIELD_TFORCE  10   /* force state per bond, 3 x bonds            */
+#define PPM_FIELD_J       11   /* volume ratio J (coupled = 1), N            */
 
 typedef struct {
     int32_t nx, ny, nz;          /* lattice of the column (single-column runs)  */
@@ -147,6 +148,20 @@ typedef struct {
                                     zero, so a y-invariant start stays
                                     y-invariant.  Single columns only; not
                                     with the adjoint calls                     */
+    int32_t coupled;             /* 1: deformation-dependent porosity, degree of
+                                    saturation, volume and mass (Eq. 15-16,
+                                    48-49): each point carries its volume ratio
+                                    J, updated from its bonds' volumetric rate;
+                                    phi = 1 - (1 - phi_0) / J; S_r from Eq. 15
+                                    (exponent -(n-1)/n, void ratio J / (1 -
+                                    phi_0) - 1); V = J dx^3 in the pairwise
+                                    force and the mass [rho_s (1 - phi) + rho_w
+                                    S_r phi] V, all at J of the start of the
+                                    step.  rho and vg_* are then unused.
+                                    Single columns only; not with the adjoint */
+    double porosity;             /* phi_0 in (0, 1), coupled = 1               */
+    double rho_s, rho_w;         /* solid and water densities, coupled = 1     */
+    double wr_a1, wr_a2, wr_n;   /* Eq. 15: a1 (1/Pa, > 0), a2 (>= 0), n (> 1) */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */

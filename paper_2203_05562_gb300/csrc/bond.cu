@@ -75,7 +75,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     // model 2: per sender bond, its matrix M = varpi sigma K^-1 (9), and (FP32) the
     // terms of its membership test, -2 zeta~ (3) and |zeta~|^2 - hf^2 (1)
     __shared__ alignas(16) Real s_M[MODEL == 2 ? kMaxRow : 1][F64 ? 9 : 16];
-    __shared__ Real s_red[NW][12];
+    __shared__ Real s_red[NW][13];
     __shared__ unsigned s_cnt[NW][5];
     // FP32 path: a plastic bond's trial stress, K~^-1, varpi and strain
     // measure, parked by its thread while the return runs (model 2 parks in
@@ -98,7 +98,14 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     const Real pc_i = s.pc[i];
     const Real eps_i = s.eps[i];
     const ColumnConst cc = s.cols[s.colid[i]];
-    const Real Srs = F64 ? (Real)cc.Srs : (Real)cc.Srsf;
+    Real Srs = F64 ? (Real)cc.Srs : (Real)cc.Srsf;
+    // coupled mode: S_r of the point's volume ratio at the start of the step
+    Real Ji = (Real)1;
+    if (k.coupled) {
+        Real mass_unused;
+        Ji = s.J[i];
+        coupled_point<Real>(k, Ji, Srs, mass_unused);
+    }
 
     // stage the family of i: bond vectors and relative velocities
     double pxi = 0, pyi = 0, pzi = 0;
@@ -132,7 +139,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         y.x = s.vh[j] - vxi;
         y.y = s.vh[n + j] - vyi;
         y.z = s.vh[2 * n + j] - vzi;
-        y.w = (Real)0;
+        y.w = k.coupled ? s.J[j] : (Real)0;          // the member's volume ratio
         s_z[t] = z;
         s_y[t] = y;
     }
@@ -142,9 +149,12 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
 
     // per-thread partial sums over its bonds (fixed order)
-    Real red[12];
+    // red: sum varpi, varpi sigma (6), varpi pc, varpi deps_s, row sum of T
+    // (3), and in the coupled mode varpi dt tr L
+    Real red[13];
 #pragma unroll
-    for (int e = 0; e < 12; e++) red[e] = (Real)0;
+    for (int e = 0; e < 13; e++) red[e] = (Real)0;
+    const Real dtr = F64 ? (Real)k.dt : (Real)k.dtf;
     unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
 
     if constexpr (MODEL == 1) {
@@ -184,6 +194,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         BondStress<Real> bs;
         bs.plastic = 0; bs.nonconv = 0; bs.ret64 = 0;
         Real SK[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        Real ev = (Real)0;                                  // dt tr L of the point
         if (active) {
             const Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
                                 (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
@@ -197,6 +208,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                     for (int c = 0; c < 3; c++)
                         L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
                                         A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
+                ev = (L[0] + L[4] + L[8]) * dtr;
                 Real st[6], des;
                 if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
                     material_return<Real>(st, pc_i, k, cc.M, cc.Mf, bs);
@@ -228,36 +240,23 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             n_pairs += cnt;
             if (!active) {
                 n_singular++;
-                Real C0 = (Real)0, C1 = (Real)0, C2 = (Real)0;
-                pair_contact(k, s_z[t], C0, C1, C2);
-                s.T[r0 + t] = C0;
-                s.T[k.cap + r0 + t] = C1;
-                s.T[2 * k.cap + r0 + t] = C2;
-                if (rb >= 0) {
-                    s.Trev[rb] = C0;
-                    s.Trev[k.cap + rb] = C1;
-                    s.Trev[2 * k.cap + rb] = C2;
-                }
-                red[9] += C0; red[10] += C1; red[11] += C2;
+                Real o[3];
+                store_force_state(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, s_z[t],
+                                  s_y[t].w, Ji, o);
+                red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
                 continue;
             }
             n_plastic += bs.plastic;
             n_nonconv += bs.nonconv;
             n_ret64 += bs.ret64;
             const R4<Real> zj = s_z[t];
-            Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
-            Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
-            Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
-            pair_contact(k, zj, T0, T1, T2);
-            s.T[r0 + t] = T0;
-            s.T[k.cap + r0 + t] = T1;
-            s.T[2 * k.cap + r0 + t] = T2;
-            if (rb >= 0) {
-                s.Trev[rb] = T0;
-                s.Trev[k.cap + rb] = T1;
-                s.Trev[2 * k.cap + rb] = T2;
-            }
-            red[9] += T0; red[10] += T1; red[11] += T2;
+            const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+            const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+            const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            Real o[3];
+            store_force_state(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, Ji, o);
+            red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
+            red[12] += varpi * ev;
             red[0] += varpi;
 #pragma unroll
             for (int c = 0; c < 6; c++) red[1 + c] += varpi * bs.sig[c];
@@ -329,17 +328,10 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         if (!active) {
             n_singular++;
             if constexpr (MODEL != 2) {
-                Real C0 = (Real)0, C1 = (Real)0, C2 = (Real)0;
-                pair_contact(k, zj, C0, C1, C2);
-                s.T[r0 + t] = C0;
-                s.T[k.cap + r0 + t] = C1;
-                s.T[2 * k.cap + r0 + t] = C2;
-                if (rb >= 0) {
-                    s.Trev[rb] = C0;
-                    s.Trev[k.cap + rb] = C1;
-                    s.Trev[2 * k.cap + rb] = C2;
-                }
-                red[9] += C0; red[10] += C1; red[11] += C2;
+                Real o[3];
+                store_force_state(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, zj,
+                                  s_y[t].w, Ji, o);
+                red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
             } else {
 #pragma unroll
                 for (int e = 0; e < 9; e++) s_M[t][e] = (Real)0;
@@ -364,6 +356,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 for (int c = 0; c < 3; c++)
                     L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
                                     A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
+            if (k.coupled) red[12] += varpi * (L[0] + L[4] + L[8]) * dtr;
             Real st[6], des;
             if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
                 if constexpr (!F64) {
@@ -421,19 +414,12 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                                          S[r * 3 + 2] * Ki[2 * 3 + c]);
         if constexpr (MODEL != 2) {
             // force state on the bond itself (Eq. 31-32, 51)
-            Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
-            Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
-            Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
-            pair_contact(k, zj, T0, T1, T2);
-            s.T[r0 + t] = T0;
-            s.T[k.cap + r0 + t] = T1;
-            s.T[2 * k.cap + r0 + t] = T2;
-            if (rb >= 0) {
-                s.Trev[rb] = T0;
-                s.Trev[k.cap + rb] = T1;
-                s.Trev[2 * k.cap + rb] = T2;
-            }
-            red[9] += T0; red[10] += T1; red[11] += T2;
+            const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+            const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+            const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+            Real o[3];
+            store_force_state(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, Ji, o);
+            red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
         } else {
 #pragma unroll
             for (int e = 0; e < 9; e++) s_M[t][e] = SK[e];
@@ -448,7 +434,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         red[8] += varpi * bs.des;
     }
     }
-    block_sum<12, Real>(red, s_red);
+    block_sum<13, Real>(red, s_red);
     const Real w = red[0];
 
     if constexpr (MODEL == 2) {
@@ -491,19 +477,12 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 #pragma unroll
                 for (int e = 0; e < 9; e++) N[e] = Nf[e];
             }
-            Real T0 = (N[0] * zt.x + N[1] * zt.y + N[2] * zt.z) * inv_w;
-            Real T1 = (N[3] * zt.x + N[4] * zt.y + N[5] * zt.z) * inv_w;
-            Real T2 = (N[6] * zt.x + N[7] * zt.y + N[8] * zt.z) * inv_w;
-            pair_contact(k, zt, T0, T1, T2);
-            s.T[r0 + t] = T0;
-            s.T[k.cap + r0 + t] = T1;
-            s.T[2 * k.cap + r0 + t] = T2;
-            if (rb >= 0) {
-                s.Trev[rb] = T0;
-                s.Trev[k.cap + rb] = T1;
-                s.Trev[2 * k.cap + rb] = T2;
-            }
-            ts[0] += T0; ts[1] += T1; ts[2] += T2;
+            const Real T0 = (N[0] * zt.x + N[1] * zt.y + N[2] * zt.z) * inv_w;
+            const Real T1 = (N[3] * zt.x + N[4] * zt.y + N[5] * zt.z) * inv_w;
+            const Real T2 = (N[6] * zt.x + N[7] * zt.y + N[8] * zt.z) * inv_w;
+            Real o[3];
+            store_force_state(s, k, (size_t)r0 + t, rb, T0, T1, T2, zt, s_y[t].w, Ji, o);
+            ts[0] += o[0]; ts[1] += o[1]; ts[2] += o[2];
         }
         block_sum<3, Real>(ts, reinterpret_cast<Real(*)[3]>(&s_red[0][0]));
         red[9] = ts[0]; red[10] = ts[1]; red[11] = ts[2];
@@ -519,6 +498,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             s.pc[i] = red[7] * iw;
             s.eps[i] = eps_i + red[8] * iw;
         }
+        // coupled mode: J_{n+1} = J_n exp(varpi-mean of dt tr L_b)
+        if (update && k.coupled) s.Jn[i] = w > (Real)0 ? Ji * exp(red[12] / w) : Ji;
         s.tsum[i] = red[9];
         s.tsum[n + i] = red[10];
         s.tsum[2 * n + i] = red[11];
@@ -551,8 +532,15 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int i = blockIdx.x * kWarpPointsPerBlock + wib;       // one warp per point
     const size_t n = (size_t)k.npoints;
-    const Real m = F64 ? (Real)(k.rho * k.dx * k.dx * k.dx) : (Real)k.massf;
-    const Real dx2 = F64 ? (Real)(k.dx * k.dx) : (Real)k.dx2f;
+    Real m = F64 ? (Real)(k.rho * k.dx * k.dx * k.dx) : (Real)k.massf;
+    Real dx2 = F64 ? (Real)(k.dx * k.dx) : (Real)k.dx2f;
+    // coupled mode: the point's mass and its volume factor J (start of the step)
+    if (k.coupled && i < k.npoints) {
+        const Real Jp = s.J[i];
+        Real srs_unused;
+        coupled_point<Real>(k, Jp, srs_unused, m);
+        dx2 = dx2 * Jp;
+    }
     const Real inv_rho_dx = F64 ? (Real)(1.0 / (k.rho * k.dx)) : (Real)k.inv_rho_dxf;
     const Real dtr = F64 ? (Real)dt : (Real)(float)dt;
     const Real hdt = (Real)0.5 * dtr;
@@ -650,6 +638,7 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
             const Real fhat = ts - gathered;
             Real f = fhat * dx2;                                     // Eq. 49-50
             Real a = fhat * inv_rho_dx + g;                          // Eq. 62
+            if (k.coupled) a = f / m + g;
             if (k.contact) {
                 f += fcon;                                           // Eq. 93
                 a = f / m + g;
@@ -676,6 +665,9 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
             }
             if (bad) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
         }
+        // coupled mode: the volume ratio the bond pass computed is the next
+        // step's (every reader of J in this step has run)
+        if (k.coupled && !initial && lane == 0) s.J[i] = s.Jn[i];
     }
     // energies of the point: lanes 0..2 hold the three components
     dwi += __shfl_down_sync(0xffffffffu, dwi, 1) + __shfl_down_sync(0xffffffffu, dwi, 2);
@@ -768,6 +760,8 @@ __global__ void k_init_state(DevState<Real> s, StepConst k, int init_stress, dou
         for (int c = 0; c < 6; c++) s.sig[(size_t)c * n + i] = (Real)sg[c];
         s.pc[i] = (Real)(-pc0);
         s.eps[i] = (Real)0;
+        s.J[i] = (Real)1;
+        s.Jn[i] = (Real)1;
     }
 }
 

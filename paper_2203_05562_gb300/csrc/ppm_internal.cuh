@@ -67,6 +67,9 @@ struct StepConst {
     int contact;                 // 1: rigid flat substrate at z = -delta_c (no fixed base)
     double contact_modulus, friction, contact_dc;   // C_s (Pa), mu_f, delta_c (m)
     float contact_kf, frictionf, contact_dcf;        // C_s dx^2, mu_f, delta_c in FP32
+    int coupled;                 // 1: J-dependent porosity, S_r, volume and mass
+    double phi0, rho_s, rho_w, wr_a1, wr_a2, wr_n, wr_s;     // and the column's suction
+    float phi0f, rho_sf, rho_wf, wr_a1f, wr_a2f, wr_nf, wr_sf;
     double pair_dc, pair_kappa;  // between points: delta_c / dx and C_s / (2 delta_c / dx)
     float pair_dcf, pair_kappaf; // the same in FP32
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
@@ -95,6 +98,32 @@ __device__ __forceinline__ void pair_contact(const StepConst& k, const V4& z, Re
     }
 }
 
+// Coupled mode at volume ratio J: S_r s of Eq. 15 (exponent -(n - 1)/n,
+// void ratio e = J / (1 - phi_0) - 1, p_w = -s; saturated when no voids or
+// no suction) and the point mass [rho_s (1 - phi) + rho_w S_r phi] J dx^3
+// with phi = 1 - (1 - phi_0) / J (Eq. 16, 48).
+template <typename Real>
+__device__ __forceinline__ void coupled_point(const StepConst& k, Real J, Real& Srs, Real& mass) {
+    constexpr bool F64 = sizeof(Real) == 8;
+    const Real phi0 = F64 ? (Real)k.phi0 : (Real)k.phi0f;
+    const Real s = F64 ? (Real)k.wr_s : (Real)k.wr_sf;
+    const Real e = J / ((Real)1 - phi0) - (Real)1;
+    Real Sr = (Real)1;
+    if (s > (Real)0 && e > (Real)0) {
+        const Real a1 = F64 ? (Real)k.wr_a1 : (Real)k.wr_a1f;
+        const Real a2 = F64 ? (Real)k.wr_a2 : (Real)k.wr_a2f;
+        const Real nn = F64 ? (Real)k.wr_n : (Real)k.wr_nf;
+        const Real alpha = a1 * pow(e, a2) * J;
+        Sr = pow((Real)1 + pow(alpha * s, nn), -(nn - (Real)1) / nn);
+    }
+    const Real phi = (Real)1 - ((Real)1 - phi0) / J;
+    const Real rs = F64 ? (Real)k.rho_s : (Real)k.rho_sf;
+    const Real rw = F64 ? (Real)k.rho_w : (Real)k.rho_wf;
+    const Real dx3 = F64 ? (Real)(k.dx * k.dx * k.dx) : (Real)k.dxf * (Real)k.dxf * (Real)k.dxf;
+    Srs = Sr * s;
+    mass = (rs * ((Real)1 - phi) + rw * Sr * phi) * J * dx3;
+}
+
 // plane strain: the periodic image of point j (lattice index lj) nearest to
 // point i (li) in y, as a multiple of the period: -1, 0 or 1
 __host__ __device__ __forceinline__ int image_shift(const StepConst& k, int lj, int li) {
@@ -120,6 +149,8 @@ struct DevState {
     Real* eps;           // N
     Real* fint;          // 3N
     Real* tsum;          // 3N sum of own force states (scaled)
+    Real* J;             // N volume ratio at the start of the step (coupled mode)
+    Real* Jn;            // N its update by the bond pass, copied to J by the gather
     int32_t* row_ptr;    // N+1
     int32_t* col;        // cap
     int32_t* rev;        // cap
@@ -139,6 +170,36 @@ struct DevState {
     int32_t* scanbuf;    // block sums of the scans
     int ncell_cap;
 };
+
+// Stores the force state T of bond (i, j) (row slot b, reverse slot rb) with
+// the pair repulsion of the bond (z: the bond in lattice units) and, in the
+// coupled mode, the point volumes: the own row carries J_j T + C / J_i and
+// the reverse slot J_i T + C / J_j, so that the gather's factor J dx^2 gives
+// V_i V_j (T_ij - T_ji) (Eq. 49) and the unscaled pair force.  Returns the
+// own-row value for the row sum.
+template <typename Real, typename V4>
+__device__ __forceinline__ void store_force_state(const DevState<Real>& s, const StepConst& k,
+                                                  size_t b, int rb, Real T0, Real T1, Real T2,
+                                                  const V4& z, Real Jj, Real Ji, Real out[3]) {
+    Real C0 = (Real)0, C1 = (Real)0, C2 = (Real)0;
+    pair_contact(k, z, C0, C1, C2);
+    Real o[3], r[3];
+    if (k.coupled) {
+        o[0] = Jj * T0 + C0 / Ji; o[1] = Jj * T1 + C1 / Ji; o[2] = Jj * T2 + C2 / Ji;
+        r[0] = Ji * T0 + C0 / Jj; r[1] = Ji * T1 + C1 / Jj; r[2] = Ji * T2 + C2 / Jj;
+    } else {
+        o[0] = r[0] = T0 + C0; o[1] = r[1] = T1 + C1; o[2] = r[2] = T2 + C2;
+    }
+    s.T[b] = o[0];
+    s.T[k.cap + b] = o[1];
+    s.T[2 * k.cap + b] = o[2];
+    if (rb >= 0) {
+        s.Trev[rb] = r[0];
+        s.Trev[k.cap + rb] = r[1];
+        s.Trev[2 * k.cap + rb] = r[2];
+    }
+    out[0] = o[0]; out[1] = o[1]; out[2] = o[2];
+}
 
 // Boundary conditions (the fixed base; the loading of Sec. 4.1): true when
 // velocity component c of point i is prescribed, with the value in vbar.

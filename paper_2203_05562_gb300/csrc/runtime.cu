@@ -77,6 +77,20 @@ double saturation(double s, double alpha, double n) {
     return pow(1.0 + pow(alpha * s, n), -(1.0 - 1.0 / n));
 }
 
+// coupled mode (Eq. 15-16, 48) at volume ratio J, on the host: S_r with the
+// void ratio J / (1 - phi_0) - 1 and the mixture density per current volume
+double coupled_saturation(const ppm_params* p, double J, double s) {
+    const double e = J / (1.0 - p->porosity) - 1.0;
+    if (!(s > 0.0) || !(e > 0.0)) return 1.0;
+    const double alpha = p->wr_a1 * pow(e, p->wr_a2) * J;
+    return pow(1.0 + pow(alpha * s, p->wr_n), -(p->wr_n - 1.0) / p->wr_n);
+}
+
+double coupled_density(const ppm_params* p, double J, double s) {
+    const double phi = 1.0 - (1.0 - p->porosity) / J;
+    return p->rho_s * (1.0 - phi) + p->rho_w * coupled_saturation(p, J, s) * phi;
+}
+
 int check_params(const ppm_params* p) {
     if (!p) return PPM_EINVAL;
     if (!(p->dx > 0) || !(p->horizon_factor > 0) || !(p->rho > 0)) return PPM_EINVAL;
@@ -100,6 +114,12 @@ int check_params(const ppm_params* p) {
     if (p->contact != 0 && p->contact != 1) return PPM_EINVAL;
     if (!(p->energy_tol >= 0) || !std::isfinite(p->energy_tol)) return PPM_EINVAL;
     if (p->plane_strain != 0 && p->plane_strain != 1) return PPM_EINVAL;
+    if (p->coupled != 0 && p->coupled != 1) return PPM_EINVAL;
+    if (p->coupled && (!(p->porosity > 0.0 && p->porosity < 1.0) || !(p->rho_s > 0) ||
+                       !(p->rho_w >= 0) || !(p->wr_a1 > 0) || !(p->wr_a2 >= 0) || !(p->wr_n > 1) ||
+                       !std::isfinite(p->rho_s) || !std::isfinite(p->rho_w) ||
+                       !std::isfinite(p->wr_a1) || !std::isfinite(p->wr_a2) || !std::isfinite(p->wr_n)))
+        return PPM_EINVAL;
     if (p->contact && (!(p->contact_modulus >= 0) || !(p->friction >= 0) || !(p->contact_cutoff > 0) ||
                        !std::isfinite(p->contact_modulus) || !std::isfinite(p->friction)))
         return PPM_EINVAL;
@@ -113,6 +133,7 @@ int collect_columns(const ppm_params* p, int n_columns, const ppm_column* cols,
     const int nc = n_columns > 0 ? n_columns : 1;
     if (n_columns > 0 && !cols) return PPM_EINVAL;
     if (p->plane_strain && n_columns > 1) return PPM_EINVAL;      // one periodic slab
+    if (p->coupled && n_columns > 1) return PPM_EINVAL;           // one column
     for (int c = 0; c < nc; c++) {
         int nx = n_columns > 0 ? cols[c].nx : p->nx;
         int ny = n_columns > 0 ? cols[c].ny : p->ny;
@@ -127,7 +148,7 @@ int collect_columns(const ppm_params* p, int n_columns, const ppm_column* cols,
         if (p->plane_strain && !((double)ny > 4.0 * p->horizon_factor)) return PPM_EINVAL;
         ColumnConst cc;
         cc.M = M;
-        cc.Srs = saturation(s, p->vg_alpha, p->vg_n) * s;
+        cc.Srs = (p->coupled ? coupled_saturation(p, 1.0, s) : saturation(s, p->vg_alpha, p->vg_n)) * s;
         cc.Mf = (float)cc.M;
         cc.Srsf = (float)cc.Srs;
         cc.nx = nx; cc.ny = ny; cc.nz = nz; cc.pad = 0;
@@ -160,6 +181,8 @@ void carve(Layout& L, char* base, int64_t N, long long cap, int ncell_cap, int g
     s.eps = L.take<Real>(base, n);
     s.fint = L.take<Real>(base, 3 * n);
     s.tsum = L.take<Real>(base, 3 * n);
+    s.J = L.take<Real>(base, n);
+    s.Jn = L.take<Real>(base, n);
     s.row_ptr = L.take<int32_t>(base, n + 1);
     s.col = L.take<int32_t>(base, (size_t)cap);
     s.rev = L.take<int32_t>(base, (size_t)cap);
@@ -445,6 +468,7 @@ int field_view(ppm_ctx* c, int field, int64_t nbonds, FieldView* v) {
         case PPM_FIELD_PC: base = PICK(pc); count = n; break;
         case PPM_FIELD_EPS_S: base = PICK(eps); count = n; break;
         case PPM_FIELD_FINT: base = PICK(fint); count = 3 * n; break;
+        case PPM_FIELD_J: base = PICK(J); count = n; break;
         case PPM_FIELD_ROW_PTR:
             v->ptr = f64 ? (void*)c->sd.row_ptr : (void*)c->sf.row_ptr;
             v->bytes = sizeof(int32_t) * (n + 1);
@@ -740,8 +764,16 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.inv_dx = 1.0 / p->dx;
     k.delta2 = delta * delta;
     k.hf2f = (float)(p->horizon_factor * p->horizon_factor);
-    k.dt = p->dt > 0 ? p->dt : 0.3 * p->dx / sqrt((p->K + 4.0 * p->mu / 3.0) / p->rho);
-    k.rho = p->rho; k.K = p->K; k.mu = p->mu;
+    // the mixture density at the start (coupled mode: of J = 1)
+    const double rho0 = p->coupled ? coupled_density(p, 1.0, p->suction) : p->rho;
+    k.dt = p->dt > 0 ? p->dt : 0.3 * p->dx / sqrt((p->K + 4.0 * p->mu / 3.0) / rho0);
+    k.rho = rho0; k.K = p->K; k.mu = p->mu;
+    k.coupled = p->coupled;
+    k.phi0 = p->porosity; k.rho_s = p->rho_s; k.rho_w = p->rho_w;
+    k.wr_a1 = p->wr_a1; k.wr_a2 = p->wr_a2; k.wr_n = p->wr_n; k.wr_s = p->suction;
+    k.phi0f = (float)k.phi0; k.rho_sf = (float)k.rho_s; k.rho_wf = (float)k.rho_w;
+    k.wr_a1f = (float)k.wr_a1; k.wr_a2f = (float)k.wr_a2; k.wr_nf = (float)k.wr_n;
+    k.wr_sf = (float)k.wr_s;
     k.lk = p->lambda_t - p->kappa_t;
     k.eta = p->eta;
     k.tol = p->newton_tol;
@@ -966,7 +998,7 @@ int ppm_adjoint_workspace_size(const ppm_ctx* c, int n_steps, int ckpt_every, si
 int ppm_adjoint_forward(ppm_ctx* c, int n_steps, int ckpt_every, void* d_ws, size_t bytes) {
     if (!c || n_steps < 0 || ckpt_every < 1 || !d_ws || ((uintptr_t)d_ws & 255u)) return PPM_EINVAL;
     if (c->started || c->ncols != 1 || c->p.model == 2 || c->p.halt_on_unstable || c->p.contact ||
-        c->p.plane_strain)
+        c->p.plane_strain || c->p.coupled)
         return PPM_ESTATE;
     if (bytes < adj_layout(c, n_steps, ckpt_every).total) return PPM_ENOSPACE;
     Range r("ppm_adjoint_forward");

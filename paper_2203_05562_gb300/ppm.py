@@ -17,8 +17,8 @@ from . import build as _build
 
 FP64, MIXED = 0, 1
 SUBHORIZON, STANDARD, SUBHORIZON_CONJUGATE = 0, 1, 2
-FIELD = dict(u=0, v=1, a=2, sigma=3, pc=4, eps_s=5, fint=6, row_ptr=7, col=8, rev=9, tforce=10)
-_NCOMP = dict(u=3, v=3, a=3, sigma=6, pc=1, eps_s=1, fint=3)
+FIELD = dict(u=0, v=1, a=2, sigma=3, pc=4, eps_s=5, fint=6, row_ptr=7, col=8, rev=9, tforce=10, J=11)
+_NCOMP = dict(u=3, v=3, a=3, sigma=6, pc=1, eps_s=1, fint=3, J=1)
 STATUS_BITS = dict(nonconv=1, singular=2, nonfinite=4, family_full=8, row_full=16, unstable=32,
                    halted=64)
 
@@ -44,6 +44,8 @@ class Params(C.Structure):
         ("halt_on_unstable", C.c_int32), ("contact", C.c_int32),
         ("contact_modulus", C.c_double), ("friction", C.c_double), ("contact_cutoff", C.c_double),
         ("energy_tol", C.c_double), ("plane_strain", C.c_int32),
+        ("coupled", C.c_int32), ("porosity", C.c_double), ("rho_s", C.c_double),
+        ("rho_w", C.c_double), ("wr_a1", C.c_double), ("wr_a2", C.c_double), ("wr_n", C.c_double),
     ]
 
 
