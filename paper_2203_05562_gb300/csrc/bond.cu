@@ -60,8 +60,10 @@ __global__ void k_predictor(DevState<Real> s, StepConst k) {
 // fused bond kernel: one CTA per point, one thread per bond
 // ---------------------------------------------------------------------------
 // TPP threads per point (a tile the autotuner picks among 32, 64, 128, 256); the
-// register budget targets 640 resident threads per SM for FP32
-template <typename Real, int MODEL, int TPP>
+// register budget targets 640 resident threads per SM for FP32.  CPL: the
+// coupled mode (per-point volume ratio, saturation and volumes), a separate
+// instantiation so that the other modes carry none of it
+template <typename Real, int MODEL, int TPP, bool CPL>
 __global__ void __launch_bounds__(TPP, sizeof(Real) == 4 ? (640 / TPP) : (256 / TPP > 0 ? 256 / TPP : 1))
 k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     constexpr bool F64 = sizeof(Real) == 8;
@@ -75,7 +77,9 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     // model 2: per sender bond, its matrix M = varpi sigma K^-1 (9), and (FP32) the
     // terms of its membership test, -2 zeta~ (3) and |zeta~|^2 - hf^2 (1)
     __shared__ alignas(16) Real s_M[MODEL == 2 ? kMaxRow : 1][F64 ? 9 : 16];
-    __shared__ Real s_red[NW][13];
+    // per-point sums (see red below): 12, and the volumetric increment in the coupled mode
+    constexpr int NRED = CPL ? 13 : 12;
+    __shared__ Real s_red[NW][NRED];
     __shared__ unsigned s_cnt[NW][5];
     // FP32 path: a plastic bond's trial stress, K~^-1, varpi and strain
     // measure, parked by its thread while the return runs (model 2 parks in
@@ -100,11 +104,9 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     const ColumnConst cc = s.cols[s.colid[i]];
     Real Srs = F64 ? (Real)cc.Srs : (Real)cc.Srsf;
     // coupled mode: S_r of the point's volume ratio at the start of the step
-    Real Ji = (Real)1;
-    if (k.coupled) {
+    if constexpr (CPL) {
         Real mass_unused;
-        Ji = s.J[i];
-        coupled_point<Real>(k, Ji, Srs, mass_unused);
+        coupled_point<Real>(k, s.J[i], Srs, mass_unused);
     }
 
     // stage the family of i: bond vectors and relative velocities
@@ -139,7 +141,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         y.x = s.vh[j] - vxi;
         y.y = s.vh[n + j] - vyi;
         y.z = s.vh[2 * n + j] - vzi;
-        y.w = k.coupled ? s.J[j] : (Real)0;          // the member's volume ratio
+        y.w = CPL ? s.J[j] : (Real)0;                // the member's volume ratio
         s_z[t] = z;
         s_y[t] = y;
     }
@@ -151,10 +153,9 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     // per-thread partial sums over its bonds (fixed order)
     // red: sum varpi, varpi sigma (6), varpi pc, varpi deps_s, row sum of T
     // (3), and in the coupled mode varpi dt tr L
-    Real red[13];
+    Real red[NRED];
 #pragma unroll
-    for (int e = 0; e < 13; e++) red[e] = (Real)0;
-    const Real dtr = F64 ? (Real)k.dt : (Real)k.dtf;
+    for (int e = 0; e < NRED; e++) red[e] = (Real)0;
     unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
 
     if constexpr (MODEL == 1) {
@@ -194,7 +195,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         BondStress<Real> bs;
         bs.plastic = 0; bs.nonconv = 0; bs.ret64 = 0;
         Real SK[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        Real ev = (Real)0;                                  // dt tr L of the point
+        Real ev = (Real)0;                                  // dt tr L of the point (CPL)
         if (active) {
             const Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
                                 (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
@@ -208,7 +209,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                     for (int c = 0; c < 3; c++)
                         L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
                                         A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
-                ev = (L[0] + L[4] + L[8]) * dtr;
+                if constexpr (CPL) ev = (L[0] + L[4] + L[8]) * (F64 ? (Real)k.dt : (Real)k.dtf);
                 Real st[6], des;
                 if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
                     material_return<Real>(st, pc_i, k, cc.M, cc.Mf, bs);
@@ -241,8 +242,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             if (!active) {
                 n_singular++;
                 Real o[3];
-                store_force_state(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, s_z[t],
-                                  s_y[t].w, Ji, o);
+                store_force_state<CPL>(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, s_z[t],
+                                  s_y[t].w, CPL ? s.J[i] : (Real)1, o);
                 red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
                 continue;
             }
@@ -254,9 +255,9 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
             const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
             Real o[3];
-            store_force_state(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, Ji, o);
+            store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, CPL ? s.J[i] : (Real)1, o);
             red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
-            red[12] += varpi * ev;
+            if constexpr (CPL) red[NRED - 1] += varpi * ev;
             red[0] += varpi;
 #pragma unroll
             for (int c = 0; c < 6; c++) red[1 + c] += varpi * bs.sig[c];
@@ -329,8 +330,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             n_singular++;
             if constexpr (MODEL != 2) {
                 Real o[3];
-                store_force_state(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, zj,
-                                  s_y[t].w, Ji, o);
+                store_force_state<CPL>(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, zj,
+                                  s_y[t].w, CPL ? s.J[i] : (Real)1, o);
                 red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
             } else {
 #pragma unroll
@@ -356,7 +357,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                 for (int c = 0; c < 3; c++)
                     L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
                                     A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
-            if (k.coupled) red[12] += varpi * (L[0] + L[4] + L[8]) * dtr;
+            if constexpr (CPL) red[NRED - 1] += varpi * (L[0] + L[4] + L[8]) * (F64 ? (Real)k.dt : (Real)k.dtf);
             Real st[6], des;
             if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
                 if constexpr (!F64) {
@@ -418,7 +419,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
             const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
             Real o[3];
-            store_force_state(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, Ji, o);
+            store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, CPL ? s.J[i] : (Real)1, o);
             red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
         } else {
 #pragma unroll
@@ -434,7 +435,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         red[8] += varpi * bs.des;
     }
     }
-    block_sum<13, Real>(red, s_red);
+    block_sum<NRED, Real>(red, s_red);
     const Real w = red[0];
 
     if constexpr (MODEL == 2) {
@@ -481,7 +482,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             const Real T1 = (N[3] * zt.x + N[4] * zt.y + N[5] * zt.z) * inv_w;
             const Real T2 = (N[6] * zt.x + N[7] * zt.y + N[8] * zt.z) * inv_w;
             Real o[3];
-            store_force_state(s, k, (size_t)r0 + t, rb, T0, T1, T2, zt, s_y[t].w, Ji, o);
+            store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zt, s_y[t].w, CPL ? s.J[i] : (Real)1, o);
             ts[0] += o[0]; ts[1] += o[1]; ts[2] += o[2];
         }
         block_sum<3, Real>(ts, reinterpret_cast<Real(*)[3]>(&s_red[0][0]));
@@ -499,7 +500,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             s.eps[i] = eps_i + red[8] * iw;
         }
         // coupled mode: J_{n+1} = J_n exp(varpi-mean of dt tr L_b)
-        if (update && k.coupled) s.Jn[i] = w > (Real)0 ? Ji * exp(red[12] / w) : Ji;
+        if constexpr (CPL)
+            if (update) s.Jn[i] = w > (Real)0 ? s.J[i] * exp(red[NRED - 1] / w) : s.J[i];
         s.tsum[i] = red[9];
         s.tsum[n + i] = red[10];
         s.tsum[2 * n + i] = red[11];
@@ -809,9 +811,11 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
     if (k.npoints <= 0) return cudaSuccess;
     const int with_dt = dt != 0.0;
     const int tpp = (k.tile == 32 || k.tile == 64 || k.tile == 256) ? k.tile : 128;
-#define PPM_BOND(M, T) k_bond<Real, M, T><<<k.npoints, T, 0, st>>>(s, k, with_dt, update)
+#define PPM_BOND(M, T) k_bond<Real, M, T, false><<<k.npoints, T, 0, st>>>(s, k, with_dt, update)
+    // the coupled mode runs its own instantiation at 128 threads per point
 #define PPM_BOND_TILES(M)                           \
-    if (tpp == 32) PPM_BOND(M, 32);                 \
+    if (k.coupled) k_bond<Real, M, 128, true><<<k.npoints, 128, 0, st>>>(s, k, with_dt, update); \
+    else if (tpp == 32) PPM_BOND(M, 32);            \
     else if (tpp == 64) PPM_BOND(M, 64);            \
     else if (tpp == 256) PPM_BOND(M, 256);          \
     else PPM_BOND(M, 128);

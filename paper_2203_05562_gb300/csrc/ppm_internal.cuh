@@ -177,14 +177,14 @@ struct DevState {
 // the reverse slot J_i T + C / J_j, so that the gather's factor J dx^2 gives
 // V_i V_j (T_ij - T_ji) (Eq. 49) and the unscaled pair force.  Returns the
 // own-row value for the row sum.
-template <typename Real, typename V4>
+template <bool CPL, typename Real, typename V4>
 __device__ __forceinline__ void store_force_state(const DevState<Real>& s, const StepConst& k,
                                                   size_t b, int rb, Real T0, Real T1, Real T2,
                                                   const V4& z, Real Jj, Real Ji, Real out[3]) {
     Real C0 = (Real)0, C1 = (Real)0, C2 = (Real)0;
     pair_contact(k, z, C0, C1, C2);
     Real o[3], r[3];
-    if (k.coupled) {
+    if constexpr (CPL) {
         o[0] = Jj * T0 + C0 / Ji; o[1] = Jj * T1 + C1 / Ji; o[2] = Jj * T2 + C2 / Ji;
         r[0] = Ji * T0 + C0 / Jj; r[1] = Ji * T1 + C1 / Jj; r[2] = Ji * T2 + C2 / Jj;
     } else {
