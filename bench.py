@@ -585,6 +585,17 @@ def main():
                 "bond_tile": figS["status"]["bond_tile"]}
     del simS
 
+    # ---- the other modes on the same column: the power-conjugate sub-horizon
+    # force state, and the coupled mode (Eq. 15-16, 48-49) on the headline's ----
+    other_modes = {}
+    for tag, mcfg in (("power_conjugate_subhorizon", dict(cfg, model=2)),
+                      ("coupled", dict(cfg, coupled=1))):
+        simO, figO = time_path(mcfg, "mixed", args.standard_steps, args.warmup, barrier)
+        other_modes[tag] = {"value": figO["bond_steps"] / (figO["ms"] * 1e-3), "unit": UNIT,
+                            "steps": args.standard_steps, "ms_per_step": figO["ms"] / args.standard_steps,
+                            "bond_tile": figO["status"]["bond_tile"], "flags": figO["status"]["flags"]}
+        del simO
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     from paper_2203_05562_gb300 import Simulation
@@ -641,7 +652,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
-            "hbm": hbm, "standard_model": standard, "uniaxial_compression": uniaxial,
+            "hbm": hbm, "standard_model": standard, "other_modes": other_modes,
+            "uniaxial_compression": uniaxial,
             "collapse_runout": runout,
             "critical_time_step": critical,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,

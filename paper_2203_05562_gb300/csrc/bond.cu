@@ -811,11 +811,13 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
     if (k.npoints <= 0) return cudaSuccess;
     const int with_dt = dt != 0.0;
     const int tpp = (k.tile == 32 || k.tile == 64 || k.tile == 256) ? k.tile : 128;
-#define PPM_BOND(M, T) k_bond<Real, M, T, false><<<k.npoints, T, 0, st>>>(s, k, with_dt, update)
-    // the coupled mode runs its own instantiation at 128 threads per point
+    // the coupled mode runs its own instantiations
+#define PPM_BOND(M, T) do {                                                                        \
+        if (k.coupled) k_bond<Real, M, T, true><<<k.npoints, T, 0, st>>>(s, k, with_dt, update);  \
+        else k_bond<Real, M, T, false><<<k.npoints, T, 0, st>>>(s, k, with_dt, update);           \
+    } while (0)
 #define PPM_BOND_TILES(M)                           \
-    if (k.coupled) k_bond<Real, M, 128, true><<<k.npoints, 128, 0, st>>>(s, k, with_dt, update); \
-    else if (tpp == 32) PPM_BOND(M, 32);            \
+    if (tpp == 32) PPM_BOND(M, 32);                 \
     else if (tpp == 64) PPM_BOND(M, 64);            \
     else if (tpp == 256) PPM_BOND(M, 256);          \
     else PPM_BOND(M, 128);
