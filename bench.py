@@ -315,7 +315,8 @@ def oracle_sample(steps: int = 4, single_steps: int = 1):
     family is built outside the timing (the oracle's search is brute force),
     one warm-up step, then `steps` steps on all the host's threads and
     `single_steps` on one thread (no family rebuild falls in the sample).
-    Returns (bond-steps/s, threads, description, single-thread bond-steps/s)."""
+    Returns (bond-steps/s, threads, description, single-thread bond-steps/s,
+    (steps taken, u, sigma) of the oracle at the end)."""
     import oracle
     cfg = pi.config(WORKLOAD)
     run = oracle.Run(cfg, pi.initial_velocity(cfg))
@@ -334,13 +335,45 @@ def oracle_sample(steps: int = 4, single_steps: int = 1):
     desc = (f"the full 40x40x80 column ({run.n:,} points, {run.nbonds:,} bonds): {steps} steps on "
             f"{threads} threads and {single_steps} on one, after one warm-up step; family built "
             f"outside the timing, no rebuild in the sample; FP64 oracle")
-    return rate, threads, desc, single
+    return rate, threads, desc, single, (run.steps_done, run.u.copy(), run.sig.copy())
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def precision_report(cfg, tile, u_timed, timed_steps, oracle_state):
+    """The mixed path's error against FP64 on the benchmark's column: after
+    the oracle's own steps, against the FP64 oracle itself (and the FP64 GPU
+    path beside it); and after the timed run, against the FP64 GPU path over
+    the same steps (which matches the oracle to 1e-10 in the parity tests)."""
+    from paper_2203_05562_gb300 import Simulation
+    out = {}
+    if oracle_state is not None:
+        n_or, u_or, sig_or = oracle_state
+        row = {"steps": n_or}
+        for prec in ("mixed", "fp64"):
+            s = Simulation(cfg, precision=prec, bond_tile=tile)
+            s.write("v", pi.initial_velocity(cfg))
+            s.step(n_or)
+            row[prec] = {"u_rel_l2": rel_l2(s.read("u"), u_or), "sigma_rel_l2": rel_l2(s.read("sigma"), sig_or)}
+            del s
+        out["against_fp64_oracle"] = row
+    s = Simulation(cfg, precision="fp64", bond_tile=0)
+    s.write("v", pi.initial_velocity(cfg))
+    s.step(timed_steps)
+    u64 = s.read("u")
+    out["after_timed_run_against_fp64_path"] = {"steps": timed_steps, "u_rel_l2": rel_l2(u_timed, u64)}
+    del s
+    return out
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    rate, threads, desc, _ = oracle_sample(max(1, min(args.steps, 5)), single_steps=0)
+    rate, threads, desc, _, _ = oracle_sample(max(1, min(args.steps, 5)), single_steps=0)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -387,6 +420,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--standard-steps", type=int, default=100)
     ap.add_argument("--no-uniaxial", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the mixed-vs-FP64 error report (about 25 s)")
     ap.add_argument("--runout", action="store_true",
                     help="also run the column-collapse run-out study of Sec. 4.2 (about 4 min)")
     ap.add_argument("--uniaxial-steps", type=int, default=33334,
@@ -439,6 +474,7 @@ def main():
     # ---- dominant kernel: per-phase CUDA-event times on the launching stream,
     # over the same warm-up and steps as the headline, on a fresh column ----
     st = sim.status()
+    u_timed = sim.read("u")                       # the precision report compares it with FP64
     # Eq. 65 (reading R30) on the column at the end of the run, beside the step used
     critical = {"eq65_s": sim.critical_time_step(), "dt_used_s": sim.dt,
                 "note": "micro-modulus over bond length; stable for models 1 and 2 up to at least 2x"}
@@ -623,10 +659,16 @@ def main():
 
     # ---- CPU baseline (oracle, host cores, bounded sample) ----
     cpu = None
+    oracle_state = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, threads, desc, single = oracle_sample()
+        rate, threads, desc, single, oracle_state = oracle_sample()
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
                "single_thread": {"value": single, "unit": UNIT, "cores": 1}}
+
+    # ---- the mixed path's error against FP64, per result ----
+    precision = None
+    if rank == 0 and not args.no_precision:
+        precision = precision_report(cfg, tile, u_timed, args.warmup + args.steps, oracle_state)
 
     # HBM GB/s of both paths: algorithmic bytes per step x steps per second,
     # and the bond kernel's profiled DRAM bytes over its event-timed launch
@@ -652,7 +694,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,
-            "hbm": hbm, "standard_model": standard, "other_modes": other_modes,
+            "hbm": hbm, "precision": precision, "standard_model": standard, "other_modes": other_modes,
             "uniaxial_compression": uniaxial,
             "collapse_runout": runout,
             "critical_time_step": critical,
