@@ -71,3 +71,37 @@ def test_init_rejects_null_and_misaligned_workspace():
     assert L.ppm_init(C.byref(p), 0, None, None, 0, None, C.byref(ctx)) == -1
     assert L.ppm_init(C.byref(p), 0, None, C.c_void_p(0x1001), 1 << 30, None, C.byref(ctx)) == -1
     assert not ctx.value
+
+
+def _ws_cols(cfg, columns):
+    p = P.make_params(cfg)
+    cols = (P.Column * len(columns))()
+    for q, c in enumerate(columns):
+        cols[q].nx, cols[q].ny, cols[q].nz = c["nx"], c["ny"], c["nz"]
+        cols[q].suction, cols[q].M = c["suction"], c["M"]
+    n = C.c_size_t(0)
+    return P.library().ppm_workspace_size(C.byref(p), len(columns), cols, C.byref(n))
+
+
+def test_the_later_parameters_are_validated():
+    # the energy tolerance, the substrate, plane strain (y period > 4 delta) and
+    # the coupled mode (material ranges), without a GPU
+    cfg = pi.small_config(6, 13, 5)
+    assert _ws(cfg)[0] == 0
+    good = [dict(energy_tol=5e-2), dict(contact=1), dict(plane_strain=1), dict(coupled=1),
+            dict(plane_strain=1, contact=1, coupled=1, halt_on_unstable=1)]
+    for kw in good:
+        assert _ws(dict(cfg, **kw))[0] == 0, kw
+    bad = [dict(energy_tol=-1e-2), dict(energy_tol=float("inf")), dict(contact=2),
+           dict(contact=1, contact_cutoff=0.0), dict(contact=1, friction=-0.1),
+           dict(plane_strain=2), dict(plane_strain=1, ny=12), dict(coupled=2),
+           dict(coupled=1, porosity=0.0), dict(coupled=1, porosity=1.0),
+           dict(coupled=1, rho_s=0.0), dict(coupled=1, wr_a1=0.0), dict(coupled=1, wr_n=1.0),
+           dict(coupled=1, wr_a2=-1.0), dict(halt_on_unstable=2)]
+    for kw in bad:
+        assert _ws(dict(cfg, **kw))[0] == -1, kw
+    # plane strain and the coupled mode take one column
+    two = [dict(nx=6, ny=13, nz=5, suction=1e3, M=1.2)] * 2
+    assert _ws_cols(cfg, two) == 0
+    assert _ws_cols(dict(cfg, plane_strain=1), two) == -1
+    assert _ws_cols(dict(cfg, coupled=1), two) == -1
