@@ -138,3 +138,36 @@ def test_a_negative_tolerance_is_rejected():
     cfg = pi.small_config(4, 4, 4, energy_tol=-1e-2)
     with pytest.raises(RuntimeError):
         oracle.Run(cfg, np.zeros((3, pi.num_points(cfg))))
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_the_identity_holds_for_random_combinations_of_the_options(seed):
+    # force state, boundary condition, substrate and friction, plane strain,
+    # suction, skeleton, initial stress, gravity and rebuild period drawn at
+    # random (the coupled mode changes the masses, which the identity assumes
+    # constant, and is left out)
+    rng = np.random.default_rng(1000 + seed)
+    plane = bool(rng.integers(2))
+    bc = int(rng.integers(2))
+    kw = dict(nx=int(rng.integers(4, 7)), ny=13 if plane else int(rng.integers(3, 6)),
+              nz=int(rng.integers(4, 7)), plane_strain=int(plane), model=int(rng.integers(3)),
+              bc=bc, load_rate=0.05 if bc else 0.0,
+              contact=int(rng.integers(2)) if bc == 0 else 0,
+              friction=float(rng.choice([0.0, 0.25, 0.5])),
+              suction=float(rng.choice([0.0, 20e3])), elastic=int(rng.integers(2)),
+              init_stress=int(rng.integers(2)), rebuild_every=int(rng.choice([0, 1, 3])),
+              pc0=float(rng.choice([5e3, 20e3])),
+              gravity=(0.0, 0.0, -9.81) if rng.integers(2) else (0.0, 0.0, 0.0))
+    cfg = pi.small_config(**kw)
+    n = pi.num_points(cfg)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=seed)
+    if plane:
+        v0 = v0.reshape(3, kw["nz"], kw["ny"], kw["nx"])[:, :, :1, :].repeat(kw["ny"], axis=2).reshape(3, n)
+        v0[1] = 0.0
+    run = oracle.Run(cfg, v0)
+    m = cfg["rho"] * cfg["dx"] ** 3
+    a0_sq = m * float((run.a ** 2).sum())
+    for _ in range(25):
+        run.step(1)
+        resid, pred, scale = residual_and_identity(run, cfg, a0_sq)
+        assert abs(resid - pred) <= 1e-10 * max(scale, abs(pred)), (kw, run.steps_done, resid, pred)
