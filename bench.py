@@ -46,12 +46,18 @@ BOND_SOURCES = ("bond.cu", "bond_device.cuh", "ppm_internal.cuh")
 
 
 def bond_source_digest():
-    """sha256 prefix over the sources the bond kernel is compiled from."""
+    """sha256 prefix over the code the bond kernel is compiled from: its
+    sources with comments removed and whitespace collapsed, so that only a
+    change of code (not of a comment) retires a profile."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in BOND_SOURCES:
-        with open(os.path.join(ROOT, "paper_2203_05562_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2203_05562_gb300", "csrc", name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,7 +5,7 @@
  *
  * One explicit step (Alg. 2) is: Newmark predictor and boundary conditions
  * (Eq. 60-61, 64) -> family search in the current configuration when due
- * (Eq. 1, Alg. 1 line 1) -> for every bond the sub-horizon shape tensor and
+ * (Eq. 1, the family of Alg. 1) -> for every bond the sub-horizon shape tensor and
  * velocity gradient (Eq. 22-26, 55, 57), the critical-state visco-plastic
  * update at constant suction (Sec. 2.3, Eq. 40-46, 70-76) and the force
  * state (Eq. 31-32, 51) -> pairwise nodal forces (Eq. 49-50) -> acceleration
@@ -203,7 +203,7 @@ int ppm_workspace_size(const ppm_params* p, int n_columns, const ppm_column* col
 /* Creates a context on the current CUDA device.  d_workspace: device
  * pointer to at least ppm_workspace_size() bytes, 256-byte aligned.
  * cuda_stream: the cudaStream_t to issue all work on (NULL: default
- * stream).  Initial state (Alg. 2 line 1): u = v = a = 0, effective stress
+ * stream).  Initial state (Alg. 2): u = v = a = 0, effective stress
  * per init_stress, pc = -pc0.  The family is not built yet. */
 int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d_workspace,
              size_t bytes, void* cuda_stream, ppm_ctx** out);
@@ -213,9 +213,9 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
  * index.  Asynchronous. */
 int ppm_build_families(ppm_ctx* c);
 
-/* Advances n_steps explicit steps (Alg. 2 lines 5-13).  The first call
+/* Advances n_steps explicit steps (the time loop of Alg. 2).  The first call
  * applies the boundary conditions to the velocities, builds the family if
- * needed and computes the initial acceleration (Alg. 2 lines 2-3).
+ * needed and computes the initial acceleration (Alg. 2).
  * Asynchronous; no host synchronisation. */
 int ppm_step(ppm_ctx* c, int n_steps);
 

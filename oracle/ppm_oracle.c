@@ -17,7 +17,7 @@
  * Readings of passages that are silent, garbled or inconsistent (each is
  * listed with its reason in the design notes):
  *   - a point is not a member of its own family; the bond partner j is a
- *     member of its own sub-horizon (Eq. 1, Eq. 22, Alg. 1 line 4);
+ *     member of its own sub-horizon (Eq. 1, Eq. 22 and the sub-horizon test of Alg. 1);
  *   - membership is inclusive, tested on ((dx*dx + dy*dy) + dz*dz) <= delta^2;
  *   - influence function omega = 1; all point volumes V = dx^3, mass rho V;
  *   - D = sym(L) (Eq. 26), not the mixed form printed in Eq. 58;
@@ -182,7 +182,7 @@ static int params_ok(const ppmo_params* p) {
 }
 
 /* ------------------------------------------------------------------ */
-/* positions and family (Eq. 1; Alg. 1 line 1)                         */
+/* positions and family (Eq. 1; the family of Alg. 1)                   */
 /* ------------------------------------------------------------------ */
 
 void ppmo_reference_positions(const ppmo_params* p, double* X0) {
@@ -489,7 +489,7 @@ typedef struct {
 } subhorizon_sums;
 
 /* Sums over the sub-horizon of bond (i, j): S = {k in H_i : |x_k - x_j| <= delta}
- * (Alg. 1 line 4); the standard model takes S = H_i. */
+ * (the sub-horizon test of Alg. 1); the standard model takes S = H_i. */
 static void subhorizon(const ppmo_params* p, int64_t n, const double* x, const double* vel,
                        const int32_t* row_ptr, const int32_t* col, int64_t i, int64_t j,
                        subhorizon_sums* s) {
@@ -933,7 +933,7 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
         /* masses of the volumes at the start of the step (Eq. 48) */
         point_masses(p, n, s->J, mass);
         /* predictor, Eq. 60-61 with beta1 = 1/2, beta2 = 0; boundary
-         * conditions; displacement, Eq. 64 (Alg. 2 lines 6-8) */
+         * conditions; displacement, Eq. 64 (the predictor of Alg. 2) */
         for (int64_t i = 0; i < n; i++)
             for (int c = 0; c < 3; c++) {
                 double v = s->v[c * n + i] + 0.5 * dt * s->a[c * n + i], vbar;
@@ -943,7 +943,7 @@ int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps) {
             }
         current_positions(p, n, s->u, x);
         if (p->rebuild_every > 0 && (s->step + 1) % p->rebuild_every == 0) rebuild(p, s, x);
-        /* internal force, Alg. 1 (Alg. 2 line 9) */
+        /* internal force, Alg. 1 (called from the time loop of Alg. 2) */
         pass_counts pcnt;
         bond_pass(p, n, x, vh, dt, s->row_ptr, s->col, s->rev, s->cap, s->sig, s->pc,
                   s->eps_s, 1, s->tforce, s->fint, &pcnt, s->J, Jnew);

@@ -147,7 +147,7 @@ int ppmo_internal_force(const ppmo_params* p, int64_t n, const double* x, const 
                         const int32_t* row_ptr, const int32_t* col, const int32_t* rev,
                         double* f);
 
-/* Alg. 2, lines 1-3: initial state.  v0 is 3n (base layer is zeroed). */
+/* Alg. 2, its initial state.  v0 is 3n (base layer is zeroed). */
 int ppmo_init(const ppmo_params* p, const double* v0, ppmo_state* s);
 /* The same with a given initial effective stress sig0 (6n; NULL: the
  * geostatic state of ppmo_initial_stress). */
@@ -158,7 +158,7 @@ int ppmo_init_state(const ppmo_params* p, const double* u0, const double* v0, co
                     ppmo_state* s);
 /* Initial effective stress of the column (6n), O(n). */
 void ppmo_initial_stress(const ppmo_params* p, double* sig);
-/* Alg. 2, lines 5-13: n_steps explicit central-difference steps. */
+/* Alg. 2, its time loop: n_steps explicit central-difference steps. */
 int ppmo_step(const ppmo_params* p, ppmo_state* s, int n_steps);
 
 /* J = sum over the top layer of (u_x^2 + u_y^2) after n_steps (Alg. 2 from

@@ -1,16 +1,16 @@
 // The per-step kernels of the explicit bond loop:
 //   k_predictor  -- Newmark predictor, boundary conditions, displacement
-//                   (Eq. 60-61, 64; Alg. 2 lines 6-8)
+//                   (Eq. 60-61, 64; the predictor of Alg. 2)
 //   k_bond       -- fused per-point kernel: sub-horizon membership and sums
 //                   (Eq. 22-25, 55, 57), FP64 shape-tensor inverse, velocity
 //                   gradient, rate of deformation and spin (Eq. 26),
 //                   Hughes-Winget rotation, linear trial stress (Eq. 41),
 //                   critical-state Perzyna return in FP64 (Eq. 40-46,
 //                   70-76), force state (Eq. 31-32, 51) and the point-state
-//                   reduction; Alg. 1 lines 2-27
+//                   reduction; Alg. 1 up to the force state
 //   k_gather     -- deterministic pairwise nodal force (Eq. 49-50), the
 //                   acceleration and velocity corrector (Eq. 62-63) and the
-//                   energy increments (Eq. 66-68); Alg. 1 lines 29-31
+//                   energy increments (Eq. 66-68); the force assembly of Alg. 1
 //
 // Scaled variables: bond vectors are carried in lattice units
 // zeta~ = zeta / dx, the shape tensor as K~ = sum zeta~ zeta~^T (the paper's
@@ -280,7 +280,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         Real A00 = 0, A01 = 0, A02 = 0, A10 = 0, A11 = 0, A12 = 0, A20 = 0, A21 = 0, A22 = 0;
         int cnt = 0;
         // sub-horizon of bond (i, j): k in H_i with |x_k - x_j| <= delta
-        // (Alg. 1 line 4)
+        // (the sub-horizon test of Alg. 1)
         if constexpr (F64) {
 #pragma unroll 2
             for (int q = 0; q < nb; q++) {
@@ -731,7 +731,7 @@ k_energy_reduce(const double* epart, int nblocks, DevCounters* ctr, int initial,
 }
 
 // ---------------------------------------------------------------------------
-// initial state (Alg. 2 line 1) and velocity boundary conditions
+// initial state (Alg. 2) and velocity boundary conditions
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void k_init_state(DevState<Real> s, StepConst k, int init_stress, double pc0) {

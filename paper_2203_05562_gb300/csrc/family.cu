@@ -1,4 +1,4 @@
-// Family search in the current configuration (Eq. 1; Alg. 1 line 1) on a
+// Family search in the current configuration (Eq. 1; the family of Alg. 1) on a
 // uniform cell grid, producing a bond-major CSR family with ascending rows
 // and the reverse index rev[b] = position of bond (j, i) in row j.
 //

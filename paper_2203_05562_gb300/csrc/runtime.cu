@@ -293,7 +293,7 @@ int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
     return PPM_OK;
 }
 
-// one explicit step (Alg. 2 lines 5-13) issued on stream st; ev (optional)
+// one explicit step (the time loop of Alg. 2) issued on stream st; ev (optional)
 // records phase boundaries: 0 start, 1 after predictor+family, 2 after
 // bond, 3 after gather
 template <typename Real>
