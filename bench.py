@@ -587,7 +587,7 @@ def main():
         torch.cuda.synchronize()
         tc = time.perf_counter()
         # the reverse call leaves the context at the final state: repeat it
-        # warm (the first call's time varies between boxes by about 1.3 s)
+        # warm (the first call's time varies between machines by about 1.3 s)
         g2 = asim.adjoint_reverse(dJ)
         torch.cuda.synchronize()
         td = time.perf_counter()
