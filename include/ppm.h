@@ -255,12 +255,15 @@ int ppm_read_state(ppm_ctx* c, int field, void* dst, size_t bytes, int dst_is_de
 
 /* Overwrites a state field from src (same layout and type as read).
  * Writing PPM_FIELD_U marks the family as stale (rebuilt before the next
- * step).  Family fields are read-only. */
+ * step).  Writing PPM_FIELD_J sets the volume ratio the next step starts
+ * from (coupled = 1; it is 1 after ppm_init).  Family fields are
+ * read-only. */
 int ppm_write_state(ppm_ctx* c, int field, const void* src, size_t bytes, int src_is_device);
 
 /* Critical time step of Eq. 65 over the current family and positions (the
  * family is built first if there is none): the minimum over points with
- * bonds of sqrt(2 rho / sum_j V C / |x_j - x_i|), V = dx^3, with the
+ * bonds of sqrt(2 rho / sum_j V C / |x_j - x_i|), V = dx^3 (rho: the initial
+ * mixture density in the coupled mode), with the
  * bond-based micro-modulus C = 18 K / (pi delta^4).  Eq. 65 as printed
  * multiplies C by |zeta|, which does not give a time; the micro-modulus is
  * divided by the bond length, as in the estimate the paper cites.  *dt is
