@@ -286,8 +286,11 @@ class Simulation:
         raise KeyError(field)
 
     def read(self, field: str, device: bool = False, out=None):
-        """A state field as a numpy array (or a torch tensor on the device);
-        ``out`` may be a preallocated host numpy array (e.g. pinned)."""
+        """A state field as a numpy array (or a torch tensor on the device):
+        u, v, a, fint (3, n); sigma (6, n: xx, yy, zz, yz, xz, xy); pc, eps_s
+        and J (the volume ratio of the coupled mode) (n,); row_ptr, col,
+        rev and tforce for the family.  ``out`` may be a preallocated host
+        numpy array (e.g. pinned)."""
         shape, dt = self._shape(field)
         if out is not None:
             if out.dtype != dt or out.size != int(np.prod(shape)) or not out.flags.c_contiguous:
@@ -309,6 +312,9 @@ class Simulation:
         return out
 
     def write(self, field: str, values):
+        """Overwrites a state field (numpy array or torch tensor, the layout
+        of ``read``).  Writing u makes the next step rebuild the family;
+        family fields are read-only."""
         if hasattr(values, "data_ptr"):
             t = values.to(device=self.device, dtype=self.tdtype).contiguous()
             _check(library().ppm_write_state(self._ctx, FIELD[field], C.c_void_p(t.data_ptr()),
@@ -320,6 +326,9 @@ class Simulation:
                                          a.nbytes, 0), "ppm_write_state")
 
     def status(self) -> dict:
+        """Counters and energies of ``ppm_status`` with the status bits as
+        names in ``flags`` (nonconv, singular, nonfinite, family_full,
+        row_full, unstable, halted)."""
         c = Counters()
         _check(library().ppm_status(self._ctx, C.byref(c)), "ppm_status")
         out = {name: getattr(c, name) for name, _ in Counters._fields_ if "pad" not in name}
