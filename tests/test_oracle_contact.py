@@ -93,3 +93,18 @@ def test_two_points_closer_than_the_cutoff_repel_each_other():
     assert np.allclose(f, want, rtol=0, atol=1e-12 * F)
     f0 = oracle.internal_force(dict(cfg, contact=0), x, sig, rp, col, rev)
     assert np.all(f0 == 0.0)
+
+
+def test_a_plane_strain_slab_stops_after_the_same_distance():
+    # friction with the periodic slab of reading R35: the motion stays in x
+    mu, v = 0.5, 0.1
+    cfg = pi.small_config(6, 13, 1, suction=0.0, elastic=1, init_stress=1, contact=1,
+                          friction=mu, rebuild_every=0, model=1, plane_strain=1)
+    n = pi.num_points(cfg)
+    v0 = np.zeros((3, n)); v0[0] = v
+    run = oracle.Run(cfg, v0)
+    g = -cfg["gravity"][2]
+    dt = oracle.time_step(cfg)
+    run.step(int(1.3 * v / (mu * g) / dt))
+    assert np.all(run.v[0] == 0.0) and np.all(run.v[1] == 0.0) and np.all(run.u[1] == 0.0)
+    assert run.u[0].mean() == pytest.approx(v * v / (2 * mu * g), rel=1e-3)
