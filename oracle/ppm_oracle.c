@@ -29,7 +29,24 @@
  *   - hardening follows Eq. 46 (compaction hardens), not the sign of Eq. 72;
  *     the viscosity is scaled by pc_n^2 unless visc_form = 1;
  *   - S_r from van Genuchten at constant suction (Eq. 15 is garbled);
- *   - Eq. 60 is read with the missing dt: v~ = v + (1-beta1) dt a.
+ *   - Eq. 60 is read with the missing dt: v~ = v + (1-beta1) dt a;
+ *   - the substrate of Eq. 91-93 is the plane z = -delta_c, its normal force
+ *     C_s dx^2 (delta_c - d) / delta_c, its friction Coulomb's on the trial
+ *     tangential velocity and never reversing it; the same repulsion acts
+ *     between soil points closer than delta_c;
+ *   - the tolerance of the Eq. 69 check is a parameter (1e-2 by default);
+ *   - plane strain is a slab periodic in y with v_y held at zero;
+ *   - the coupled mode reads Eq. 15 with the exponent -(n-1)/n, the void
+ *     ratio J / (1 - phi_0) - 1 and a1 per Pa, and updates J from the bonds'
+ *     volumetric rate.
+ *
+ * Parity unpinned (nothing in the paper or the mathematics fixes the
+ * result independently of the reading): the configuration of the bond loop,
+ * omega = 1, the constant point volumes, the point-state mean, the
+ * viscosity scaling, b1 = 0 and b2 = 1 of Eq. 45, the geostatic initial
+ * state, the van Genuchten curve, the ensemble sampler, and which force
+ * state is used.  Everything else is pinned by the CPU tests against closed
+ * forms, brute force, invariants or special cases.
  */
 #include "ppm_oracle.h"
 
