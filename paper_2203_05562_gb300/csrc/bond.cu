@@ -6,11 +6,19 @@
 //                   gradient, rate of deformation and spin (Eq. 26),
 //                   Hughes-Winget rotation, linear trial stress (Eq. 41),
 //                   critical-state Perzyna return in FP64 (Eq. 40-46,
-//                   70-76), force state (Eq. 31-32, 51) and the point-state
-//                   reduction; Alg. 1 up to the force state
+//                   70-76), force state (Eq. 31-32, 51; or the standard and
+//                   power-conjugate forms) with the repulsion between points
+//                   closer than delta_c (Eq. 91), and the point-state
+//                   reduction; Alg. 1 up to the force state.  A separate
+//                   instantiation carries the coupled mode (Eq. 15-16,
+//                   48-49: per-point volume ratio, saturation and volumes).
+//                   Under plane strain the bond vectors take the nearest
+//                   periodic image in y at staging
 //   k_gather     -- deterministic pairwise nodal force (Eq. 49-50), the
+//                   substrate's normal force and friction (Eq. 91-93), the
 //                   acceleration and velocity corrector (Eq. 62-63) and the
 //                   energy increments (Eq. 66-68); the force assembly of Alg. 1
+//   k_energy_reduce -- the Eq. 69 check as a status bit or a hard stop
 //
 // Scaled variables: bond vectors are carried in lattice units
 // zeta~ = zeta / dx, the shape tensor as K~ = sum zeta~ zeta~^T (the paper's
