@@ -7,7 +7,17 @@ explicit Newmark step of the whole path: predictor, family search when due,
 the fused bond kernel, the force gather with the corrector, and the energy
 terms.  The FP64 path is timed on the same column for comparison.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--runout]
+
+Besides the headline, the JSON line carries:
+- the roofline of the bond kernel, the HBM figures and the clocks;
+- the end-to-end rate through the API with host buffers;
+- the mixed path's error against FP64 (precision);
+- the FP64 path, the other force states and the coupled mode;
+- the 64-column ensemble, the 1M-point column and the adjoint;
+- Eq. 65's critical step, the uniaxial compression of Sec. 4.1 (3-D and plane strain);
+- with --runout, the collapse study of Sec. 4.2;
+- the oracle's CPU baseline.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload on the host cores.  Under torchrun each rank runs an
