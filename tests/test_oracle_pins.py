@@ -239,23 +239,6 @@ def test_linear_stress_field_gives_exact_divergence(model):
     assert np.abs(got - div[:, None]).max() < 1e-6 * np.abs(div).max()
 
 
-def test_eq51_force_reproduces_a_fixed_fraction_of_divergence():
-    # Eq. 51 (own-bond force state) is not consistent with div(sigma):
-    # on the interior of a cubic lattice with delta = 3.015 dx it gives a
-    # fixed isotropic fraction of it (recorded in the design notes).
-    cfg = pi.small_config(16, 16, 16, model=0)
-    X = oracle.reference_positions(cfg)
-    rp, col, rev = oracle.family(X, cfg["horizon_factor"] * cfg["dx"])
-    G = np.zeros((6, 3))
-    G[2, 2] = 1e6
-    f = oracle.internal_force(cfg, X, G @ X, rp, col, rev)
-    ijk = np.round(X / cfg["dx"]).astype(int)
-    inner = np.all((ijk >= 7) & (ijk <= 8), axis=0)
-    ratio = f[2, inner] / cfg["dx"] ** 3 / 1e6
-    assert np.allclose(ratio, ratio[0], rtol=1e-9)
-    assert 0.80 < ratio[0] < 0.86
-
-
 @pytest.mark.parametrize("model", [0, 1, 2])
 def test_pairwise_forces_conserve_linear_momentum(model):
     cfg = pi.small_config(6, 5, 7, model=model)
@@ -453,18 +436,90 @@ def _wave_run(model, nx, nz, periods):
     return run, zc, quarter
 
 
-@pytest.mark.slow
-def test_one_dimensional_elastic_wave_period():
-    # quarter-wave column, fixed base and free top: T1 = 4 H / c_p with
-    # c_p = sqrt((K + 4 mu / 3) / rho); nonlocal softening of the lattice
-    # lengthens it by a few per cent
-    run, zc, quarter = _wave_run(1, 12, 20, 0.9)
-    half = zc[1] - zc[0]
-    assert zc[0] == pytest.approx(quarter, rel=0.10)
-    assert half == pytest.approx(2 * quarter, rel=0.08)
+def _linear_standard_modes(cfg):
+    """Small-amplitude dynamics of the standard correspondence model (Sec.
+    2.1, Eq. 5-14) on the undeformed lattice with only z motion (x and y
+    held), the base layer fixed and the other faces free, assembled here
+    from the definitions: K_i = sum_j zeta zeta^T V, L_i = sum_j V (u_j -
+    u_i) (x) K_i^-1 zeta_ij, linear isotropic total stress of sym(L_i), and
+    f_i = V^2 sum_j (sigma_i K_i^-1 + sigma_j K_j^-1) zeta_ij (Eq. 49 with
+    T_(ji) = -sigma_j K_j^-1 zeta_ij).  Returns the free points, the
+    eigenvalues omega^2 of M^-1 Kstiff and the modes (columns)."""
+    X = oracle.reference_positions(cfg)
+    n = X.shape[1]
+    dx = cfg["dx"]
+    V = dx ** 3
+    rp, col, _ = oracle.family(X, cfg["horizon_factor"] * dx)
+    lam, mu = cfg["K"] - 2 * cfg["mu"] / 3, cfg["mu"]
+    Kinv, Zs = [], []
+    G = np.zeros((n, 3, n))       # L_i[z, c] = G[i, c] . u_z
+    for i in range(n):
+        js = col[rp[i]:rp[i + 1]]
+        Z = X[:, js] - X[:, [i]]
+        Kinv.append(np.linalg.inv((Z @ Z.T) * V))
+        Zs.append(Z)
+        W = (Kinv[i] @ Z) * V
+        G[i][:, js] += W
+        G[i][:, i] -= W.sum(axis=1)
+    S = G * np.array([mu, mu, lam + 2 * mu])[None, :, None]   # sigma_zc of each point
+    F = np.zeros((n, n))
+    for i in range(n):
+        js = col[rp[i]:rp[i + 1]]
+        F[i] += V * V * (S[i].T @ (Kinv[i] @ Zs[i])).sum(axis=1)
+        for t, j in enumerate(js):
+            F[i] += V * V * (S[j].T @ (Kinv[j] @ Zs[i][:, t]))
+    free = np.round(X[2] / dx).astype(int) > 0
+    w2, vec = np.linalg.eig(-F[np.ix_(free, free)] / (cfg["rho"] * V))
+    order = np.argsort(w2.real)
+    return X, free, w2.real[order], vec.real[:, order]
+
+
+def _mode_zero_crossings(cfg, X, free, mode_free, periods):
+    mode = np.zeros(X.shape[1])
+    mode[free] = mode_free / np.abs(mode_free).max()
+    v0 = np.zeros_like(X)
+    v0[2] = 1e-3 * mode
+    run = oracle.Run(cfg, v0)
+    hist = [float((run.v[2] * mode).sum())]
+    for _ in range(periods):
+        run.step(1)
+        hist.append(float((run.v[2] * mode).sum()))
+    return [i - 1 + hist[i - 1] / (hist[i - 1] - hist[i]) for i in range(1, len(hist))
+            if hist[i - 1] * hist[i] < 0], run
+
+
+@pytest.mark.parametrize("which", ["quarter_wave", pytest.param("lowest", marks=pytest.mark.slow)])
+def test_elastic_mode_period_matches_the_linearised_lattice(which):
+    # 1-D elastic wave (P7) without the surface guesswork: a column started in
+    # an exact mode of the linearised lattice oscillates as cos(omega t), so
+    # its velocity, projected on the mode, crosses zero at T/4 and 3T/4, with
+    # T from the central-difference scheme, 2 pi / [(2/dt) asin(omega dt/2)]
+    # (Eq. 60-63).  The amplitude (strains ~1e-5) keeps the geometric terms
+    # of the updated-Lagrangian step at that order, hence a 2e-4 tolerance.
+    cfg = pi.small_config(6, 6, 20, suction=1e6, pc0=1e9, gravity=(0, 0, 0), lock_lateral=1,
+                          rebuild_every=0, model=1)
+    X, free, w2, vec = _linear_standard_modes(cfg)
+    H = (cfg["nz"] - 1) * cfg["dx"]
+    if which == "quarter_wave":
+        # the mode closest to the quarter wave sin(pi z / 2H): the closed form
+        # T1 = 4 H / c_p (c_p = sqrt((K + 4 mu/3) / rho)) up to the softening
+        # of the free faces' truncated families (a few per cent)
+        shape = np.sin(np.pi * X[2] / (2 * H))[free]
+        k = int(np.argmax(np.abs(vec.T @ shape) / np.linalg.norm(vec, axis=0)))
+        cp = math.sqrt((cfg["K"] + 4 * cfg["mu"] / 3) / cfg["rho"])
+        assert 2 * math.pi / math.sqrt(w2[k]) == pytest.approx(4 * (H + cfg["dx"] / 2) / cp, rel=0.06)
+    else:
+        # the softest mode of the standard form (motion varying across the section)
+        k = 0
+    omega = math.sqrt(w2[k])
+    dt = oracle.time_step(cfg)
+    T = 2 * math.pi / ((2 / dt) * math.asin(omega * dt / 2))
+    zc, run = _mode_zero_crossings(cfg, X, free, vec[:, k], int(0.8 * T / dt) + 2)
+    assert zc[0] == pytest.approx(0.25 * T / dt, rel=2e-4)
+    assert zc[1] == pytest.approx(0.75 * T / dt, rel=2e-4)
     e = run.energies()
     bal = abs(e["W_int"] + e["W_kin"] - e["W_ext"] - e["W_kin0"])
-    assert bal <= 1e-2 * max(e["W_kin"], abs(e["W_int"]), e["W_kin0"])   # Eq. 69
+    assert bal <= 1e-3 * max(e["W_kin"], abs(e["W_int"]), e["W_kin0"])   # Eq. 69
 
 
 @pytest.mark.parametrize("model", [1, 2])
