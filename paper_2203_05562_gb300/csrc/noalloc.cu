@@ -2,12 +2,13 @@
 // as ppm_build_families, with their scratch in a fixed-size array that is
 // part of the library image instead of the caller's workspace.
 //
-// For callers that cannot allocate device memory: code that runs while a
-// stream is being captured into a CUDA graph (where cudaMalloc is not
-// allowed), real-time loops that must not enter the allocator, and hosts
-// whose device memory is owned by another allocator or memory pool that the
-// library must not touch.
+// For callers that cannot allocate device memory: real-time loops that must
+// not enter the allocator (cudaMalloc can block and synchronise the
+// device), and hosts whose device memory is owned by another allocator or
+// memory pool that the library must not touch.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "ppm_internal.cuh"
 
@@ -39,12 +40,15 @@ static __device__ __align__(256) unsigned char g_family_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 char* g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mutex;   // guards g_scratch_addr against concurrent host threads
 
-// device address of the scratch array for the current device, looked up
-// once per device
-int scratch_address(char** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PPM_ECUDA;
+// Device address of the scratch array on device dev, looked up on the first
+// call for that device (with dev current) and kept for the life of the
+// process.  In host code the array's name is only a host-side stand-in,
+// so the kernels get this address, never the name.
+int scratch_address(int dev, char** out) {
+    if (dev < 0 || dev >= kMaxDevices) return PPM_ECUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_addr[dev]) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_family_scratch) != cudaSuccess || !ptr) return PPM_ECUDA;
@@ -62,10 +66,16 @@ extern "C" int ppm_family_noalloc(int64_t n, const double* d_x, double delta, in
     if (n < 1 || n > kNoAllocMaxPoints) return PPM_EINVAL;
     if (!d_x || !d_row_ptr || !d_col || !d_rev || !(delta > 0.0)) return PPM_EINVAL;
     if (max_family < 1 || max_family > kMaxRow || cap < 0 || cap > 0x7fffffffLL) return PPM_EINVAL;
-    char* base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the stream must belong to the current device, whose copy of the
+    // array the kernels will use
+    int dev = -1, sdev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess)
+        return PPM_ECUDA;
+    if (sdev != dev) return PPM_EINVAL;
+    char* base = nullptr;
+    int rc = scratch_address(dev, &base);
+    if (rc) return rc;
 
     DevState<double> s = {};
     s.xabs = d_x;
