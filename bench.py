@@ -88,15 +88,23 @@ def profiled_traffic():
 
 def algorithmic_bytes(nbonds: int, npoints: int, mixed: bool) -> float:
     """DRAM bytes one step must move (R = 4 B mixed, 8 B FP64).
-    Per bond: col and rev read (8 B), the force state written in bond order
-    and at its reverse slot (2 x 3R), the reverse-slot row read back by the
-    gather (3R).  Per point: the bond kernel reads lat, colid, row_ptr
-    (12 B), u, vh, sigma, pc, eps (14R) and writes sigma, pc, eps, tsum
-    (11R); the gather reads row_ptr, lat (8 B), tsum, vh (6R) and writes
-    fint, a, v (9R); the predictor reads u, v, a (9R) and writes u, vh (6R),
-    plus the FP32 displacement compensation (read and written, 24 B)."""
+    Per bond: col and rev read (8 B), the force state written at its
+    reverse slot (3R), that row read back by the gather (3R).  Per point:
+    the bond kernel reads lat, colid, row_ptr (12 B), u, vh, sigma, pc, eps
+    (14R) and writes sigma, pc, eps, tsum (11R); the gather reads row_ptr,
+    lat (8 B), tsum, vh (6R) and writes fint, a, v (9R); the predictor reads
+    u, v, a (9R) and writes u, vh (6R), plus the FP32 displacement
+    compensation (read and written, 24 B)."""
     R = 4 if mixed else 8
-    return nbonds * (8 + 9 * R) + npoints * (20 + 55 * R + (24 if mixed else 0))
+    return nbonds * (8 + 6 * R) + npoints * (20 + 55 * R + (24 if mixed else 0))
+
+
+def bond_kernel_bytes(nbonds: int, npoints: int) -> float:
+    """DRAM bytes of one launch of the mixed bond kernel: col and rev read,
+    the reverse-slot force state written (20 B per bond); per point lat,
+    colid, row_ptr, u, vh, sigma, pc, eps read and sigma, pc, eps, tsum
+    written (12 + 14 x 4 + 11 x 4 = 112 B)."""
+    return nbonds * 20 + npoints * 112
 
 
 def uniaxial_config(m: int, plane_strain: bool = False) -> dict:
@@ -403,13 +411,24 @@ def run_reference(args, world, rank):
     return 0
 
 
+def align_to_rebuild(warmup: int, rebuild_every: int) -> int:
+    """Untimed steps after `warmup` so that the first timed step is one
+    that rebuilds the family (a step with index s rebuilds when
+    (s + 1) % R == 0): the timed region then holds ceil(K / R) family
+    searches for K steps, the whole periods' share when R divides K."""
+    if rebuild_every <= 1:
+        return 0
+    return (rebuild_every - 1 - warmup) % rebuild_every
+
+
 def time_path(cfg, precision, steps, warmup, stream_sync):
-    """Device-timed steps of one precision; returns a dict of figures."""
+    """Device-timed steps of one precision; returns a dict of figures.  The
+    timed region starts at a family rebuild (align_to_rebuild)."""
     import torch
     from paper_2203_05562_gb300 import Simulation
     sim = Simulation(cfg, precision=precision, bond_tile=0)
     sim.write("v", pi.initial_velocity(cfg))
-    sim.step(warmup)
+    sim.step(warmup + align_to_rebuild(warmup, cfg.get("rebuild_every", 0)))
     torch.cuda.synchronize()
     st0 = sim.status()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -423,7 +442,7 @@ def time_path(cfg, precision, steps, warmup, stream_sync):
     st1 = sim.status()
     return sim, dict(ms=ms, bond_steps=st1["bond_steps"] - st0["bond_steps"],
                      pairs=st1["pairs"] - st0["pairs"], launches=st1["launches"] - st0["launches"],
-                     nbonds=st1["nbonds"], status=st1)
+                     rebuilds=st1["rebuilds"] - st0["rebuilds"], nbonds=st1["nbonds"], status=st1)
 
 
 def main():
@@ -499,7 +518,7 @@ def main():
     tile = fig["status"]["bond_tile"]          # the autotuner's choice, reused below
     tsim = Simulation(cfg, precision="mixed", bond_tile=tile)
     tsim.write("v", pi.initial_velocity(cfg))
-    tsim.step(args.warmup)
+    tsim.step(args.warmup + align_to_rebuild(args.warmup, cfg["rebuild_every"]))
     t0 = tsim.status()
     phase = tsim.step_timed(args.steps)
     t1 = tsim.status()
@@ -513,13 +532,18 @@ def main():
     flops = FLOPS_TEST * fam_sq + FLOPS_PAIR * pairs_per_step
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * LANES * 2 * sm_max * 1e6 / 1e12
+    nominal_tflops = SMS * LANES * 2 * sm_max * 1e6 / 1e12
+    from paper_2203_05562_gb300.ppm import measure_fp32_peak
+    peak_tflops = measure_fp32_peak()             # FMA chains on this GPU, now
     achieved = flops / (bond_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": profiled_traffic(),
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
-                "kernel": "k_bond<float,0> (fused sub-horizon / constitutive / force state)",
-                "peak_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
+                "kernel": f"k_bond<float,0,{tile}> (fused sub-horizon / constitutive / force state)",
+                "peak_kind": "measured: FP32 FMA chains on every SM (ppm_measure_fp32_peak), this run",
+                "peak_nominal": nominal_tflops, "frac_of_nominal": achieved / nominal_tflops,
+                "nominal_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
+                "flops_per_launch": flops,
                 "bond_kernel_ms": bond_ms, "gather_ms": phase[2] / nph,
                 "predictor_family_ms": phase[0] / nph}
 
@@ -655,7 +679,7 @@ def main():
     host_u = torch.empty((3, n), dtype=torch.float32).pin_memory()
     esim = Simulation(cfg, precision="mixed", bond_tile=tile)
     esim.write("v", host_v0.numpy())
-    esim.step(args.warmup)
+    esim.step(args.warmup + align_to_rebuild(args.warmup, cfg["rebuild_every"]))
     torch.cuda.synchronize()
     barrier()
     s0 = esim.status()["bond_steps"]
@@ -694,6 +718,7 @@ def main():
     traffic = roofline["traffic"]
     hbm = {"unit": "GB/s", "peak": hbm_peak, "peak_kind": peak_kind,
            "mixed": {"bytes_per_step": b_mixed, "gbs": b_mixed * (value / world / nb) / 1e9,
+                     "bond_kernel_algorithmic_gbs": bond_kernel_bytes(nb, n) / (bond_ms * 1e-3) / 1e9,
                      "bond_kernel_dram_gbs": traffic / (bond_ms * 1e-3) / 1e9 if traffic else None},
            "fp64": {"bytes_per_step": b_fp64, "gbs": b_fp64 * (fp64_rate / nb) / 1e9},
            "note": "the path is FP32-issue-bound (roofline above); these are far below the HBM roof"}
@@ -707,6 +732,9 @@ def main():
             "config": {"workload": WORKLOAD, "points": n, "bonds": nb, "dx": cfg["dx"],
                        "horizon": "3.015 dx", "rebuild_every": cfg["rebuild_every"],
                        "l2": "inputs larger than L2 (force states + family > 129 MB)",
+                       "timed_region": "starts at a family rebuild: ceil(steps / rebuild_every) "
+                                       "family searches inside",
+                       "rebuilds_timed": fig["rebuilds"],
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,

@@ -281,10 +281,11 @@ int ppm_info(const ppm_ctx* c, double* dt, int64_t* npoints);
 
 /* Family search (as ppm_build_families) of n points with explicit FP64
  * positions, allocating nothing.  The paper has no counterpart of this
- * call; it exists for callers that cannot allocate device memory -- code
- * running while a stream is captured into a CUDA graph, real-time loops
- * that must not enter the allocator, hosts whose device memory belongs to
- * another allocator.
+ * call; it exists for callers that cannot allocate device memory --
+ * real-time loops that must not enter the allocator (cudaMalloc can block
+ * and synchronise the device), hosts whose device memory belongs to
+ * another allocator or pool.  The caller passes the inputs and outputs;
+ * the scratch lives in the library itself.
  *
  *   d_x        device, 3n doubles, component-major (x[c*n + i])
  *   delta      horizon; j is in the family of i iff j != i and
@@ -293,18 +294,28 @@ int ppm_info(const ppm_ctx* c, double* dt, int64_t* npoints);
  *              gets an empty row and the call returns PPM_ENOSPACE
  *   d_row_ptr  device, n+1 int32 (written); d_col, d_rev: device, cap int32
  *              each (written: rows ascending, rev[b] = index of (j,i))
+ *   cuda_stream a stream of the current device (NULL: the default stream)
  *   nbonds     host, may be NULL: bonds found
  * Returns PPM_EINVAL for n < 1 or n > 262,144 points (the size of the
- * built-in scratch) or bad arguments, PPM_ENOSPACE if the bonds exceed cap
- * (row_ptr is then all zero).  The scratch is one fixed array of about
- * 9.5 MB that every GPU loading the library holds until exit; its device
- * address is looked up on the first call on each device (make that first
- * call before any stream capture).  All calls share the array: calls that
- * overlap on the GPU race.  The call synchronises the stream to return its
- * status. */
+ * built-in scratch), a stream of another device, or bad arguments;
+ * PPM_ENOSPACE if the bonds exceed cap (row_ptr is then all zero, *nbonds
+ * 0).  The scratch is one fixed array of about 9.5 MB in the library's
+ * device image, which every GPU that loads the library holds until exit.
+ * Its device address is looked up on the first call on each device, with
+ * that device current, and kept (the lookup is guarded for concurrent host
+ * threads).  All calls share the array and the array keeps the last call's
+ * contents (the call clears what must start at zero): calls that overlap
+ * on the GPU race.  The call synchronises the stream to return its status. */
 int ppm_family_noalloc(int64_t n, const double* d_x, double delta, int max_family,
                        int32_t* d_row_ptr, int32_t* d_col, int32_t* d_rev, int64_t cap,
                        void* cuda_stream, int64_t* nbonds);
+
+/* Measured FP32 fused multiply-add rate of the current device in TFLOP/s
+ * (*tflops): independent FMA chains on every SM, the best of three timed
+ * launches on cuda_stream (which it synchronises).  Measurement plumbing
+ * with no counterpart in the paper: the benchmark divides the bond
+ * kernel's algorithmic FLOP rate by it.  Allocates nothing. */
+int ppm_measure_fp32_peak(void* cuda_stream, double* tflops);
 
 const char* ppm_error_string(int code);
 

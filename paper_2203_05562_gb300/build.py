@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libppm.so")
-SOURCES = ["family.cu", "bond.cu", "runtime.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["family.cu", "bond.cu", "runtime.cu", "noalloc.cu", "adjoint.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

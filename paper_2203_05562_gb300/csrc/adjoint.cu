@@ -332,7 +332,7 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
             for (int q = 0; q < nb; q++) {
                 const R4<Real> zk = s_z[q];
                 const R4<Real> yk = s_y[q];
-                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + zk.w));
+                const float tst = member_test_lhs(zk.x, zk.y, zk.z, zk.w, mjx, mjy, mjz);
                 masked_accumulate(tst, thj, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
             }
             K00 = Kf[0]; K11 = Kf[1]; K22 = Kf[2]; K12 = Kf[3]; K02 = Kf[4]; K01 = Kf[5];
@@ -509,7 +509,7 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
                     const float4 g1 = *reinterpret_cast<const float4*>(sq + 8);
                     const float4 g2 = *reinterpret_cast<const float4*>(sq + 12);
                     const float4 g3 = *reinterpret_cast<const float4*>(sq + 16);
-                    const float tst = zt.x * m.x + (zt.y * m.y + (zt.z * m.z + zt.w));
+                    const float tst = member_test_lhs(zt.x, zt.y, zt.z, zt.w, m.x, m.y, m.z);
                     masked_add15(tst, m.w, g0, g1, g2, g3, Gf, Af);
                 }
 #pragma unroll

@@ -65,6 +65,181 @@ __global__ void k_predictor(DevState<Real> s, StepConst k) {
 }
 
 // ---------------------------------------------------------------------------
+// The update of one bond (i, j) after its sub-horizon sums (the part of
+// Alg. 1 after the sub-horizon loop): FP64 inverse of the shape tensor
+// (Eq. 23, 25), velocity gradient (Eq. 25, 57), constitutive update (Sec.
+// 2.3), force state (Eq. 31-32, 51; model 2: the sender matrix in sM) and
+// the bond's share of the point-state reduction (red).  b: the bond's row
+// slot, rb: its reverse slot, zj: its vector (lattice units, |.|^2), Jj:
+// the member's volume ratio (coupled mode), K (xx yy zz yz xz xy), A (row-
+// major) and cntr = |S_b| its sums, (mjx, mjy, mjz, thj): the terms of its
+// membership test, park: a 16-entry row the thread owns (FP32 path).
+template <typename Real, int MODEL, bool CPL, int NRED>
+__device__ __forceinline__ void bond_epilogue(
+    const DevState<Real>& s, const StepConst& k, int i, int r0, int t, int rb, const R4<Real>& zj,
+    Real Jj, Real K00, Real K11, Real K22, Real K12, Real K02, Real K01, Real A00, Real A01,
+    Real A02, Real A10, Real A11, Real A12, Real A20, Real A21, Real A22, Real cntr, int cnt,
+    Real mjx, Real mjy, Real mjz, Real thj, const Real (&sig_i)[6], Real pc_i,
+    const ColumnConst& cc, Real Srs, Real inv_nb, Real inv_dx, int with_dt, Real* park, Real* sM,
+    Real (&red)[NRED], unsigned& n_pairs, unsigned& n_plastic, unsigned& n_nonconv,
+    unsigned& n_singular, unsigned& n_ret64) {
+    constexpr bool F64 = sizeof(Real) == 8;
+    n_pairs += (unsigned)cnt;
+    // shape-tensor inverse with FP64 cofactors and determinant (Eq. 23, 25)
+    Real Kid[6];
+    bool active = cntr >= (Real)3;
+    if constexpr (F64) {
+        const double Kd[6] = {K00, K11, K22, K12, K02, K01};
+        active = active && inverse_sym_fp64(Kd, Kid);
+    } else {
+        active = active && inverse_sym_mixed(K00, K11, K22, K12, K02, K01, Kid);
+    }
+    if (!active) {
+        n_singular++;
+        if constexpr (MODEL != 2) {
+            Real o[3];
+            store_force_state<CPL>(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, zj,
+                              Jj, CPL ? s.J[i] : (Real)1, o);
+            red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 9; e++) sM[e] = (Real)0;
+            if constexpr (!F64) {
+                sM[9] = mjx; sM[10] = mjy; sM[11] = mjz; sM[12] = thj;
+            }
+        }
+        return;
+    }
+    Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
+                  (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
+                  (Real)Kid[4], (Real)Kid[3], (Real)Kid[2]};
+    Real varpi = cntr * inv_nb;                         // Eq. 55
+    BondStress<Real> bs;
+    if (with_dt) {
+        // velocity gradient L = A~ K~^-1 / dx (Eq. 25, 57)
+        const Real A[9] = {A00, A01, A02, A10, A11, A12, A20, A21, A22};
+        Real L[9];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
+                                A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
+        if constexpr (CPL) red[NRED - 1] += varpi * (L[0] + L[4] + L[8]) * (F64 ? (Real)k.dt : (Real)k.dtf);
+        Real st[6], des;
+        if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
+            if constexpr (!F64) {
+                // the bond waits in shared memory while the return runs, so
+                // that none of it is held in registers across the return's
+                // calls (the compiler barriers keep it from being forwarded)
+                Real* pk = (MODEL == 2) ? sM : park;
+#pragma unroll
+                for (int c = 0; c < 6; c++) pk[c] = st[c];
+#pragma unroll
+                for (int c = 0; c < 6; c++) pk[6 + c] = Kid[c];
+                pk[12] = varpi;
+                pk[13] = des;
+                asm volatile("" ::: "memory");
+                Real stp[6];
+#pragma unroll
+                for (int c = 0; c < 6; c++) stp[c] = pk[c];
+                material_return<Real>(stp, pc_i, k, cc.M, cc.Mf, bs);
+                asm volatile("" ::: "memory");
+                const Real* q = (MODEL == 2) ? sM : park;
+                Ki[0] = q[6]; Ki[1] = q[11]; Ki[2] = q[10];
+                Ki[3] = q[11]; Ki[4] = q[7]; Ki[5] = q[9];
+                Ki[6] = q[10]; Ki[7] = q[9]; Ki[8] = q[8];
+                varpi = q[12];
+                bs.des = q[13];
+            } else {
+                material_return<Real>(st, pc_i, k, cc.M, cc.Mf, bs);
+                bs.des = des;
+            }
+            n_plastic++;
+            n_nonconv += bs.nonconv;
+            n_ret64 += bs.ret64;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; c++) bs.sig[c] = st[c];
+            bs.pc = pc_i;
+            bs.des = des;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; c++) bs.sig[c] = sig_i[c];
+        bs.pc = pc_i;
+        bs.des = (Real)0;
+    }
+    // total stress sigma_bar - S_r p_w 1 = sigma_bar + S_r s 1 (Eq. 32)
+    const Real S[9] = {bs.sig[0] + Srs, bs.sig[5], bs.sig[4],
+                       bs.sig[5], bs.sig[1] + Srs, bs.sig[3],
+                       bs.sig[4], bs.sig[3], bs.sig[2] + Srs};
+    Real SK[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            SK[r * 3 + c] = varpi * (S[r * 3 + 0] * Ki[0 * 3 + c] + S[r * 3 + 1] * Ki[1 * 3 + c] +
+                                     S[r * 3 + 2] * Ki[2 * 3 + c]);
+    if constexpr (MODEL != 2) {
+        // force state on the bond itself (Eq. 31-32, 51)
+        const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+        const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+        const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+        Real o[3];
+        store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, Jj, CPL ? s.J[i] : (Real)1, o);
+        red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 9; e++) sM[e] = SK[e];
+        if constexpr (!F64) {
+            sM[9] = mjx; sM[10] = mjy; sM[11] = mjz; sM[12] = thj;
+        }
+    }
+    red[0] += varpi;
+#pragma unroll
+    for (int c = 0; c < 6; c++) red[1 + c] += varpi * bs.sig[c];
+    red[7] += varpi * bs.pc;
+    red[8] += varpi * bs.des;
+}
+
+// The point's new state (the varpi-weighted means of its bonds, reading R8),
+// its row sum of force states and the step's counters, written by thread 0
+// (red and cnts are block sums: every thread holds them).
+template <typename Real, bool CPL, int NRED>
+__device__ __forceinline__ void point_commit(const DevState<Real>& s, int i, size_t n,
+                                             const Real (&red)[NRED], Real w, Real eps_i,
+                                             const unsigned (&cnts)[5], int update) {
+    if (threadIdx.x == 0) {
+        if (update && w > (Real)0) {
+            const Real iw = (Real)1 / w;
+#pragma unroll
+            for (int c = 0; c < 6; c++) s.sig[c * n + i] = red[1 + c] * iw;
+            s.pc[i] = red[7] * iw;
+            s.eps[i] = eps_i + red[8] * iw;
+        }
+        // coupled mode: J_{n+1} = J_n exp(varpi-mean of dt tr L_b)
+        if constexpr (CPL)
+            if (update) s.Jn[i] = w > (Real)0 ? s.J[i] * exp(red[NRED - 1] / w) : s.J[i];
+        s.tsum[i] = red[9];
+        s.tsum[n + i] = red[10];
+        s.tsum[2 * n + i] = red[11];
+        // only committed passes count (not the initial pass or the autotuner's)
+        if (update && cnts[3]) atomicAdd(&s.ctr->pairs, (unsigned long long)cnts[3]);
+        if (update && cnts[0]) atomicAdd(&s.ctr->plastic, (unsigned long long)cnts[0]);
+        if (update && cnts[4]) atomicAdd(&s.ctr->ret64, (unsigned long long)cnts[4]);
+        if (update && cnts[1]) {
+            atomicAdd(&s.ctr->nonconv, (unsigned long long)cnts[1]);
+            atomicOr(&s.ctr->status, PPM_STATUS_NONCONV);
+        }
+        if (update && cnts[2]) {
+            atomicAdd(&s.ctr->singular, (unsigned long long)cnts[2]);
+            atomicOr(&s.ctr->status, PPM_STATUS_SINGULAR);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // fused bond kernel: one CTA per point, one thread per bond
 // ---------------------------------------------------------------------------
 // TPP threads per point (a tile the autotuner picks among 32, 64, 128, 256); the
@@ -72,13 +247,13 @@ __global__ void k_predictor(DevState<Real> s, StepConst k) {
 // coupled mode (per-point volume ratio, saturation and volumes), a separate
 // instantiation so that the other modes carry none of it
 template <typename Real, int MODEL, int TPP, bool CPL>
-__global__ void __launch_bounds__(TPP, sizeof(Real) == 4 ? (640 / TPP) : (256 / TPP > 0 ? 256 / TPP : 1))
-k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
+__device__ __forceinline__ void bond_point(const DevState<Real>& s, const StepConst& k, const int i,
+                                           int with_dt, int update) {
     constexpr bool F64 = sizeof(Real) == 8;
     constexpr int NW = TPP / 32;
-    // the run has stopped (set by the energy check between steps, so every
-    // thread of the block reads the same value)
-    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
+    // a block that takes several points in turn: the previous one is done
+    // with the shared arrays
+    __syncthreads();
     __shared__ R4<Real> s_z[kMaxRow];                         // zeta~_k, lattice units
     __shared__ R4<Real> s_y[kMaxRow];                         // Ydot_k, m/s
     __shared__ double s_p[F64 ? 3 : 1][F64 ? kMaxRow : 1];    // FP64: absolute x_k
@@ -94,7 +269,6 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
     // the bond's own row of s_M, which is written only after the return)
     __shared__ alignas(16) Real s_park[(F64 || MODEL == 2) ? 1 : TPP][16];
 
-    const int i = blockIdx.x;
     const size_t n = (size_t)k.npoints;
     const int r0 = s.row_ptr[i];
     int nb = s.row_ptr[i + 1] - r0;
@@ -287,6 +461,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
         Real K00 = 0, K11 = 0, K22 = 0, K12 = 0, K02 = 0, K01 = 0;
         Real A00 = 0, A01 = 0, A02 = 0, A10 = 0, A11 = 0, A12 = 0, A20 = 0, A21 = 0, A22 = 0;
         int cnt = 0;
+        Real cntr = (Real)0;
         // sub-horizon of bond (i, j): k in H_i with |x_k - x_j| <= delta
         // (the sub-horizon test of Alg. 1)
         if constexpr (F64) {
@@ -308,6 +483,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                     cnt++;
                 }
             }
+            cntr = (Real)cnt;
         } else {
             // FP32 sub-horizon sums, predicated (no branches, no mask multiplies)
             float Kf[6] = {0, 0, 0, 0, 0, 0}, Af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -316,131 +492,20 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
             for (int q = 0; q < nb; q++) {
                 const R4<Real> zk = s_z[q];
                 const R4<Real> yk = s_y[q];
-                const float tst = zk.x * mjx + (zk.y * mjy + (zk.z * mjz + zk.w));
+                const float tst = member_test_lhs(zk.x, zk.y, zk.z, zk.w, mjx, mjy, mjz);
                 masked_accumulate(tst, thj, zk.x, zk.y, zk.z, yk.x, yk.y, yk.z, Kf, Af, cntf);
             }
             K00 = Kf[0]; K11 = Kf[1]; K22 = Kf[2]; K12 = Kf[3]; K02 = Kf[4]; K01 = Kf[5];
             A00 = Af[0]; A01 = Af[1]; A02 = Af[2]; A10 = Af[3]; A11 = Af[4]; A12 = Af[5];
             A20 = Af[6]; A21 = Af[7]; A22 = Af[8];
-            cnt = (int)cntf;
+            cntr = cntf;
+            cnt = small_count(cntf);
         }
-        n_pairs += cnt;
-        // shape-tensor inverse with FP64 cofactors and determinant (Eq. 23, 25)
-        Real Kid[6];
-        bool active = cnt >= 3;
-        if constexpr (F64) {
-            const double Kd[6] = {K00, K11, K22, K12, K02, K01};
-            active = active && inverse_sym_fp64(Kd, Kid);
-        } else {
-            active = active && inverse_sym_mixed(K00, K11, K22, K12, K02, K01, Kid);
-        }
-        if (!active) {
-            n_singular++;
-            if constexpr (MODEL != 2) {
-                Real o[3];
-                store_force_state<CPL>(s, k, (size_t)r0 + t, rb, (Real)0, (Real)0, (Real)0, zj,
-                                  s_y[t].w, CPL ? s.J[i] : (Real)1, o);
-                red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
-            } else {
-#pragma unroll
-                for (int e = 0; e < 9; e++) s_M[t][e] = (Real)0;
-                if constexpr (!F64) {
-                    s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = thj;
-                }
-            }
-            continue;
-        }
-        Real Ki[9] = {(Real)Kid[0], (Real)Kid[5], (Real)Kid[4],
-                      (Real)Kid[5], (Real)Kid[1], (Real)Kid[3],
-                      (Real)Kid[4], (Real)Kid[3], (Real)Kid[2]};
-        Real varpi = (Real)cnt * inv_nb;                    // Eq. 55
-        BondStress<Real> bs;
-        if (with_dt) {
-            // velocity gradient L = A~ K~^-1 / dx (Eq. 25, 57)
-            const Real A[9] = {A00, A01, A02, A10, A11, A12, A20, A21, A22};
-            Real L[9];
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    L[r * 3 + c] = (A[r * 3 + 0] * Ki[0 * 3 + c] + A[r * 3 + 1] * Ki[1 * 3 + c] +
-                                    A[r * 3 + 2] * Ki[2 * 3 + c]) * inv_dx;
-            if constexpr (CPL) red[NRED - 1] += varpi * (L[0] + L[4] + L[8]) * (F64 ? (Real)k.dt : (Real)k.dtf);
-            Real st[6], des;
-            if (material_trial<Real>(L, sig_i, pc_i, k, cc.M, cc.Mf, st, des)) {
-                if constexpr (!F64) {
-                    // the bond waits in shared memory while the return runs, so
-                    // that none of it is held in registers across the return's
-                    // calls (the compiler barriers keep it from being forwarded)
-                    Real* pk = (MODEL == 2) ? s_M[t] : s_park[threadIdx.x];
-#pragma unroll
-                    for (int c = 0; c < 6; c++) pk[c] = st[c];
-#pragma unroll
-                    for (int c = 0; c < 6; c++) pk[6 + c] = Kid[c];
-                    pk[12] = varpi;
-                    pk[13] = des;
-                    asm volatile("" ::: "memory");
-                    Real stp[6];
-#pragma unroll
-                    for (int c = 0; c < 6; c++) stp[c] = pk[c];
-                    material_return<Real>(stp, pc_i, k, cc.M, cc.Mf, bs);
-                    asm volatile("" ::: "memory");
-                    const Real* q = (MODEL == 2) ? s_M[t] : s_park[threadIdx.x];
-                    Ki[0] = q[6]; Ki[1] = q[11]; Ki[2] = q[10];
-                    Ki[3] = q[11]; Ki[4] = q[7]; Ki[5] = q[9];
-                    Ki[6] = q[10]; Ki[7] = q[9]; Ki[8] = q[8];
-                    varpi = q[12];
-                    bs.des = q[13];
-                } else {
-                    material_return<Real>(st, pc_i, k, cc.M, cc.Mf, bs);
-                    bs.des = des;
-                }
-                n_plastic++;
-                n_nonconv += bs.nonconv;
-                n_ret64 += bs.ret64;
-            } else {
-#pragma unroll
-                for (int c = 0; c < 6; c++) bs.sig[c] = st[c];
-                bs.pc = pc_i;
-                bs.des = des;
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 6; c++) bs.sig[c] = sig_i[c];
-            bs.pc = pc_i;
-            bs.des = (Real)0;
-        }
-        // total stress sigma_bar - S_r p_w 1 = sigma_bar + S_r s 1 (Eq. 32)
-        const Real S[9] = {bs.sig[0] + Srs, bs.sig[5], bs.sig[4],
-                           bs.sig[5], bs.sig[1] + Srs, bs.sig[3],
-                           bs.sig[4], bs.sig[3], bs.sig[2] + Srs};
-        Real SK[9];
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                SK[r * 3 + c] = varpi * (S[r * 3 + 0] * Ki[0 * 3 + c] + S[r * 3 + 1] * Ki[1 * 3 + c] +
-                                         S[r * 3 + 2] * Ki[2 * 3 + c]);
-        if constexpr (MODEL != 2) {
-            // force state on the bond itself (Eq. 31-32, 51)
-            const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
-            const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
-            const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
-            Real o[3];
-            store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, s_y[t].w, CPL ? s.J[i] : (Real)1, o);
-            red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
-        } else {
-#pragma unroll
-            for (int e = 0; e < 9; e++) s_M[t][e] = SK[e];
-            if constexpr (!F64) {
-                s_M[t][9] = mjx; s_M[t][10] = mjy; s_M[t][11] = mjz; s_M[t][12] = thj;
-            }
-        }
-        red[0] += varpi;
-#pragma unroll
-        for (int c = 0; c < 6; c++) red[1 + c] += varpi * bs.sig[c];
-        red[7] += varpi * bs.pc;
-        red[8] += varpi * bs.des;
+        bond_epilogue<Real, MODEL, CPL, NRED>(
+            s, k, i, r0, t, rb, zj, s_y[t].w, K00, K11, K22, K12, K02, K01, A00, A01, A02, A10, A11,
+            A12, A20, A21, A22, cntr, cnt, mjx, mjy, mjz, thj, sig_i, pc_i, cc, Srs, inv_nb, inv_dx,
+            with_dt, s_park[(F64 || MODEL == 2) ? 0 : threadIdx.x], s_M[MODEL == 2 ? t : 0], red,
+            n_pairs, n_plastic, n_nonconv, n_singular, n_ret64);
     }
     }
     block_sum<NRED, Real>(red, s_red);
@@ -480,7 +545,7 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
                     const float4 m1 = *reinterpret_cast<const float4*>(&s_M[q][4]);
                     const float4 m2 = *reinterpret_cast<const float4*>(&s_M[q][8]);
                     const float4 m3 = *reinterpret_cast<const float4*>(&s_M[q][12]);
-                    const float tst = zt.x * m2.y + (zt.y * m2.z + (zt.z * m2.w + zt.w));
+                    const float tst = member_test_lhs(zt.x, zt.y, zt.z, zt.w, m2.y, m2.z, m2.w);
                     masked_add9(tst, m3.x, m0, m1, m2.x, Nf);
                 }
 #pragma unroll
@@ -499,53 +564,162 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 
     unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
     block_sum<5, unsigned>(cnts, s_cnt);
-    if (threadIdx.x == 0) {
-        if (update && w > (Real)0) {
-            const Real iw = (Real)1 / w;
-#pragma unroll
-            for (int c = 0; c < 6; c++) s.sig[c * n + i] = red[1 + c] * iw;
-            s.pc[i] = red[7] * iw;
-            s.eps[i] = eps_i + red[8] * iw;
-        }
-        // coupled mode: J_{n+1} = J_n exp(varpi-mean of dt tr L_b)
-        if constexpr (CPL)
-            if (update) s.Jn[i] = w > (Real)0 ? s.J[i] * exp(red[NRED - 1] / w) : s.J[i];
-        s.tsum[i] = red[9];
-        s.tsum[n + i] = red[10];
-        s.tsum[2 * n + i] = red[11];
-        // only committed passes count (not the initial pass or the autotuner's)
-        if (update && cnts[3]) atomicAdd(&s.ctr->pairs, (unsigned long long)cnts[3]);
-        if (update && cnts[0]) atomicAdd(&s.ctr->plastic, (unsigned long long)cnts[0]);
-        if (update && cnts[4]) atomicAdd(&s.ctr->ret64, (unsigned long long)cnts[4]);
-        if (update && cnts[1]) {
-            atomicAdd(&s.ctr->nonconv, (unsigned long long)cnts[1]);
-            atomicOr(&s.ctr->status, PPM_STATUS_NONCONV);
-        }
-        if (update && cnts[2]) {
-            atomicAdd(&s.ctr->singular, (unsigned long long)cnts[2]);
-            atomicOr(&s.ctr->status, PPM_STATUS_SINGULAR);
+    point_commit<Real, CPL, NRED>(s, i, n, red, w, eps_i, cnts, update);
+}
+
+template <typename Real, int MODEL, int TPP, bool CPL>
+__global__ void __launch_bounds__(TPP, sizeof(Real) == 4 ? (640 / TPP) : (256 / TPP > 0 ? 256 / TPP : 1))
+k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
+    // the run has stopped (set by the energy check between steps, so every
+    // thread of the block reads the same value)
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
+    bond_point<Real, MODEL, TPP, CPL>(s, k, blockIdx.x, with_dt, update);
+}
+
+// The points with more than kTcRows bonds, for the tensor-core kernel below
+// (which leaves them): one warp per block scans 32 points at a time and
+// runs the scalar sums on each that has more.  Only the mixed path with the
+// force state of Eq. 51 runs this pair of kernels.
+template <bool CPL>
+__global__ void __launch_bounds__(32, 16)
+k_bond_big(DevState<float> s, StepConst k, int with_dt, int update) {
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
+    for (int base = blockIdx.x * 32; base < k.npoints; base += gridDim.x * 32) {
+        const int i = base + (int)threadIdx.x;
+        const bool big = i < k.npoints && s.row_ptr[i + 1] - s.row_ptr[i] > kTcRows;
+        unsigned m = __ballot_sync(0xffffffffu, big);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            bond_point<float, 0, 32, CPL>(s, k, base + l, with_dt, update);
         }
     }
+}
+
+// Fused bond kernel with the sub-horizon sums on the tensor cores
+// (tc_pass_sums): one warp per point with at most kTcRows bonds, the mixed
+// path, the force state of Eq. 51 (and the coupled mode).  The member
+// features are built once; then, 32 bonds at a time, their sums and their
+// updates (bond_epilogue), as in bond_point.
+template <bool CPL>
+__global__ void __launch_bounds__(32, 16)
+k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
+    using Real = float;
+    constexpr int NRED = CPL ? 13 : 12;
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x;
+    const size_t n = (size_t)k.npoints;
+    const int r0 = s.row_ptr[i];
+    const int nb = s.row_ptr[i + 1] - r0;
+    if (nb > kTcRows) return;                       // k_bond_big takes this point
+    __shared__ R4<float> s_z[kTcRows];              // zeta~_k, lattice units, |zeta~_k|^2
+    // Ydot_k while the features are built, then the sums of a pass (and the
+    // rows where plastic bonds park during their returns)
+    __shared__ alignas(16) unsigned char s_yF[kTcYF];
+    __shared__ float s_Jm[CPL ? kTcRows : 1];       // coupled mode: the members' volume ratios
+    __shared__ alignas(16) unsigned s_phi[32][kTcPhiStride / 2];
+    __shared__ Real s_red[1][NRED];
+    __shared__ unsigned s_cnt[1][5];
+    R4<float>* s_y = reinterpret_cast<R4<float>*>(s_yF);
+    float(*F)[kTcF] = reinterpret_cast<float(*)[kTcF]>(s_yF);
+
+    const int li = s.lat[i];
+    const int ix = lat_x(li), iy = lat_y(li), iz = lat_z(li);
+    const Real inv_dx = k.inv_dxf;
+    Real sig_i[6];
+#pragma unroll
+    for (int c = 0; c < 6; c++) sig_i[c] = s.sig[c * n + i];
+    const Real pc_i = s.pc[i];
+    const Real eps_i = s.eps[i];
+    const ColumnConst cc = s.cols[s.colid[i]];
+    Real Srs = cc.Srsf;
+    if constexpr (CPL) {
+        Real mass_unused;
+        coupled_point<Real>(k, s.J[i], Srs, mass_unused);
+    }
+    // stage the family of i (the FP32 staging of bond_point)
+    const Real uxi = s.u[i], uyi = s.u[n + i], uzi = s.u[2 * n + i];
+    const Real vxi = s.vh[i], vyi = s.vh[n + i], vzi = s.vh[2 * n + i];
+    for (int t = lane; t < nb; t += 32) {
+        const int j = s.col[r0 + t];
+        const int lj = s.lat[j];
+        R4<Real> z, y;
+        z.x = (Real)(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
+        z.y = (Real)(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) + (s.u[n + j] - uyi) * inv_dx;
+        z.z = (Real)(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
+        z.w = z.x * z.x + z.y * z.y + z.z * z.z;
+        y.x = s.vh[j] - vxi;
+        y.y = s.vh[n + j] - vyi;
+        y.z = s.vh[2 * n + j] - vzi;
+        y.w = (Real)0;
+        s_z[t] = z;
+        s_y[t] = y;
+        if constexpr (CPL) s_Jm[t] = s.J[j];
+    }
+    __syncwarp();
+    float uK, uA;
+    tc_build_features(s_z, s_y, nb, s_phi, uK, uA);   // s_y is free afterwards
+
+    const Real hf2 = k.hf2f;
+    const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
+    Real red[NRED];
+#pragma unroll
+    for (int e = 0; e < NRED; e++) red[e] = (Real)0;
+    unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
+    // one copy of the pass in the code (its body is large: the loop is not unrolled)
+#pragma unroll 1
+    for (int p = 0; 32 * p < nb; p++) {
+        const int t = 32 * p + lane;
+        // the bond's reverse slot, issued before the sums so that its latency hides
+        const int rb = t < nb ? s.rev[r0 + t] : -1;
+        __syncwarp();                                 // the previous pass's rows are free
+        tc_pass_sums(s_z, nb, p, hf2, s_phi, F, uK, uA);
+        if (t < nb) {
+            const float* Fr = F[lane];
+            const Real K00 = Fr[0], K11 = Fr[1], K22 = Fr[2], K12 = Fr[3], K02 = Fr[4], K01 = Fr[5];
+            const Real A00 = Fr[6], A01 = Fr[7], A02 = Fr[8], A10 = Fr[9], A11 = Fr[10], A12 = Fr[11];
+            const Real A20 = Fr[12], A21 = Fr[13], A22 = Fr[14];
+            const Real cntr = Fr[15];
+            const R4<Real> zj = s_z[t];
+            // the row is this lane's until the next pass: it parks there
+            bond_epilogue<Real, 0, CPL, NRED>(
+                s, k, i, r0, t, rb, zj, CPL ? s_Jm[t] : (Real)1, K00, K11, K22, K12, K02, K01,
+                A00, A01, A02, A10, A11, A12, A20, A21, A22, cntr, small_count(cntr), (Real)0, (Real)0,
+                (Real)0, (Real)0, sig_i, pc_i, cc, Srs, inv_nb, inv_dx, with_dt, F[lane], nullptr, red,
+                n_pairs, n_plastic, n_nonconv, n_singular, n_ret64);
+        }
+    }
+    block_sum<NRED, Real>(red, s_red);
+    unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
+    block_sum<5, unsigned>(cnts, s_cnt);
+    point_commit<Real, CPL, NRED>(s, i, n, red, red[0], eps_i, cnts, update);
 }
 
 // ---------------------------------------------------------------------------
 // gather: f_i = dx^2 (sum_own T^ - sum T^[rev]); acceleration, corrector
 // ---------------------------------------------------------------------------
 
+// kGatherLanes lanes per point (four points per warp): each lane sums every
+// kGatherLanes-th entry of the point's row with a compensated running sum,
+// then the group combines its lanes in a fixed butterfly; lanes 0..2 of the
+// group finish the point's three components
 template <typename Real>
-__global__ void __launch_bounds__(kWarpPointsPerBlock * 32)
+__global__ void __launch_bounds__(kGatherPointsPerBlock * kGatherLanes)
 k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     constexpr bool F64 = sizeof(Real) == 8;
-    constexpr int kIt = kMaxRow / 32;
+    constexpr int G = kGatherLanes;
     if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;   // the run has stopped
-    __shared__ Real s_e[kWarpPointsPerBlock][3];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int i = blockIdx.x * kWarpPointsPerBlock + wib;       // one warp per point
+    __shared__ Real s_e[kGatherPointsPerBlock][3];
+    const int lane = threadIdx.x & 31, sub = threadIdx.x & (G - 1), grp = threadIdx.x / G;
+    const int lead = lane & ~(G - 1);                            // the group's first lane
+    const int i = blockIdx.x * kGatherPointsPerBlock + grp;
+    const bool valid = i < k.npoints;
     const size_t n = (size_t)k.npoints;
     Real m = F64 ? (Real)(k.rho * k.dx * k.dx * k.dx) : (Real)k.massf;
     Real dx2 = F64 ? (Real)(k.dx * k.dx) : (Real)k.dx2f;
     // coupled mode: the point's mass and its volume factor J (start of the step)
-    if (k.coupled && i < k.npoints) {
+    if (k.coupled && valid) {
         const Real Jp = s.J[i];
         Real srs_unused;
         coupled_point<Real>(k, Jp, srs_unused, m);
@@ -555,29 +729,34 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     const Real dtr = F64 ? (Real)dt : (Real)(float)dt;
     const Real hdt = (Real)0.5 * dtr;
     Real dwi = 0, dwe = 0, wk = 0;
-    if (i < k.npoints) {
-        const int r0 = s.row_ptr[i], r1 = s.row_ptr[i + 1];
-        // lanes 0..2 fetch the per-point data of component c = lane early
-        const int c = lane < 3 ? lane : 0;
-        const size_t t = (size_t)c * n + i;
-        const Real ts = s.tsum[t], fo = s.fint[t], vh = s.vh[t], v0 = s.v[t];
-        Real vbar;
-        const bool fixed = prescribed(s, k, (size_t)i, c, vbar);
-        // every load of the row T_(ji) (stored contiguously in Trev) first
-        Real x[3][kIt];
+    // lanes 0..2 of the group fetch the per-point data of component c = sub early
+    const int c = sub < 3 ? sub : 0;
+    const size_t t = (size_t)c * n + (valid ? i : 0);
+    Real ts = 0, fo = 0, vh = 0, v0 = 0, vbar = 0;
+    bool fixed = false;
+    int r0 = 0, r1 = 0;
+    if (valid) {
+        r0 = s.row_ptr[i];
+        r1 = s.row_ptr[i + 1];
+        ts = s.tsum[t]; fo = s.fint[t]; vh = s.vh[t]; v0 = s.v[t];
+        fixed = prescribed(s, k, (size_t)i, c, vbar);
+    }
+    // the row T_(ji) (stored contiguously in Trev), four strides of loads at a time
+    Real sum[3], cmp[3];
 #pragma unroll
-        for (int it = 0; it < kIt; it++) {
-            const int b = r0 + lane + 32 * it;
+    for (int q = 0; q < 3; q++) { sum[q] = (Real)0; cmp[q] = (Real)0; }
+    for (int b0 = r0 + sub; b0 < r1; b0 += 4 * G) {
+        Real x[3][4];
+#pragma unroll
+        for (int it = 0; it < 4; it++) {
+            const int b = b0 + G * it;
 #pragma unroll
             for (int q = 0; q < 3; q++) x[q][it] = b < r1 ? s.Trev[(size_t)q * k.cap + b] : (Real)0;
         }
-        Real sum[3], cmp[3];
 #pragma unroll
-        for (int q = 0; q < 3; q++) {
-            sum[q] = (Real)0;
-            cmp[q] = (Real)0;
+        for (int q = 0; q < 3; q++)
 #pragma unroll
-            for (int it = 0; it < kIt; it++) {
+            for (int it = 0; it < 4; it++) {
                 if constexpr (F64) {
                     sum[q] += x[q][it];
                 } else {
@@ -587,111 +766,110 @@ k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
                     cmp[q] += ee;
                 }
             }
-        }
-        // fixed-order butterfly over lanes (every lane ends with the total)
+    }
+    // fixed-order butterfly over the group's lanes (each ends with the total)
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
+    for (int off = G / 2; off > 0; off >>= 1) {
 #pragma unroll
-            for (int q = 0; q < 3; q++) {
-                const Real so = __shfl_xor_sync(0xffffffffu, sum[q], off);
-                const Real co = __shfl_xor_sync(0xffffffffu, cmp[q], off);
-                if constexpr (F64) {
-                    sum[q] += so;
-                } else {
-                    float ss, ee;
-                    two_sum(sum[q], so, ss, ee);
-                    sum[q] = ss;
-                    cmp[q] = cmp[q] + co + ee;
-                }
+        for (int q = 0; q < 3; q++) {
+            const Real so = __shfl_xor_sync(0xffffffffu, sum[q], off);
+            const Real co = __shfl_xor_sync(0xffffffffu, cmp[q], off);
+            if constexpr (F64) {
+                sum[q] += so;
+            } else {
+                float ss, ee;
+                two_sum(sum[q], so, ss, ee);
+                sum[q] = ss;
+                cmp[q] = cmp[q] + co + ee;
             }
         }
-        // contact with the rigid substrate (Sec. 4.2, Eq. 91-93; readings
-        // R31-R33): the plane z = -delta_c below the bottom layer; normal
-        // force C_s dx^2 (delta_c - d) / delta_c at a distance d < delta_c,
-        // Coulomb friction on the tangential velocity the point would have
-        // after the half step without it, never reversing that velocity
-        Real fcon = (Real)0;
-        if (k.contact) {
-            const Real tsx = __shfl_sync(0xffffffffu, ts, 0), tsy = __shfl_sync(0xffffffffu, ts, 1);
-            if (lane < 3) {
-                const int li = s.lat[i];
-                Real z;
-                if constexpr (F64) z = __dadd_rn(__dmul_rn((double)lat_z(li), k.dx), (double)s.u[2 * n + i]);
-                else z = (float)lat_z(li) * k.dxf + s.u[2 * n + i];
-                const Real dc = F64 ? (Real)k.contact_dc : (Real)k.contact_dcf;
-                const Real d = z + dc;
-                if (d < dc) {
-                    const Real Fn = F64 ? (Real)(k.contact_modulus * k.dx * k.dx) * (dc - d) / dc
-                                        : (Real)k.contact_kf * (dc - d) / dc;
-                    if (c == 2) {
-                        fcon = Fn;
-                    } else if (k.friction > 0.0) {
-                        const Real hdc = F64 ? (Real)(0.5 * k.dt) : (Real)k.hdtf;
-                        const Real* w = initial ? s.v : s.vh;
-                        const Real gx = F64 ? (Real)k.g[0] : (Real)k.gf[0];
-                        const Real gy = F64 ? (Real)k.g[1] : (Real)k.gf[1];
-                        const Real vtx = w[i] + hdc * ((tsx - (sum[0] + cmp[0])) * dx2 / m + gx);
-                        const Real vty = w[n + i] + hdc * ((tsy - (sum[1] + cmp[1])) * dx2 / m + gy);
-                        const Real nrm = sqrt(vtx * vtx + vty * vty);
-                        if (nrm > (Real)0) {
-                            const Real mu = F64 ? (Real)k.friction : (Real)k.frictionf;
-                            const Real Ft = fmin(mu * Fn, m * nrm / hdc);
-                            fcon = -Ft * (c == 0 ? vtx : vty) / nrm;
-                        }
+    }
+    // contact with the rigid substrate (Sec. 4.2, Eq. 91-93; readings
+    // R31-R33): the plane z = -delta_c below the bottom layer; normal
+    // force C_s dx^2 (delta_c - d) / delta_c at a distance d < delta_c,
+    // Coulomb friction on the tangential velocity the point would have
+    // after the half step without it, never reversing that velocity
+    Real fcon = (Real)0;
+    if (k.contact) {
+        const Real tsx = __shfl_sync(0xffffffffu, ts, lead), tsy = __shfl_sync(0xffffffffu, ts, lead + 1);
+        if (valid && sub < 3) {
+            const int li = s.lat[i];
+            Real z;
+            if constexpr (F64) z = __dadd_rn(__dmul_rn((double)lat_z(li), k.dx), (double)s.u[2 * n + i]);
+            else z = (float)lat_z(li) * k.dxf + s.u[2 * n + i];
+            const Real dc = F64 ? (Real)k.contact_dc : (Real)k.contact_dcf;
+            const Real d = z + dc;
+            if (d < dc) {
+                const Real Fn = F64 ? (Real)(k.contact_modulus * k.dx * k.dx) * (dc - d) / dc
+                                    : (Real)k.contact_kf * (dc - d) / dc;
+                if (c == 2) {
+                    fcon = Fn;
+                } else if (k.friction > 0.0) {
+                    const Real hdc = F64 ? (Real)(0.5 * k.dt) : (Real)k.hdtf;
+                    const Real* w = initial ? s.v : s.vh;
+                    const Real gx = F64 ? (Real)k.g[0] : (Real)k.gf[0];
+                    const Real gy = F64 ? (Real)k.g[1] : (Real)k.gf[1];
+                    const Real vtx = w[i] + hdc * ((tsx - (sum[0] + cmp[0])) * dx2 / m + gx);
+                    const Real vty = w[n + i] + hdc * ((tsy - (sum[1] + cmp[1])) * dx2 / m + gy);
+                    const Real nrm = sqrt(vtx * vtx + vty * vty);
+                    if (nrm > (Real)0) {
+                        const Real mu = F64 ? (Real)k.friction : (Real)k.frictionf;
+                        const Real Ft = fmin(mu * Fn, m * nrm / hdc);
+                        fcon = -Ft * (c == 0 ? vtx : vty) / nrm;
                     }
                 }
             }
         }
-        if (lane < 3) {
-            const Real g = F64 ? (Real)k.g[c] : (Real)k.gf[c];
-            const Real gathered = c == 0 ? sum[0] + cmp[0] : (c == 1 ? sum[1] + cmp[1] : sum[2] + cmp[2]);
-            const Real fhat = ts - gathered;
-            Real f = fhat * dx2;                                     // Eq. 49-50
-            Real a = fhat * inv_rho_dx + g;                          // Eq. 62
-            if (k.coupled) a = f / m + g;
-            if (k.contact) {
-                f += fcon;                                           // Eq. 93
-                a = f / m + g;
-            }
-            if (fixed) a = (Real)0;
-            bool bad = !isfinite(a);
-            s.fint[t] = f;
-            s.a[t] = a;
-            if (initial) {
-                bad = bad || !isfinite(v0);
-                wk = (Real)0.5 * m * v0 * v0;
-            } else {
-                const Real v = vh + hdt * a;                         // Eq. 63
-                // a point whose position stopped being finite leaves every
-                // family and keeps a finite acceleration: its velocity tells
-                bad = bad || !isfinite(v);
-                s.v[t] = v;
-                dwi = -hdt * vh * (fo + f);                          // Eq. 66
-                dwe = dtr * m * vh * g;                              // Eq. 67
-                // a prescribed component moves under the reaction -(f + m g);
-                // its work is external (zero where the component is held)
-                if (fixed) dwe += -hdt * vh * (fo + f + (Real)2 * m * g);
-                wk = (Real)0.5 * m * v * v;                          // Eq. 68
-            }
-            if (bad) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
-        }
-        // coupled mode: the volume ratio the bond pass computed is the next
-        // step's (every reader of J in this step has run)
-        if (k.coupled && !initial && lane == 0) s.J[i] = s.Jn[i];
     }
-    // energies of the point: lanes 0..2 hold the three components
+    if (valid && sub < 3) {
+        const Real g = F64 ? (Real)k.g[c] : (Real)k.gf[c];
+        const Real gathered = c == 0 ? sum[0] + cmp[0] : (c == 1 ? sum[1] + cmp[1] : sum[2] + cmp[2]);
+        const Real fhat = ts - gathered;
+        Real f = fhat * dx2;                                     // Eq. 49-50
+        Real a = fhat * inv_rho_dx + g;                          // Eq. 62
+        if (k.coupled) a = f / m + g;
+        if (k.contact) {
+            f += fcon;                                           // Eq. 93
+            a = f / m + g;
+        }
+        if (fixed) a = (Real)0;
+        bool bad = !isfinite(a);
+        s.fint[t] = f;
+        s.a[t] = a;
+        if (initial) {
+            bad = bad || !isfinite(v0);
+            wk = (Real)0.5 * m * v0 * v0;
+        } else {
+            const Real v = vh + hdt * a;                         // Eq. 63
+            // a point whose position stopped being finite leaves every
+            // family and keeps a finite acceleration: its velocity tells
+            bad = bad || !isfinite(v);
+            s.v[t] = v;
+            dwi = -hdt * vh * (fo + f);                          // Eq. 66
+            dwe = dtr * m * vh * g;                              // Eq. 67
+            // a prescribed component moves under the reaction -(f + m g);
+            // its work is external (zero where the component is held)
+            if (fixed) dwe += -hdt * vh * (fo + f + (Real)2 * m * g);
+            wk = (Real)0.5 * m * v * v;                          // Eq. 68
+        }
+        if (bad) atomicOr(&s.ctr->status, PPM_STATUS_NONFINITE);
+    }
+    // coupled mode: the volume ratio the bond pass computed is the next
+    // step's (every reader of J in this step has run)
+    if (k.coupled && !initial && valid && sub == 0) s.J[i] = s.Jn[i];
+    // energies of the point: lanes 0..2 of the group hold the three components
     dwi += __shfl_down_sync(0xffffffffu, dwi, 1) + __shfl_down_sync(0xffffffffu, dwi, 2);
     dwe += __shfl_down_sync(0xffffffffu, dwe, 1) + __shfl_down_sync(0xffffffffu, dwe, 2);
     wk += __shfl_down_sync(0xffffffffu, wk, 1) + __shfl_down_sync(0xffffffffu, wk, 2);
-    if (lane == 0) {
-        s_e[wib][0] = dwi;
-        s_e[wib][1] = dwe;
-        s_e[wib][2] = wk;
+    if (sub == 0) {
+        s_e[grp][0] = valid ? dwi : (Real)0;
+        s_e[grp][1] = valid ? dwe : (Real)0;
+        s_e[grp][2] = valid ? wk : (Real)0;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
         double tot = 0.0;
-        for (int q = 0; q < kWarpPointsPerBlock; q++) tot += (double)s_e[q][threadIdx.x];
+        for (int q = 0; q < kGatherPointsPerBlock; q++) tot += (double)s_e[q][threadIdx.x];
         s.epart[(size_t)blockIdx.x * 3 + threadIdx.x] = tot;
     }
 }
@@ -787,6 +965,22 @@ __global__ void k_velocity_bc(DevState<Real> s, StepConst k) {
     }
 }
 
+template <typename Real>
+__global__ void k_tforce_from_rev(DevState<Real> s, long long cap, long long nbonds) {
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbonds;
+         b += (long long)gridDim.x * blockDim.x) {
+        const long long rb = s.rev[b];
+#pragma unroll
+        for (int q = 0; q < 3; q++) s.T[q * cap + b] = s.Trev[q * cap + rb];
+    }
+}
+
+// blocks of k_bond_big: each scans 32 points at a time
+inline int big_blocks(int npoints) {
+    const int b = (npoints + 31) / 32;
+    return b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16;
+}
+
 inline int blocks_for(size_t work, int tpb) {
     size_t b = (work + tpb - 1) / tpb;
     return (int)(b < 65536 ? (b > 0 ? b : 1) : 65536);
@@ -829,6 +1023,20 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
     else if (tpp == 64) PPM_BOND(M, 64);            \
     else if (tpp == 256) PPM_BOND(M, 256);          \
     else PPM_BOND(M, 128);
+    if constexpr (sizeof(Real) == 4) {
+        if (k.model == 0 && tpp == 32) {
+            // tensor-core sums, one warp per point; then the points with more
+            // than kTcRows bonds (normally none) with the scalar sums
+            if (k.coupled) {
+                k_bond_tcw<true><<<k.npoints, 32, 0, st>>>(s, k, with_dt, update);
+                k_bond_big<true><<<big_blocks(k.npoints), 32, 0, st>>>(s, k, with_dt, update);
+            } else {
+                k_bond_tcw<false><<<k.npoints, 32, 0, st>>>(s, k, with_dt, update);
+                k_bond_big<false><<<big_blocks(k.npoints), 32, 0, st>>>(s, k, with_dt, update);
+            }
+            return cudaGetLastError();
+        }
+    }
     switch (k.model) {
         case 0: PPM_BOND_TILES(0); break;
         case 1: PPM_BOND_TILES(1); break;
@@ -842,7 +1050,15 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
 template <typename Real>
 cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt, int initial,
                           int gather_blocks, cudaStream_t st) {
-    k_gather<Real><<<gather_blocks, kWarpPointsPerBlock * 32, 0, st>>>(s, k, dt, initial);
+    k_gather<Real><<<gather_blocks, kGatherPointsPerBlock * kGatherLanes, 0, st>>>(s, k, dt, initial);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_tforce_from_rev(const DevState<Real>& s, const StepConst& k, long long nbonds,
+                                   cudaStream_t st) {
+    if (nbonds <= 0) return cudaSuccess;
+    k_tforce_from_rev<Real><<<blocks_for((size_t)nbonds, 256), 256, 0, st>>>(s, k.cap, nbonds);
     return cudaGetLastError();
 }
 
@@ -862,7 +1078,9 @@ cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, i
     template cudaError_t launch_bond<R>(const DevState<R>&, const StepConst&, double, int,         \
                                         cudaStream_t);                                             \
     template cudaError_t launch_gather<R>(const DevState<R>&, const StepConst&, double, int, int,  \
-                                          cudaStream_t);
+                                          cudaStream_t);                                           \
+    template cudaError_t launch_tforce_from_rev<R>(const DevState<R>&, const StepConst&, long long, \
+                                                   cudaStream_t);
 PPM_INSTANTIATE(double)
 PPM_INSTANTIATE(float)
 #undef PPM_INSTANTIATE

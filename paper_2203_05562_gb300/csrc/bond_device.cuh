@@ -3,7 +3,9 @@
 // FP64 and FP32, the constitutive update of one bond, predicated
 // sub-horizon accumulation and deterministic block sums.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 
 #include "ppm_internal.cuh"
@@ -39,25 +41,67 @@ __device__ __forceinline__ bool inverse_sym_fp64(const double k[6], double inv[6
     return true;
 }
 
+// Exact IEEE 754 re-encodings between binary32 and binary64 in integer
+// operations.  On GB300 the hardware conversions issue on the FP64 pipe at
+// the FP64 rate (about 1/64 of FP32); these take the integer and FP32 pipes.
+// binary32 -> binary64 is exact: the exponent is re-biased by 1023 - 127 =
+// 896 and the 23-bit fraction moves to the top of the 52-bit one; zero keeps
+// its sign; subnormal, infinite and NaN inputs (rare here) take the
+// hardware conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u, mag = u & 0x7fffffffu;
+    if (mag - 0x00800000u < 0x7f000000u || mag == 0u) {
+        const unsigned hi = mag ? (sign | ((mag >> 3) + 0x38000000u)) : sign;
+        return __hiloint2double((int)hi, (int)(mag << 29));
+    }
+    return (double)f;
+}
+
+// binary64 -> binary32, round to nearest even: for results in the normal
+// binary32 range the top 23 fraction bits are kept and the 29 dropped bits
+// decide the rounding (above half: up; exactly half: up when the kept lsb
+// is odd); a carry out of the fraction moves into the exponent, and out of
+// the largest exponent into infinity, as the rounding rule requires.
+// Zero and binary64 subnormals give a signed zero; results that are
+// binary32 subnormal, and infinities and NaN, take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sign = hi & 0x80000000u, E = (hi >> 20) & 0x7ffu;
+    if (E - 897u < 254u) {
+        unsigned f = ((E - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;
+        f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+        return __uint_as_float(sign | f);
+    }
+    if (E == 0u) return __uint_as_float(sign);
+    return (float)d;
+}
+
 // Mixed path: the cancellation-prone steps -- cofactors and determinant --
 // in FP64 from the FP32 sums; the degeneracy test, the reciprocal of the
 // determinant and the final scaling in FP32 (the result is FP32 either
-// way, so a full FP64 division would change it by at most an ulp).
+// way, so a full FP64 division would change it by at most an ulp).  The
+// conversions between the formats are the exact re-encodings above (the
+// same bits as the hardware's), so that only the 15 FP64 operations of the
+// cofactors and the determinant use the FP64 pipe.
 __device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K22, float K12,
                                                   float K02, float K01, float inv[6]) {
-    const double k00 = K00, k11 = K11, k22 = K22, k12 = K12, k02 = K02, k01 = K01;
+    const double k00 = f32_to_f64_exact(K00), k11 = f32_to_f64_exact(K11);
+    const double k22 = f32_to_f64_exact(K22), k12 = f32_to_f64_exact(K12);
+    const double k02 = f32_to_f64_exact(K02), k01 = f32_to_f64_exact(K01);
     const double c00 = k11 * k22 - k12 * k12;
     const double c11 = k00 * k22 - k02 * k02;
     const double c22 = k00 * k11 - k01 * k01;
     const double c12 = k01 * k02 - k00 * k12;
     const double c02 = k01 * k12 - k02 * k11;
     const double c01 = k02 * k12 - k01 * k22;
-    const float det = (float)(k00 * c00 + k01 * c01 + k02 * c02);
+    const float det = f64_to_f32_rn(k00 * c00 + k01 * c01 + k02 * c02);
     const float t = (K00 + K11 + K22) * (1.0f / 3.0f);
     if (!(det > 1e-12f * t * t * t) || det == 0.0f) return false;
     const float r = 1.0f / det;
-    inv[0] = (float)c00 * r; inv[1] = (float)c11 * r; inv[2] = (float)c22 * r;
-    inv[3] = (float)c12 * r; inv[4] = (float)c02 * r; inv[5] = (float)c01 * r;
+    inv[0] = f64_to_f32_rn(c00) * r; inv[1] = f64_to_f32_rn(c11) * r; inv[2] = f64_to_f32_rn(c22) * r;
+    inv[3] = f64_to_f32_rn(c12) * r; inv[4] = f64_to_f32_rn(c02) * r; inv[5] = f64_to_f32_rn(c01) * r;
     return true;
 }
 
@@ -606,6 +650,237 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
+}
+
+// A non-negative integer held exactly in a float (below 2^22) as an int,
+// by adding 1.5 * 2^23 so that the value lands in the low mantissa bits:
+// the same result as the conversion instruction, which on GB300 issues on
+// the FP64 pipe.
+__device__ __forceinline__ int small_count(float c) {
+    return __float_as_int(c + 12582912.0f) - 0x4B400000;
+}
+
+// FP32 sub-horizon membership test of member k (z_k = (zeta~_k, |zeta~_k|^2))
+// for bond j, with m_j = (-2 zeta~_j, hf^2 - |zeta~_j|^2):
+// |z_k|^2 - 2 z_k.z_j <= hf^2 - |z_j|^2, i.e. |zeta~_k - zeta~_j|^2 <= hf^2
+// (the sub-horizon test of Alg. 1), always with this rounding sequence, so
+// that every kernel that tests a pair takes the same decision.
+__device__ __forceinline__ float member_test_lhs(float zx, float zy, float zz, float zw, float mx,
+                                                 float my, float mz) {
+    return __fmaf_rn(zx, mx, __fmaf_rn(zy, my, __fmaf_rn(zz, mz, zw)));
+}
+
+// ---------------------------------------------------------------------------
+// Sub-horizon sums on the tensor cores (mixed path)
+// ---------------------------------------------------------------------------
+// For one point with nb <= kTcRows bonds, the sums of every bond t over its
+// sub-horizon (Eq. 23-25, 55) form a product: F = Mask * Phi, where
+// Mask[t][k] = 1 if family member k lies in the sub-horizon of bond t (the
+// FP32 test above, the same decision as the scalar loop) and Phi[k] holds
+// the member's features zeta~ zeta~^T (6), Ydot zeta~^T (9) and 1 (count).
+// Mask is exact in fp16.  Each feature is scaled by a power of two into
+// [-1, 1] and split (Veltkamp, in FP32) into a part of 11 significant bits
+// and the remainder; both are fp16 terms, together within 2^-24 of the
+// largest scaled feature.  The products are exact and accumulate in FP32
+// (mma.sync m16n8k16; each lane builds its 16x16 mask fragment with the FP32
+// tests), so the sums have the accuracy of the FP32 sums they replace, with
+// another rounding order.  One warp does a point: the features once, then
+// 32 bonds (two 16-row tiles) per pass, just before their updates.
+constexpr int kTcRows = 128;        // bonds (and members) of a point summed this way
+constexpr int kTcPhiStride = 136;   // halfs per feature row: 16-byte rows, conflict-free ldmatrix
+constexpr int kTcF = 17;            // floats per bond row of a pass's sums (odd: conflict-free)
+constexpr int kTcYF = (kTcRows * 16 > 32 * kTcF * 4) ? kTcRows * 16 : 32 * kTcF * 4;
+
+// 2^-(e+1) for 2^e <= m < 2^(e+1): m times it lies in [1/2, 1)
+__device__ __forceinline__ float tc_scale(float m) {
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xffu);
+    if (e == 0 || e >= 253) return 1.0f;
+    return __uint_as_float((unsigned)(253 - e) << 23);
+}
+
+__device__ __forceinline__ unsigned tc_mask_pair(bool lo, bool hi) {
+    return (lo ? 0x3C00u : 0u) | (hi ? 0x3C000000u : 0u);     // fp16 1.0 in each half
+}
+
+// two FP32 values as an fp16 pair (lo in the low half), one packed conversion
+__device__ __forceinline__ unsigned tc_pack(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&h);
+}
+
+// Veltkamp split with the factor 2^13 + 1: hi keeps 11 significant bits of
+// f, lo = f - hi exactly (no contraction into fused operations)
+__device__ __forceinline__ void tc_split(float f, float& hi, float& lo) {
+    const float c = __fmul_rn(f, 8193.0f);
+    hi = __fsub_rn(c, __fsub_rn(c, f));
+    lo = __fsub_rn(f, hi);
+}
+
+__device__ __forceinline__ void tc_mma(float (&c)[4], unsigned a0, unsigned a1, unsigned a2,
+                                       unsigned a3, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void tc_ldmatrix_x4(unsigned addr, unsigned& r0, unsigned& r1,
+                                               unsigned& r2, unsigned& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+// The 15 scaled features and the count of member k (all zero for a padding
+// member or one without a finite position: it is in no sub-horizon; a
+// non-finite velocity stays in its features and makes the point's velocity
+// gradients NaN, as in the scalar sums)
+__device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R4<float>* s_y, int k,
+                                                   int nb, float sK, float sA, float (&f)[16]) {
+    R4<float> z, y;
+    z.x = z.y = z.z = z.w = 0.0f;
+    y = z;
+    if (k < nb) {
+        z = s_z[k];
+        y = s_y[k];
+    }
+    const bool ok = k < nb && fmaxf(fabsf(z.x), fmaxf(fabsf(z.y), fabsf(z.z))) <= FLT_MAX;
+    if (!ok) {
+        z.x = z.y = z.z = 0.0f;
+        y.x = y.y = y.z = 0.0f;
+    }
+    f[0] = z.x * z.x * sK; f[1] = z.y * z.y * sK; f[2] = z.z * z.z * sK;
+    f[3] = z.y * z.z * sK; f[4] = z.x * z.z * sK; f[5] = z.x * z.y * sK;
+    f[6] = y.x * z.x * sA; f[7] = y.x * z.y * sA; f[8] = y.x * z.z * sA;
+    f[9] = y.y * z.x * sA; f[10] = y.y * z.y * sA; f[11] = y.y * z.z * sA;
+    f[12] = y.z * z.x * sA; f[13] = y.z * z.y * sA; f[14] = y.z * z.z * sA;
+    f[15] = ok ? 1.0f : 0.0f;
+}
+
+// One warp: the member features of a point into phi (row 2f: the high part
+// of feature f, row 2f + 1: the low part, 32 rows of fp16 pairs along the
+// members), and the factors uK, uA that undo the scaling of the K~ and A~
+// sums.  Members [nb, 16 ceil(nb/16)) of s_z are zeroed (tile padding).
+__device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float>* s_y, int nb,
+                                                  unsigned (*phi)[kTcPhiStride / 2], float& uK,
+                                                  float& uA) {
+    const int lane = threadIdx.x & 31;
+    const int KT = (nb + 15) >> 4;
+    // largest |component| of zeta~ and of Ydot over the members with finite values
+    float mz = 0.0f, my = 0.0f;
+    for (int k = lane; k < nb; k += 32) {
+        const R4<float> z = s_z[k], y = s_y[k];
+        const float az = fmaxf(fabsf(z.x), fmaxf(fabsf(z.y), fabsf(z.z)));
+        const float ay = fmaxf(fabsf(y.x), fmaxf(fabsf(y.y), fabsf(y.z)));
+        if (az <= FLT_MAX) mz = fmaxf(mz, az);
+        if (az <= FLT_MAX && ay <= FLT_MAX) my = fmaxf(my, ay);
+    }
+    // non-negative floats order as their bit patterns
+    mz = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mz)));
+    my = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(my)));
+    const float sK = tc_scale(mz * mz), sA = tc_scale(mz * my);
+    uK = 1.0f / sK;                                      // powers of two: exact
+    uA = 1.0f / sA;
+    for (int kp = lane; kp < KT * 8; kp += 32) {
+        float f0[16], f1[16];
+        tc_member_features(s_z, s_y, 2 * kp, nb, sK, sA, f0);
+        tc_member_features(s_z, s_y, 2 * kp + 1, nb, sK, sA, f1);
+#pragma unroll
+        for (int e = 0; e < 15; e++) {
+            float h0, l0, h1, l1;
+            tc_split(f0[e], h0, l0);
+            tc_split(f1[e], h1, l1);
+            phi[2 * e][kp] = tc_pack(h0, h1);
+            phi[2 * e + 1][kp] = tc_pack(l0, l1);
+        }
+        phi[30][kp] = tc_pack(f0[15], f1[15]);
+        phi[31][kp] = 0u;
+    }
+    __syncwarp();
+    for (int k = nb + lane; k < KT * 16; k += 32) {
+        R4<float> zero;
+        zero.x = zero.y = zero.z = zero.w = 0.0f;
+        s_z[k] = zero;
+    }
+    __syncwarp();
+}
+
+// One warp, pass p: the sums of bonds 32p .. 32p + 31 (row tiles 2p, 2p + 1)
+// into F[0..31][0..15]: F[r][0..5] = K~ (xx yy zz yz xz xy), F[r][6..14] = A~
+// (row-major, A_rc = sum Ydot_r zeta~_c), F[r][15] = |S| of bond 32p + r.
+__device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, int nb, int p, float hf2,
+                                             const unsigned (*phi)[kTcPhiStride / 2],
+                                             float (*F)[kTcF], float uK, float uA) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const int KT = (nb + 15) >> 4;
+    const int nm = KT - 2 * p >= 2 ? 2 : 1;              // row tiles with bonds in this pass
+    // bond-side terms of the test for this lane's rows 32p + 16m + g (+ 8)
+    float mj[2][2][4];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int r = 32 * p + 16 * m + g + 8 * h;
+            R4<float> z;
+            z.x = z.y = z.z = z.w = 0.0f;
+            if (r < nb) z = s_z[r];
+            mj[m][h][0] = -2.0f * z.x;
+            mj[m][h][1] = -2.0f * z.y;
+            mj[m][h][2] = -2.0f * z.z;
+            mj[m][h][3] = hf2 - z.w;
+        }
+    float acc[2][4][4];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) acc[m][nt][e] = 0.0f;
+    // ldmatrix rows: lanes 8q .. 8q + 7 address matrix q = (n-tile q/2, k half q%2)
+    const int lm = lane >> 3, lr = lane & 7;
+    const unsigned phi_base = (unsigned)__cvta_generic_to_shared(&phi[0][0]);
+    for (int kt = 0; kt < KT; kt++) {
+        const int c0 = 16 * kt + 2 * tq;
+        const R4<float> z0 = s_z[c0], z1 = s_z[c0 + 1], z2 = s_z[c0 + 8], z3 = s_z[c0 + 9];
+        unsigned b[4][2];
+#pragma unroll
+        for (int np = 0; np < 2; np++) {
+            const int row = 8 * (2 * np + (lm >> 1)) + lr;
+            const unsigned addr = phi_base + (unsigned)(row * kTcPhiStride + 16 * kt + 8 * (lm & 1)) * 2u;
+            tc_ldmatrix_x4(addr, b[2 * np][0], b[2 * np][1], b[2 * np + 1][0], b[2 * np + 1][1]);
+        }
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            if (m >= nm) continue;                       // warp-uniform
+            bool q[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                q[h][0] = member_test_lhs(z0.x, z0.y, z0.z, z0.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
+                q[h][1] = member_test_lhs(z1.x, z1.y, z1.z, z1.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
+                q[h][2] = member_test_lhs(z2.x, z2.y, z2.z, z2.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
+                q[h][3] = member_test_lhs(z3.x, z3.y, z3.z, z3.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
+            }
+            const unsigned a0 = tc_mask_pair(q[0][0], q[0][1]);   // row g, columns 2tq, 2tq + 1
+            const unsigned a1 = tc_mask_pair(q[1][0], q[1][1]);   // row g + 8
+            const unsigned a2 = tc_mask_pair(q[0][2], q[0][3]);   // row g, columns 2tq + 8, 2tq + 9
+            const unsigned a3 = tc_mask_pair(q[1][2], q[1][3]);   // row g + 8
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) tc_mma(acc[m][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+        if (m >= nm) continue;
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            const int f = 4 * nt + tq;                   // columns 2f (high part) and 2f + 1 (low)
+            const float u = f < 6 ? uK : (f < 15 ? uA : 1.0f);
+            F[16 * m + g][f] = (acc[m][nt][0] + acc[m][nt][1]) * u;
+            F[16 * m + g + 8][f] = (acc[m][nt][2] + acc[m][nt][3]) * u;
+        }
+    }
+    __syncwarp();
 }
 
 }  // namespace

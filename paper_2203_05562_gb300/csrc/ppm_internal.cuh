@@ -10,7 +10,9 @@ namespace ppm {
 
 constexpr int kMaxRow = 256;          // hard cap of bonds per point (smem staging)
 constexpr int kDefaultMaxFamily = 192;
-constexpr int kWarpPointsPerBlock = 8;  // family / gather kernels: one warp per point
+constexpr int kWarpPointsPerBlock = 8;  // family kernels: one warp per point
+constexpr int kGatherLanes = 8;         // force gather: lanes per point ...
+constexpr int kGatherPointsPerBlock = 32;   // ... and points per block (256 threads)
 constexpr int kAdjAccDoubles = 32;     // adjoint accumulators (gradient, state sums) ...
 constexpr int kAdjRedBlocks = 152;     // ... followed by 5 partial sums per reduction block
 constexpr int kLatBits = 10;          // packed lattice index: ix | iy << 10 | iz << 20
@@ -154,7 +156,8 @@ struct DevState {
     int32_t* row_ptr;    // N+1
     int32_t* col;        // cap
     int32_t* rev;        // cap
-    Real* T;             // 3 x cap scaled force state, bond order
+    Real* T;             // 3 x cap scaled force state, bond order (written by the step in the
+                         // coupled mode only; otherwise rebuilt from Trev when read)
     Real* Trev;          // 3 x cap: Trev[rev[b]] = T[b], so row j holds T_(ij)
     double* epart;       // energy partials, 3 x gather blocks
     DevCounters* ctr;
@@ -176,7 +179,10 @@ struct DevState {
 // coupled mode, the point volumes: the own row carries J_j T + C / J_i and
 // the reverse slot J_i T + C / J_j, so that the gather's factor J dx^2 gives
 // V_i V_j (T_ij - T_ji) (Eq. 49) and the unscaled pair force.  Returns the
-// own-row value for the row sum.
+// own-row value for the row sum.  Only the reverse slot is written: the
+// gather reads that copy, and outside the coupled mode the bond-order value
+// is Trev[rev[b]] (rebuilt on demand when a caller reads the force states);
+// in the coupled mode the two differ and the bond-order copy is kept.
 template <bool CPL, typename Real, typename V4>
 __device__ __forceinline__ void store_force_state(const DevState<Real>& s, const StepConst& k,
                                                   size_t b, int rb, Real T0, Real T1, Real T2,
@@ -190,9 +196,11 @@ __device__ __forceinline__ void store_force_state(const DevState<Real>& s, const
     } else {
         o[0] = r[0] = T0 + C0; o[1] = r[1] = T1 + C1; o[2] = r[2] = T2 + C2;
     }
-    s.T[b] = o[0];
-    s.T[k.cap + b] = o[1];
-    s.T[2 * k.cap + b] = o[2];
+    if constexpr (CPL) {
+        s.T[b] = o[0];
+        s.T[k.cap + b] = o[1];
+        s.T[2 * k.cap + b] = o[2];
+    }
     if (rb >= 0) {
         s.Trev[rb] = r[0];
         s.Trev[k.cap + rb] = r[1];
@@ -264,6 +272,10 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
 template <typename Real>
 cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt, int initial,
                           int gather_blocks, cudaStream_t st);
+// bond-order force states from the reverse slots: T[b] = Trev[rev[b]]
+template <typename Real>
+cudaError_t launch_tforce_from_rev(const DevState<Real>& s, const StepConst& k, long long nbonds,
+                                   cudaStream_t st);
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
                                  const int32_t* row_ptr, int npoints, int halt, double tol,
                                  cudaStream_t st);

@@ -215,8 +215,8 @@ Sizes sizes_for(const ppm_params* p, int64_t N) {
     z.cap = (long long)N * z.max_family;
     if (z.cap > 0x7fffffffLL) z.cap = 0x7fffffffLL;
     z.ncell_cap = (int)((2 * N > 4096) ? 2 * N : 4096);
-    // the gather runs one warp per point
-    z.gather_blocks = (int)((N + kWarpPointsPerBlock - 1) / kWarpPointsPerBlock);
+    // the gather runs kGatherPointsPerBlock points per block
+    z.gather_blocks = (int)((N + kGatherPointsPerBlock - 1) / kGatherPointsPerBlock);
     return z;
 }
 
@@ -915,6 +915,13 @@ int ppm_read_state(ppm_ctx* c, int field, void* dst, size_t bytes, int dst_is_de
     int rc = field_view(c, field, nb, &v);
     if (rc) return rc;
     if (bytes < v.bytes * (size_t)v.ncomp) return PPM_EINVAL;
+    // the step keeps only the reverse-slot copy of the force states (outside
+    // the coupled mode): the bond-order copy is rebuilt here
+    if (field == PPM_FIELD_TFORCE && !c->p.coupled) {
+        if (c->p.precision == PPM_FP64) CU(launch_tforce_from_rev<double>(c->sd, c->k, nb, c->stream));
+        else CU(launch_tforce_from_rev<float>(c->sf, c->k, nb, c->stream));
+        c->launches += 1;
+    }
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     for (int q = 0; q < v.ncomp; q++)
         CU(cudaMemcpyAsync((char*)dst + q * v.bytes, (char*)v.ptr + q * v.stride_bytes, v.bytes,

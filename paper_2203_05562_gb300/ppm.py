@@ -99,6 +99,7 @@ def library(build_if_missing: bool = True):
             L.ppm_adjoint_workspace_size.argtypes = [vp, C.c_int, C.c_int, szp]
             L.ppm_adjoint_forward.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t]
             L.ppm_adjoint_reverse.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double)]
+            L.ppm_measure_fp32_peak.argtypes = [vp, C.POINTER(C.c_double)]
             L.ppm_struct_size.restype = C.c_size_t
             L.ppm_struct_size.argtypes = [C.c_int]
             L.ppm_destroy.restype = None
@@ -139,6 +140,17 @@ def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_famil
     return p
 
 
+def measure_fp32_peak() -> float:
+    """Measured FP32 multiply-add rate of the current device (TFLOP/s),
+    through ``ppm_measure_fp32_peak`` on the current stream."""
+    import torch
+
+    out = C.c_double(0.0)
+    _check(library().ppm_measure_fp32_peak(C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                           C.byref(out)), "ppm_measure_fp32_peak")
+    return float(out.value)
+
+
 def family_noalloc(x, delta: float, max_family: int = 192, cap: int | None = None):
     """Family of the points x (torch CUDA tensor (3, n), float64) through
     ``ppm_family_noalloc``, which allocates no device memory itself; the
@@ -155,11 +167,14 @@ def family_noalloc(x, delta: float, max_family: int = 192, cap: int | None = Non
     col = torch.empty(max(cap, 1), dtype=torch.int32, device=x.device)
     rev = torch.empty(max(cap, 1), dtype=torch.int32, device=x.device)
     nb = C.c_int64(0)
-    stream = torch.cuda.current_stream(x.device).cuda_stream
-    _check(library().ppm_family_noalloc(n, C.c_void_p(x.data_ptr()), float(delta), int(max_family),
-                                        C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()),
-                                        C.c_void_p(rev.data_ptr()), cap, C.c_void_p(stream),
-                                        C.byref(nb)), "ppm_family_noalloc")
+    # the library uses the current device's copy of its scratch array
+    with torch.cuda.device(x.device):
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        _check(library().ppm_family_noalloc(n, C.c_void_p(x.data_ptr()), float(delta),
+                                            int(max_family), C.c_void_p(row_ptr.data_ptr()),
+                                            C.c_void_p(col.data_ptr()), C.c_void_p(rev.data_ptr()),
+                                            cap, C.c_void_p(stream), C.byref(nb)),
+               "ppm_family_noalloc")
     B = int(nb.value)
     return row_ptr, col[:B], rev[:B]
 
