@@ -465,10 +465,13 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--large-steps", type=int, default=50)
-    ap.add_argument("--tile", type=int, default=128, help="bond-kernel tile for --profile-only")
+    ap.add_argument("--tile", type=int, default=32, help="bond-kernel tile for --profile-only")
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + steps of the mixed path only (for ncu captures)")
+    ap.add_argument("--profile-workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "large_64x64x256_mixed"],
+                    help="the column --profile-only runs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -491,8 +494,9 @@ def main():
     sampler = ClockSampler(local)
     if args.profile_only:
         from paper_2203_05562_gb300 import Simulation
-        sim = Simulation(cfg, precision="mixed", use_graph=False, bond_tile=args.tile)
-        sim.write("v", pi.initial_velocity(cfg))
+        pcfg = pi.config(args.profile_workload)
+        sim = Simulation(pcfg, precision="mixed", use_graph=False, bond_tile=args.tile)
+        sim.write("v", pi.initial_velocity(pcfg))
         sim.step(args.warmup + args.steps)
         torch.cuda.synchronize()
         print(json.dumps({"profile_only": True, "status": sim.status()["flags"]}))
@@ -516,7 +520,11 @@ def main():
     del sim
     from paper_2203_05562_gb300 import Simulation
     tile = fig["status"]["bond_tile"]          # the autotuner's choice, reused below
-    tsim = Simulation(cfg, precision="mixed", bond_tile=tile)
+    shape = {"threads_per_point": tile, "points_per_block": fig["status"]["points_per_block"],
+             "persistent_blocks": fig["status"]["bond_blocks"]}
+    shape_kw = dict(bond_tile=tile, points_per_block=shape["points_per_block"],
+                    bond_grid=2 if shape["persistent_blocks"] else 1)
+    tsim = Simulation(cfg, precision="mixed", **shape_kw)
     tsim.write("v", pi.initial_velocity(cfg))
     tsim.step(args.warmup + align_to_rebuild(args.warmup, cfg["rebuild_every"]))
     t0 = tsim.status()
@@ -539,7 +547,10 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": profiled_traffic(),
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
-                "kernel": f"k_bond<float,0,{tile}> (fused sub-horizon / constitutive / force state)",
+                "kernel": ("k_bond_tcw<0> (fused bond kernel, sub-horizon sums on the tensor cores, "
+                           "one warp per point)" if tile == 32 else
+                           f"k_bond<float,0,{tile}> (fused sub-horizon / constitutive / force state)"),
+                "launch_shape": shape,
                 "peak_kind": "measured: FP32 FMA chains on every SM (ppm_measure_fp32_peak), this run",
                 "peak_nominal": nominal_tflops, "frac_of_nominal": achieved / nominal_tflops,
                 "nominal_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
@@ -555,7 +566,7 @@ def main():
         esim0 = Simulation(ecfg, columns=cols, precision="mixed", bond_tile=0)
         ne = esim0.n
         esim0.write("v", np.random.default_rng(ecfg["seed"]).normal(0, 1e-6, size=(3, ne)))
-        esim0.step(args.warmup)
+        esim0.step(args.warmup + align_to_rebuild(args.warmup, ecfg["rebuild_every"]))
         torch.cuda.synchronize()
         e0 = esim0.status()
         eva, evb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -569,7 +580,9 @@ def main():
                "bonds": e1["nbonds"], "steps": args.ensemble_steps,
                "value": (e1["bond_steps"] - e0["bond_steps"]) / (ems * 1e-3), "unit": UNIT,
                "ms_per_step": ems / args.ensemble_steps, "bond_tile": e1["bond_tile"],
-               "graph": "one CUDA graph per 50-step rebuild period"}
+               "points_per_block": e1["points_per_block"], "persistent_blocks": e1["bond_blocks"],
+               "rebuilds_timed": e1["rebuilds"] - e0["rebuilds"],
+               "graph": "one CUDA graph per 50-step rebuild period; the bond pass one launch over all columns"}
         del esim0
 
     # ---- large column (64x64x256, 1,048,576 points), mixed ----
@@ -578,7 +591,7 @@ def main():
         lcfg = pi.config("large_64x64x256_mixed")
         lsim = Simulation(lcfg, precision="mixed", bond_tile=0)
         lsim.write("v", pi.initial_velocity(lcfg))
-        lsim.step(args.warmup)
+        lsim.step(args.warmup + align_to_rebuild(args.warmup, lcfg["rebuild_every"]))
         torch.cuda.synchronize()
         l0 = lsim.status()
         la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -590,7 +603,9 @@ def main():
         lms = la.elapsed_time(lb)
         large = {"workload": "large_64x64x256_mixed", "points": lsim.n, "bonds": l1["nbonds"],
                  "steps": args.large_steps, "value": (l1["bond_steps"] - l0["bond_steps"]) / (lms * 1e-3),
-                 "unit": UNIT, "ms_per_step": lms / args.large_steps, "bond_tile": l1["bond_tile"]}
+                 "unit": UNIT, "ms_per_step": lms / args.large_steps, "bond_tile": l1["bond_tile"],
+                 "points_per_block": l1["points_per_block"], "persistent_blocks": l1["bond_blocks"],
+                 "rebuilds_timed": l1["rebuilds"] - l0["rebuilds"]}
         del lsim
 
     # ---- adjoint: 40x40x80 column, 200 steps, checkpoints every 20 ----
@@ -677,7 +692,7 @@ def main():
     from paper_2203_05562_gb300 import Simulation
     host_v0 = torch.from_numpy(pi.initial_velocity(cfg).astype(np.float32)).pin_memory()
     host_u = torch.empty((3, n), dtype=torch.float32).pin_memory()
-    esim = Simulation(cfg, precision="mixed", bond_tile=tile)
+    esim = Simulation(cfg, precision="mixed", **shape_kw)
     esim.write("v", host_v0.numpy())
     esim.step(args.warmup + align_to_rebuild(args.warmup, cfg["rebuild_every"]))
     torch.cuda.synchronize()
@@ -735,6 +750,7 @@ def main():
                        "timed_region": "starts at a family rebuild: ceil(steps / rebuild_every) "
                                        "family searches inside",
                        "rebuilds_timed": fig["rebuilds"],
+                       "bond_launch_shape": shape,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_rate, "unit": UNIT, "steps": args.fp64_steps},
             "mixed_over_fp64": value / world / fp64_rate if fp64_rate > 0 else None,

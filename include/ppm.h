@@ -162,6 +162,14 @@ typedef struct {
     double porosity;             /* phi_0 in (0, 1), coupled = 1               */
     double rho_s, rho_w;         /* solid and water densities, coupled = 1     */
     double wr_a1, wr_a2, wr_n;   /* Eq. 15: a1 (1/Pa, > 0), a2 (>= 0), n (> 1) */
+    int32_t points_per_block;    /* tensor-core bond kernel (PPM_MIXED, model 0,
+                                    bond_tile 32): points (one warp each) per
+                                    block, 1 or 2 (0: 1); with bond_tile = 0
+                                    the autotuner chooses                      */
+    int32_t bond_grid;           /* that kernel's grid: 1 (or 0) one warp per
+                                    point; 2 a persistent resident wave of
+                                    blocks looping over the points; with
+                                    bond_tile = 0 the autotuner chooses        */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */
@@ -191,12 +199,17 @@ typedef struct {
     int32_t unstable_step;       /* PPM_STATUS_UNSTABLE: the first step that
                                     failed the Eq. 69 check (from 1), else 0  */
     double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */
+    int32_t points_per_block;    /* tensor-core bond kernel: points per block   */
+    int32_t bond_blocks;         /* its grid: 0 one warp per point, else the
+                                    blocks of the persistent wave              */
 } ppm_counters;
 
 typedef struct ppm_ctx ppm_ctx;
 
 /* Bytes of device workspace needed for these parameters.  n_columns = 0
- * (cols = NULL) means one column described by p->nx, ny, nz, suction, M. */
+ * (cols = NULL) means one column described by p->nx, ny, nz, suction, M.
+ * Plumbing of the library (the caller owns the device memory); the paper
+ * has no counterpart. */
 int ppm_workspace_size(const ppm_params* p, int n_columns, const ppm_column* cols,
                        size_t* bytes);
 
@@ -223,7 +236,8 @@ int ppm_step(ppm_ctx* c, int n_steps);
  * context's stream around each phase and adding the elapsed milliseconds
  * to ms[0] (predictor and, when due, the family search), ms[1] (the fused
  * bond kernel) and ms[2] (gather, corrector and energy terms).
- * Synchronises the stream after every step. */
+ * Synchronises the stream after every step.  Measurement plumbing: the
+ * step it times is ppm_step's; the timing has no counterpart in the paper. */
 int ppm_step_timed(ppm_ctx* c, int n_steps, double ms[3]);
 
 /* Adjoint (reverse-mode gradient) of n_steps explicit steps.  The paper has
@@ -250,14 +264,19 @@ int ppm_adjoint_reverse(ppm_ctx* c, const double* dJ_du, int src_is_device, doub
 
 /* Copies a state field (PPM_FIELD_*) to dst (device pointer if
  * dst_is_device, else host).  bytes must be at least the field's size.
- * Synchronises the stream when dst is a host pointer. */
+ * Synchronises the stream when dst is a host pointer.  PPM_FIELD_TFORCE:
+ * the step keeps the force states at their reverse slots only (outside the
+ * coupled mode), so this call first rebuilds the bond-order copy (one
+ * kernel).  Plumbing (state transfer for checkpoints, tests and output);
+ * the paper has no counterpart. */
 int ppm_read_state(ppm_ctx* c, int field, void* dst, size_t bytes, int dst_is_device);
 
 /* Overwrites a state field from src (same layout and type as read).
  * Writing PPM_FIELD_U marks the family as stale (rebuilt before the next
  * step).  Writing PPM_FIELD_J sets the volume ratio the next step starts
  * from (coupled = 1; it is 1 after ppm_init).  Family fields are
- * read-only. */
+ * read-only.  Plumbing (resume from a checkpoint, set an initial state);
+ * the paper has no counterpart. */
 int ppm_write_state(ppm_ctx* c, int field, const void* src, size_t bytes, int src_is_device);
 
 /* Critical time step of Eq. 65 over the current family and positions (the
@@ -270,13 +289,17 @@ int ppm_write_state(ppm_ctx* c, int field, const void* src, size_t bytes, int sr
  * +inf when no point has a bond.  Synchronises the stream. */
 int ppm_critical_time_step(ppm_ctx* c, double* dt);
 
-/* Number of bonds of the current family (synchronises the stream). */
+/* Number of bonds of the current family (synchronises the stream).
+ * Plumbing; the paper has no counterpart. */
 int ppm_num_bonds(ppm_ctx* c, int64_t* nbonds);
 
-/* Synchronises the stream and returns the counters and status word. */
+/* Synchronises the stream and returns the counters and status word.
+ * Plumbing; the paper has no counterpart, except the energy terms of
+ * Eq. 66-68 and the check of Eq. 69 that they carry. */
 int ppm_status(ppm_ctx* c, ppm_counters* out);
 
-/* Time step in use and total number of points. */
+/* Time step in use and total number of points.  Plumbing; the paper
+ * has no counterpart. */
 int ppm_info(const ppm_ctx* c, double* dt, int64_t* npoints);
 
 /* Family search (as ppm_build_families) of n points with explicit FP64
@@ -317,15 +340,17 @@ int ppm_family_noalloc(int64_t n, const double* d_x, double delta, int max_famil
  * kernel's algorithmic FLOP rate by it.  Allocates nothing. */
 int ppm_measure_fp32_peak(void* cuda_stream, double* tflops);
 
+/* Text of a return code.  Plumbing; the paper has no counterpart. */
 const char* ppm_error_string(int code);
 
 /* sizeof of the ABI structs as compiled into the library, so that a
  * binding can check its own layout: which = 0 ppm_params, 1 ppm_column,
- * 2 ppm_counters; 0 for anything else.  Needs no GPU. */
+ * 2 ppm_counters; 0 for anything else.  Needs no GPU.  Plumbing; the
+ * paper has no counterpart. */
 size_t ppm_struct_size(int which);
 
 /* Frees host-side resources (graphs, events).  The workspace stays the
- * caller's. */
+ * caller's.  Plumbing; the paper has no counterpart. */
 void ppm_destroy(ppm_ctx* c);
 
 #ifdef __cplusplus

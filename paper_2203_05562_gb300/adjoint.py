@@ -27,7 +27,7 @@ class ColumnRun(torch.autograd.Function):
     is the bond kernel's threads per point (32, 64, 128, 256)."""
 
     @staticmethod
-    def forward(ctx, theta, cfg, v0, n_steps, ckpt_every, precision="mixed", bond_tile=128):
+    def forward(ctx, theta, cfg, v0, n_steps, ckpt_every, precision="mixed", bond_tile=32):
         vals = theta.detach().cpu().double().numpy()
         run_cfg = dict(cfg)
         for name, val in zip(PARAMS, vals):

@@ -265,9 +265,9 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
             z.y = (Real)((py - pyi) * k.inv_dx);
             z.z = (Real)((pz - pzi) * k.inv_dx);
         } else {
-            z.x = (Real)(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
-            z.y = (Real)(lat_y(lj) - iy) + (s.u[n + j] - uyi) * inv_dx;
-            z.z = (Real)(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
+            z.x = small_float(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
+            z.y = small_float(lat_y(lj) - iy) + (s.u[n + j] - uyi) * inv_dx;
+            z.z = small_float(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
         }
         z.w = z.x * z.x + z.y * z.y + z.z * z.z;
         if (INITIAL) {

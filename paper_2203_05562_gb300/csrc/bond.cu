@@ -204,13 +204,13 @@ __device__ __forceinline__ void bond_epilogue(
 }
 
 // The point's new state (the varpi-weighted means of its bonds, reading R8),
-// its row sum of force states and the step's counters, written by thread 0
-// (red and cnts are block sums: every thread holds them).
+// its row sum of force states and the step's counters, written by one
+// thread (red and cnts are sums over the point's bonds).
 template <typename Real, bool CPL, int NRED>
 __device__ __forceinline__ void point_commit(const DevState<Real>& s, int i, size_t n,
                                              const Real (&red)[NRED], Real w, Real eps_i,
                                              const unsigned (&cnts)[5], int update) {
-    if (threadIdx.x == 0) {
+    {
         if (update && w > (Real)0) {
             const Real iw = (Real)1 / w;
 #pragma unroll
@@ -315,9 +315,9 @@ __device__ __forceinline__ void bond_point(const DevState<Real>& s, const StepCo
             z.y = (Real)((py - pyi) * k.inv_dx);
             z.z = (Real)((pz - pzi) * k.inv_dx);
         } else {
-            z.x = (Real)(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
-            z.y = (Real)(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) + (s.u[n + j] - uyi) * inv_dx;
-            z.z = (Real)(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
+            z.x = small_float(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
+            z.y = small_float(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) + (s.u[n + j] - uyi) * inv_dx;
+            z.z = small_float(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
         }
         z.w = z.x * z.x + z.y * z.y + z.z * z.z;
         y.x = s.vh[j] - vxi;
@@ -564,7 +564,7 @@ __device__ __forceinline__ void bond_point(const DevState<Real>& s, const StepCo
 
     unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
     block_sum<5, unsigned>(cnts, s_cnt);
-    point_commit<Real, CPL, NRED>(s, i, n, red, w, eps_i, cnts, update);
+    if (threadIdx.x == 0) point_commit<Real, CPL, NRED>(s, i, n, red, w, eps_i, cnts, update);
 }
 
 template <typename Real, int MODEL, int TPP, bool CPL>
@@ -579,8 +579,8 @@ k_bond(DevState<Real> s, StepConst k, int with_dt, int update) {
 // The points with more than kTcRows bonds, for the tensor-core kernel below
 // (which leaves them): one warp per block scans 32 points at a time and
 // runs the scalar sums on each that has more.  Only the mixed path with the
-// force state of Eq. 51 runs this pair of kernels.
-template <bool CPL>
+// force state of Eq. 51 or the power-conjugate one runs this pair of kernels.
+template <int MODEL, bool CPL>
 __global__ void __launch_bounds__(32, 16)
 k_bond_big(DevState<float> s, StepConst k, int with_dt, int update) {
     if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
@@ -591,109 +591,151 @@ k_bond_big(DevState<float> s, StepConst k, int with_dt, int update) {
         while (m) {
             const int l = __ffs(m) - 1;
             m &= m - 1;
-            bond_point<float, 0, 32, CPL>(s, k, base + l, with_dt, update);
+            bond_point<float, MODEL, 32, CPL>(s, k, base + l, with_dt, update);
         }
     }
 }
 
 // Fused bond kernel with the sub-horizon sums on the tensor cores
 // (tc_pass_sums): one warp per point with at most kTcRows bonds, the mixed
-// path, the force state of Eq. 51 (and the coupled mode).  The member
-// features are built once; then, 32 bonds at a time, their sums and their
-// updates (bond_epilogue), as in bond_point.
-template <bool CPL>
-__global__ void __launch_bounds__(32, 16)
+// path, the force state of Eq. 51 (MODEL 0) or the power-conjugate one
+// (MODEL 2), and the coupled mode.  The member features are built once;
+// then, 32 bonds at a time, their sums and their updates (bond_epilogue), as
+// in bond_point.  Model 2 then sums each receiver's senders the same way
+// (tc_pass_receiver).  PPB warps per block, each on its own points: warp w
+// of block b takes points (b PPB + w) + m gridDim.x PPB, m = 0, 1, ..., so
+// the grid may cover every point once or be a persistent wave of resident
+// blocks that loop over them (the launch shape the autotuner picks).
+template <int MODEL, bool CPL, int PPB>
+__global__ void __launch_bounds__(32 * PPB, 16 / PPB)
 k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
     using Real = float;
     constexpr int NRED = CPL ? 13 : 12;
+    static_assert(MODEL == 0 || MODEL == 2, "the sub-horizon force states");
     if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;
-    const int i = blockIdx.x;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const size_t n = (size_t)k.npoints;
-    const int r0 = s.row_ptr[i];
-    const int nb = s.row_ptr[i + 1] - r0;
-    if (nb > kTcRows) return;                       // k_bond_big takes this point
-    __shared__ R4<float> s_z[kTcRows];              // zeta~_k, lattice units, |zeta~_k|^2
+    __shared__ R4<float> s_zs[PPB][kTcRows];          // zeta~_k, lattice units, |zeta~_k|^2
     // Ydot_k while the features are built, then the sums of a pass (and the
     // rows where plastic bonds park during their returns)
-    __shared__ alignas(16) unsigned char s_yF[kTcYF];
-    __shared__ float s_Jm[CPL ? kTcRows : 1];       // coupled mode: the members' volume ratios
-    __shared__ alignas(16) unsigned s_phi[32][kTcPhiStride / 2];
-    __shared__ Real s_red[1][NRED];
-    __shared__ unsigned s_cnt[1][5];
-    R4<float>* s_y = reinterpret_cast<R4<float>*>(s_yF);
-    float(*F)[kTcF] = reinterpret_cast<float(*)[kTcF]>(s_yF);
+    __shared__ alignas(16) unsigned char s_yFs[PPB][kTcYF];
+    __shared__ float s_Jms[PPB][CPL ? kTcRows : 1];   // coupled mode: the members' volume ratios
+    __shared__ alignas(16) unsigned s_phis[PPB][32][kTcPhiStride / 2];
+    // model 2: each sender's matrix M = varpi sigma K^-1 (and its park row)
+    __shared__ alignas(16) float s_Ms[PPB][MODEL == 2 ? kTcRows : 1][16];
+    R4<float>* s_z = s_zs[w];
+    float(*s_M)[16] = s_Ms[w];
+    R4<float>* s_y = reinterpret_cast<R4<float>*>(s_yFs[w]);
+    float(*F)[kTcF] = reinterpret_cast<float(*)[kTcF]>(s_yFs[w]);
+    float* s_Jm = s_Jms[w];
+    unsigned(*s_phi)[kTcPhiStride / 2] = s_phis[w];
 
-    const int li = s.lat[i];
-    const int ix = lat_x(li), iy = lat_y(li), iz = lat_z(li);
-    const Real inv_dx = k.inv_dxf;
-    Real sig_i[6];
+    for (int i = blockIdx.x * PPB + w; i < k.npoints; i += gridDim.x * PPB) {
+        const int r0 = s.row_ptr[i];
+        const int nb = s.row_ptr[i + 1] - r0;
+        if (nb > kTcRows) continue;                   // k_bond_big takes this point (warp-uniform)
+        __syncwarp();                                 // the previous point is done with the arrays
+        const int li = s.lat[i];
+        const int ix = lat_x(li), iy = lat_y(li), iz = lat_z(li);
+        const Real inv_dx = k.inv_dxf;
+        Real sig_i[6];
 #pragma unroll
-    for (int c = 0; c < 6; c++) sig_i[c] = s.sig[c * n + i];
-    const Real pc_i = s.pc[i];
-    const Real eps_i = s.eps[i];
-    const ColumnConst cc = s.cols[s.colid[i]];
-    Real Srs = cc.Srsf;
-    if constexpr (CPL) {
-        Real mass_unused;
-        coupled_point<Real>(k, s.J[i], Srs, mass_unused);
-    }
-    // stage the family of i (the FP32 staging of bond_point)
-    const Real uxi = s.u[i], uyi = s.u[n + i], uzi = s.u[2 * n + i];
-    const Real vxi = s.vh[i], vyi = s.vh[n + i], vzi = s.vh[2 * n + i];
-    for (int t = lane; t < nb; t += 32) {
-        const int j = s.col[r0 + t];
-        const int lj = s.lat[j];
-        R4<Real> z, y;
-        z.x = (Real)(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
-        z.y = (Real)(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) + (s.u[n + j] - uyi) * inv_dx;
-        z.z = (Real)(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
-        z.w = z.x * z.x + z.y * z.y + z.z * z.z;
-        y.x = s.vh[j] - vxi;
-        y.y = s.vh[n + j] - vyi;
-        y.z = s.vh[2 * n + j] - vzi;
-        y.w = (Real)0;
-        s_z[t] = z;
-        s_y[t] = y;
-        if constexpr (CPL) s_Jm[t] = s.J[j];
-    }
-    __syncwarp();
-    float uK, uA;
-    tc_build_features(s_z, s_y, nb, s_phi, uK, uA);   // s_y is free afterwards
-
-    const Real hf2 = k.hf2f;
-    const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
-    Real red[NRED];
-#pragma unroll
-    for (int e = 0; e < NRED; e++) red[e] = (Real)0;
-    unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
-    // one copy of the pass in the code (its body is large: the loop is not unrolled)
-#pragma unroll 1
-    for (int p = 0; 32 * p < nb; p++) {
-        const int t = 32 * p + lane;
-        // the bond's reverse slot, issued before the sums so that its latency hides
-        const int rb = t < nb ? s.rev[r0 + t] : -1;
-        __syncwarp();                                 // the previous pass's rows are free
-        tc_pass_sums(s_z, nb, p, hf2, s_phi, F, uK, uA);
-        if (t < nb) {
-            const float* Fr = F[lane];
-            const Real K00 = Fr[0], K11 = Fr[1], K22 = Fr[2], K12 = Fr[3], K02 = Fr[4], K01 = Fr[5];
-            const Real A00 = Fr[6], A01 = Fr[7], A02 = Fr[8], A10 = Fr[9], A11 = Fr[10], A12 = Fr[11];
-            const Real A20 = Fr[12], A21 = Fr[13], A22 = Fr[14];
-            const Real cntr = Fr[15];
-            const R4<Real> zj = s_z[t];
-            // the row is this lane's until the next pass: it parks there
-            bond_epilogue<Real, 0, CPL, NRED>(
-                s, k, i, r0, t, rb, zj, CPL ? s_Jm[t] : (Real)1, K00, K11, K22, K12, K02, K01,
-                A00, A01, A02, A10, A11, A12, A20, A21, A22, cntr, small_count(cntr), (Real)0, (Real)0,
-                (Real)0, (Real)0, sig_i, pc_i, cc, Srs, inv_nb, inv_dx, with_dt, F[lane], nullptr, red,
-                n_pairs, n_plastic, n_nonconv, n_singular, n_ret64);
+        for (int c = 0; c < 6; c++) sig_i[c] = s.sig[c * n + i];
+        const Real pc_i = s.pc[i];
+        const Real eps_i = s.eps[i];
+        const ColumnConst cc = s.cols[s.colid[i]];
+        Real Srs = cc.Srsf;
+        if constexpr (CPL) {
+            Real mass_unused;
+            coupled_point<Real>(k, s.J[i], Srs, mass_unused);
         }
+        // stage the family of i (the FP32 staging of bond_point)
+        const Real uxi = s.u[i], uyi = s.u[n + i], uzi = s.u[2 * n + i];
+        const Real vxi = s.vh[i], vyi = s.vh[n + i], vzi = s.vh[2 * n + i];
+        for (int t = lane; t < nb; t += 32) {
+            const int j = s.col[r0 + t];
+            const int lj = s.lat[j];
+            R4<Real> z, y;
+            z.x = small_float(lat_x(lj) - ix) + (s.u[j] - uxi) * inv_dx;
+            z.y = small_float(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) + (s.u[n + j] - uyi) * inv_dx;
+            z.z = small_float(lat_z(lj) - iz) + (s.u[2 * n + j] - uzi) * inv_dx;
+            z.w = z.x * z.x + z.y * z.y + z.z * z.z;
+            y.x = s.vh[j] - vxi;
+            y.y = s.vh[n + j] - vyi;
+            y.z = s.vh[2 * n + j] - vzi;
+            y.w = (Real)0;
+            s_z[t] = z;
+            s_y[t] = y;
+            if constexpr (CPL) s_Jm[t] = s.J[j];
+        }
+        __syncwarp();
+        float uK, uA;
+        tc_build_features(s_z, s_y, nb, s_phi, uK, uA);   // s_y is free afterwards
+
+        const Real hf2 = k.hf2f;
+        const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
+        Real red[NRED];
+#pragma unroll
+        for (int e = 0; e < NRED; e++) red[e] = (Real)0;
+        unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
+        // one copy of the pass in the code (its body is large: the loop is not unrolled)
+#pragma unroll 1
+        for (int p = 0; 32 * p < nb; p++) {
+            const int t = 32 * p + lane;
+            // the bond's reverse slot, issued before the sums so that its latency hides
+            const int rb = (MODEL == 0 && t < nb) ? s.rev[r0 + t] : -1;
+            __syncwarp();                             // the previous pass's rows are free
+            tc_pass_sums(s_z, nb, p, hf2, s_phi, F, uK, uA);
+            if (t < nb) {
+                const float* Fr = F[lane];
+                const Real K00 = Fr[0], K11 = Fr[1], K22 = Fr[2], K12 = Fr[3], K02 = Fr[4], K01 = Fr[5];
+                const Real A00 = Fr[6], A01 = Fr[7], A02 = Fr[8], A10 = Fr[9], A11 = Fr[10], A12 = Fr[11];
+                const Real A20 = Fr[12], A21 = Fr[13], A22 = Fr[14];
+                const Real cntr = Fr[15];
+                const R4<Real> zj = s_z[t];
+                // the row is this lane's until the next pass: it parks there
+                // (model 2 parks in the sender's row of s_M)
+                bond_epilogue<Real, MODEL, CPL, NRED>(
+                    s, k, i, r0, t, rb, zj, CPL ? s_Jm[t] : (Real)1, K00, K11, K22, K12, K02, K01,
+                    A00, A01, A02, A10, A11, A12, A20, A21, A22, cntr, small_count(cntr), (Real)0,
+                    (Real)0, (Real)0, (Real)0, sig_i, pc_i, cc, Srs, inv_nb, inv_dx, with_dt, F[lane],
+                    s_M[MODEL == 2 ? t : 0], red, n_pairs, n_plastic, n_nonconv, n_singular, n_ret64);
+            }
+        }
+        warp_sum<NRED, Real>(red);
+        if constexpr (MODEL == 2) {
+            // power-conjugate form: every sub-horizon's force acts on each of
+            // its members; the row is normalised by sum(varpi)
+            const Real w_sum = red[0];
+            const Real inv_w = w_sum > (Real)0 ? (Real)1 / w_sum : (Real)0;
+            __syncwarp();                             // every sender's row of s_M is written
+            const float uM = tc_build_sender_features(s_M, nb, s_phi);
+            Real ts[3] = {(Real)0, (Real)0, (Real)0};
+#pragma unroll 1
+            for (int p = 0; 32 * p < nb; p++) {
+                const int t = 32 * p + lane;
+                const int rb = t < nb ? s.rev[r0 + t] : -1;
+                __syncwarp();
+                tc_pass_receiver(s_z, nb, p, hf2, s_phi, F, uM);
+                if (t < nb) {
+                    const float* Nr = F[lane];
+                    const R4<Real> zt = s_z[t];
+                    const Real T0 = (Nr[0] * zt.x + Nr[1] * zt.y + Nr[2] * zt.z) * inv_w;
+                    const Real T1 = (Nr[3] * zt.x + Nr[4] * zt.y + Nr[5] * zt.z) * inv_w;
+                    const Real T2 = (Nr[6] * zt.x + Nr[7] * zt.y + Nr[8] * zt.z) * inv_w;
+                    Real o[3];
+                    store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zt,
+                                           CPL ? s_Jm[t] : (Real)1, CPL ? s.J[i] : (Real)1, o);
+                    ts[0] += o[0]; ts[1] += o[1]; ts[2] += o[2];
+                }
+            }
+            warp_sum<3, Real>(ts);
+            red[9] = ts[0]; red[10] = ts[1]; red[11] = ts[2];
+        }
+        unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
+        warp_sum<5, unsigned>(cnts);
+        if (lane == 0) point_commit<Real, CPL, NRED>(s, i, n, red, red[0], eps_i, cnts, update);
     }
-    block_sum<NRED, Real>(red, s_red);
-    unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
-    block_sum<5, unsigned>(cnts, s_cnt);
-    point_commit<Real, CPL, NRED>(s, i, n, red, red[0], eps_i, cnts, update);
 }
 
 // ---------------------------------------------------------------------------
@@ -1024,16 +1066,24 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
     else if (tpp == 256) PPM_BOND(M, 256);          \
     else PPM_BOND(M, 128);
     if constexpr (sizeof(Real) == 4) {
-        if (k.model == 0 && tpp == 32) {
+        if ((k.model == 0 || k.model == 2) && tpp == 32) {
             // tensor-core sums, one warp per point; then the points with more
             // than kTcRows bonds (normally none) with the scalar sums
-            if (k.coupled) {
-                k_bond_tcw<true><<<k.npoints, 32, 0, st>>>(s, k, with_dt, update);
-                k_bond_big<true><<<big_blocks(k.npoints), 32, 0, st>>>(s, k, with_dt, update);
+            const int ppb = k.tc_ppb == 2 ? 2 : 1;
+            const int full = (k.npoints + ppb - 1) / ppb;
+            const int grid = (k.tc_blocks > 0 && k.tc_blocks < full) ? k.tc_blocks : full;
+#define PPM_TCW(M, C)                                                                               \
+    do {                                                                                            \
+        if (ppb == 1) k_bond_tcw<M, C, 1><<<grid, 32, 0, st>>>(s, k, with_dt, update);              \
+        else k_bond_tcw<M, C, 2><<<grid, 64, 0, st>>>(s, k, with_dt, update);                       \
+        k_bond_big<M, C><<<big_blocks(k.npoints), 32, 0, st>>>(s, k, with_dt, update);              \
+    } while (0)
+            if (k.model == 0) {
+                if (k.coupled) PPM_TCW(0, true); else PPM_TCW(0, false);
             } else {
-                k_bond_tcw<false><<<k.npoints, 32, 0, st>>>(s, k, with_dt, update);
-                k_bond_big<false><<<big_blocks(k.npoints), 32, 0, st>>>(s, k, with_dt, update);
+                if (k.coupled) PPM_TCW(2, true); else PPM_TCW(2, false);
             }
+#undef PPM_TCW
             return cudaGetLastError();
         }
     }
@@ -1060,6 +1110,24 @@ cudaError_t launch_tforce_from_rev(const DevState<Real>& s, const StepConst& k, 
     if (nbonds <= 0) return cudaSuccess;
     k_tforce_from_rev<Real><<<blocks_for((size_t)nbonds, 256), 256, 0, st>>>(s, k.cap, nbonds);
     return cudaGetLastError();
+}
+
+cudaError_t bond_tc_resident_blocks(int model, int ppb, int coupled, int* blocks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+#define PPM_OCC(M, C, P) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bond_tcw<M, C, P>, 32 * P, 0)
+    if (model == 2) {
+        if (ppb == 2) e = coupled ? PPM_OCC(2, true, 2) : PPM_OCC(2, false, 2);
+        else e = coupled ? PPM_OCC(2, true, 1) : PPM_OCC(2, false, 1);
+    } else {
+        if (ppb == 2) e = coupled ? PPM_OCC(0, true, 2) : PPM_OCC(0, false, 2);
+        else e = coupled ? PPM_OCC(0, true, 1) : PPM_OCC(0, false, 1);
+    }
+#undef PPM_OCC
+    *blocks = sms * (per_sm > 0 ? per_sm : 1);
+    return e;
 }
 
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,

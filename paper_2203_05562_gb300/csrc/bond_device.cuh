@@ -99,7 +99,7 @@ __device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K2
     const float det = f64_to_f32_rn(k00 * c00 + k01 * c01 + k02 * c02);
     const float t = (K00 + K11 + K22) * (1.0f / 3.0f);
     if (!(det > 1e-12f * t * t * t) || det == 0.0f) return false;
-    const float r = 1.0f / det;
+    const float r = __frcp_rn(det);                     // = 1 / det, correctly rounded
     inv[0] = f64_to_f32_rn(c00) * r; inv[1] = f64_to_f32_rn(c11) * r; inv[2] = f64_to_f32_rn(c22) * r;
     inv[3] = f64_to_f32_rn(c12) * r; inv[4] = f64_to_f32_rn(c02) * r; inv[5] = f64_to_f32_rn(c01) * r;
     return true;
@@ -366,7 +366,10 @@ __device__ __forceinline__ bool material_trial(const Real L[9], const Real sn[6]
     const Real a2 = h * (Real)0.5 * (L[2] - L[6]);
     const Real a3 = h * (Real)0.5 * (L[3] - L[1]);
     const Real aa = a1 * a1 + a2 * a2 + a3 * a3;
-    const Real kap = (Real)2 / ((Real)1 + aa);
+    // 2 / (1 + a.a); twice the correctly rounded reciprocal is the same number
+    Real kap;
+    if constexpr (F64) kap = (Real)2 / ((Real)1 + aa);
+    else kap = 2.0f * __frcp_rn(1.0f + aa);
     Real Q[9];
     Q[0] = (Real)1 + kap * (a1 * a1 - aa); Q[1] = kap * (-a3 + a1 * a2); Q[2] = kap * (a2 + a1 * a3);
     Q[3] = kap * (a3 + a2 * a1); Q[4] = (Real)1 + kap * (a2 * a2 - aa); Q[5] = kap * (-a1 + a2 * a3);
@@ -622,6 +625,15 @@ __device__ __forceinline__ void masked_add15(float tst, float thr, const float4&
           "f"(g3.z));
 }
 
+// butterfly sum within one warp: every lane ends with the same bits
+template <int NV, typename T>
+__device__ __forceinline__ void warp_sum(T (&v)[NV]) {
+#pragma unroll
+    for (int e = 0; e < NV; e++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], off);
+}
+
 // deterministic block sum: butterfly within warps, then warps in order.  The
 // butterfly leaves every lane with the same bits (each stage adds the same two
 // operands on both partners), so a one-warp block needs nothing more.
@@ -658,6 +670,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // the FP64 pipe.
 __device__ __forceinline__ int small_count(float c) {
     return __float_as_int(c + 12582912.0f) - 0x4B400000;
+}
+
+// A small integer (|x| < 2^22) as a float, exactly, by the inverse of
+// small_count: the conversion instruction issues on the FP64 pipe on GB300.
+__device__ __forceinline__ float small_float(int x) {
+    return __int_as_float(0x4B400000 + x) - 12582912.0f;
 }
 
 // FP32 sub-horizon membership test of member k (z_k = (zeta~_k, |zeta~_k|^2))
@@ -791,7 +809,7 @@ __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float
             float h0, l0, h1, l1;
             tc_split(f0[e], h0, l0);
             tc_split(f1[e], h1, l1);
-            phi[2 * e][kp] = tc_pack(h0, h1);
+            phi[2 * e][kp] = tc_pack(h0, h1);      // exact: 11 significant bits
             phi[2 * e + 1][kp] = tc_pack(l0, l1);
         }
         phi[30][kp] = tc_pack(f0[15], f1[15]);
@@ -881,6 +899,127 @@ __device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, int nb, int p
         }
     }
     __syncwarp();
+}
+
+// One warp, pass p of the receiver sums of the power-conjugate force state
+// (model 2): for receivers t = 32p .. 32p + 31, N_t = sum over senders q of
+// [t in S_q] M_q, with M_q = varpi sigma K^-1 of sender bond q (9 values,
+// row-major).  The mask element (t, q) is the sender's own FP32 test of
+// member t (member_test_lhs with q's bond terms), so it is the decision
+// the sender pass took.  phi holds M split into fp16 pairs (row 2f: high,
+// 2f + 1: low part of entry f, rows 18..23 zero) scaled by a power of two;
+// uM undoes it.  Writes F[r][0..8] = N of receiver 32p + r.
+__device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, int nb, int p, float hf2,
+                                                 const unsigned (*phi)[kTcPhiStride / 2],
+                                                 float (*F)[kTcF], float uM) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const int KT = (nb + 15) >> 4;
+    const int nm = KT - 2 * p >= 2 ? 2 : 1;
+    // member-side terms of this lane's receivers 32p + 16m + g (+ 8)
+    R4<float> zr[2][2];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int r = 32 * p + 16 * m + g + 8 * h;
+            zr[m][h].x = zr[m][h].y = zr[m][h].z = zr[m][h].w = 0.0f;
+            if (r < nb) zr[m][h] = s_z[r];
+        }
+    float acc[2][3][4];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int nt = 0; nt < 3; nt++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) acc[m][nt][e] = 0.0f;
+    const int lm = lane >> 3, lr = lane & 7;
+    const unsigned phi_base = (unsigned)__cvta_generic_to_shared(&phi[0][0]);
+    for (int kt = 0; kt < KT; kt++) {
+        const int c0 = 16 * kt + 2 * tq;
+        float mq[4][4];                                   // senders' bond terms
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const R4<float> z = s_z[c0 + (c & 1) + 8 * (c >> 1)];
+            mq[c][0] = -2.0f * z.x;
+            mq[c][1] = -2.0f * z.y;
+            mq[c][2] = -2.0f * z.z;
+            mq[c][3] = hf2 - z.w;
+        }
+        unsigned b[3][2], bx, by;
+        {
+            const int row = 8 * (lm >> 1) + lr;
+            const unsigned addr = phi_base + (unsigned)(row * kTcPhiStride + 16 * kt + 8 * (lm & 1)) * 2u;
+            tc_ldmatrix_x4(addr, b[0][0], b[0][1], b[1][0], b[1][1]);
+            const unsigned addr2 = phi_base + (unsigned)((16 + row) * kTcPhiStride + 16 * kt + 8 * (lm & 1)) * 2u;
+            tc_ldmatrix_x4(addr2, b[2][0], b[2][1], bx, by);   // rows 24..31 are not used
+        }
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            if (m >= nm) continue;
+            bool q[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    q[h][c] = member_test_lhs(zr[m][h].x, zr[m][h].y, zr[m][h].z, zr[m][h].w, mq[c][0],
+                                              mq[c][1], mq[c][2]) <= mq[c][3];
+            const unsigned a0 = tc_mask_pair(q[0][0], q[0][1]);
+            const unsigned a1 = tc_mask_pair(q[1][0], q[1][1]);
+            const unsigned a2 = tc_mask_pair(q[0][2], q[0][3]);
+            const unsigned a3 = tc_mask_pair(q[1][2], q[1][3]);
+#pragma unroll
+            for (int nt = 0; nt < 3; nt++) tc_mma(acc[m][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+        if (m >= nm) continue;
+#pragma unroll
+        for (int nt = 0; nt < 3; nt++) {
+            const int f = 4 * nt + tq;
+            if (f < 9) {
+                F[16 * m + g][f] = (acc[m][nt][0] + acc[m][nt][1]) * uM;
+                F[16 * m + g + 8][f] = (acc[m][nt][2] + acc[m][nt][3]) * uM;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// One warp: the senders' matrices sM[q][0..8] (q < nb) into phi for
+// tc_pass_receiver, scaled by a power of two below the largest |entry|;
+// returns the factor that undoes the scaling.  Rows 18..31 are zero, and so
+// are members [nb, 16 ceil(nb/16)).
+__device__ __forceinline__ float tc_build_sender_features(const float (*sM)[16], int nb,
+                                                          unsigned (*phi)[kTcPhiStride / 2]) {
+    const int lane = threadIdx.x & 31;
+    const int KT = (nb + 15) >> 4;
+    float mx = 0.0f;
+    for (int q = lane; q < nb; q += 32)
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+            const float a = fabsf(sM[q][e]);
+            if (a <= FLT_MAX) mx = fmaxf(mx, a);
+        }
+    mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+    const float sc = tc_scale(mx);
+    for (int kp = lane; kp < KT * 8; kp += 32) {
+        const int q0 = 2 * kp, q1 = 2 * kp + 1;
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+            const float v0 = q0 < nb ? sM[q0][e] * sc : 0.0f;
+            const float v1 = q1 < nb ? sM[q1][e] * sc : 0.0f;
+            float h0, l0, h1, l1;
+            tc_split(v0, h0, l0);
+            tc_split(v1, h1, l1);
+            phi[2 * e][kp] = tc_pack(h0, h1);
+            phi[2 * e + 1][kp] = tc_pack(l0, l1);
+        }
+#pragma unroll
+        for (int r = 18; r < 32; r++) phi[r][kp] = 0u;
+    }
+    __syncwarp();
+    return 1.0f / sc;
 }
 
 }  // namespace

@@ -75,6 +75,8 @@ struct StepConst {
     double pair_dc, pair_kappa;  // between points: delta_c / dx and C_s / (2 delta_c / dx)
     float pair_dcf, pair_kappaf; // the same in FP32
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
+    int tc_ppb, tc_blocks;       // tensor-core bond kernel: points per block; grid (0: one
+                                 // point per warp, else a persistent grid of that many blocks)
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;
@@ -279,6 +281,9 @@ cudaError_t launch_tforce_from_rev(const DevState<Real>& s, const StepConst& k, 
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,
                                  const int32_t* row_ptr, int npoints, int halt, double tol,
                                  cudaStream_t st);
+// blocks of one resident wave of the tensor-core bond kernel (force state
+// model 0 or 2, points per block ppb = 1 or 2) on the current device
+cudaError_t bond_tc_resident_blocks(int model, int ppb, int coupled, int* blocks);
 
 // ---- launchers (adjoint.cu) ----
 // one reverse step from the restored start state (predictor already

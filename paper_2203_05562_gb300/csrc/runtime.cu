@@ -104,6 +104,8 @@ int check_params(const ppm_params* p) {
     if (p->bond_tile != 0 && p->bond_tile != 32 && p->bond_tile != 64 && p->bond_tile != 128 &&
         p->bond_tile != 256)
         return PPM_EINVAL;
+    if (p->points_per_block < 0 || p->points_per_block > 2 || p->bond_grid < 0 || p->bond_grid > 2)
+        return PPM_EINVAL;
     if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
         return PPM_EINVAL;
     if ((p->bc != 0 && p->bc != 1) || !(p->load_rate >= 0) || !std::isfinite(p->load_rate))
@@ -362,16 +364,42 @@ int capture_segment(ppm_ctx* c, const DevState<Real>& s, int len, cudaGraphExec_
     return e == cudaSuccess ? PPM_OK : PPM_ECUDA;
 }
 
-// bond-kernel tile: time a full bond pass (with the time step, so the
-// constitutive update runs, but without committing the point state) with
-// 32, 64, 128 and 256 threads per point and keep the fastest
+// Launch shape of the bond pass: time a full bond pass (with the time step,
+// so the constitutive update runs, but without committing the point state)
+// for each candidate and keep the fastest.  Candidates: 32, 64, 128 and 256
+// threads per point; for the mixed path with a sub-horizon force state
+// (Eq. 51 or the power-conjugate one), 32 means the tensor-core kernel,
+// tried with one and two points per block, each with a grid that covers
+// every point once and with a persistent resident wave that loops over
+// the points.
+struct LaunchShape {
+    int tile, ppb, blocks;
+};
+
 template <typename Real>
 int autotune_tile(ppm_ctx* c, const DevState<Real>& s) {
-    const int tiles[4] = {32, 64, 128, 256};
+    LaunchShape cand[8];
+    int nc = 0;
+    const bool tc = sizeof(Real) == 4 && (c->k.model == 0 || c->k.model == 2);
+    if (tc) {
+        for (int ppb = 1; ppb <= 2; ppb++) {
+            int resident = 0;
+            CU(bond_tc_resident_blocks(c->k.model, ppb, c->k.coupled, &resident));
+            cand[nc++] = {32, ppb, 0};
+            cand[nc++] = {32, ppb, resident};
+        }
+    } else {
+        cand[nc++] = {32, 1, 0};
+    }
+    cand[nc++] = {64, 1, 0};
+    cand[nc++] = {128, 1, 0};
+    cand[nc++] = {256, 1, 0};
     float best = 1e30f;
-    int pick = 128;
-    for (int q = 0; q < 4; q++) {
-        c->k.tile = tiles[q];
+    LaunchShape pick = {128, 1, 0};
+    for (int q = 0; q < nc; q++) {
+        c->k.tile = cand[q].tile;
+        c->k.tc_ppb = cand[q].ppb;
+        c->k.tc_blocks = cand[q].blocks;
         CU(launch_bond<Real>(s, c->k, c->k.dt, 0, c->stream));      // warm
         CU(cudaEventRecord(c->ev[4], c->stream));
         for (int r = 0; r < 2; r++) CU(launch_bond<Real>(s, c->k, c->k.dt, 0, c->stream));
@@ -380,9 +408,11 @@ int autotune_tile(ppm_ctx* c, const DevState<Real>& s) {
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
         c->launches += 3;
-        if (ms < best) { best = ms; pick = tiles[q]; }
+        if (ms < best) { best = ms; pick = cand[q]; }
     }
-    c->k.tile = pick;
+    c->k.tile = pick.tile;
+    c->k.tc_ppb = pick.ppb;
+    c->k.tc_blocks = pick.blocks;
     return PPM_OK;
 }
 
@@ -807,6 +837,16 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
     k.ncols = c->ncols;
     k.max_family = z.max_family;
     k.tile = p->bond_tile ? p->bond_tile : 128;
+    k.tc_ppb = p->points_per_block == 2 ? 2 : 1;
+    k.tc_blocks = 0;
+    if (p->bond_grid == 2 && p->precision == PPM_MIXED) {
+        int resident = 0;
+        if (bond_tc_resident_blocks(p->model, k.tc_ppb, p->coupled, &resident) != cudaSuccess) {
+            delete c;
+            return PPM_ECUDA;
+        }
+        k.tc_blocks = resident;
+    }
     k.cap = c->cap;
     k.dxf = (float)k.dx;
     k.inv_dxf = (float)k.inv_dx;
@@ -967,6 +1007,8 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     out->pairs = (int64_t)h.pairs;
     out->returns_fp64 = (int64_t)h.ret64;
     out->bond_tile = c->k.tile;
+    out->points_per_block = c->k.tc_ppb;
+    out->bond_blocks = c->k.tc_blocks;
     out->halted_step = (int32_t)h.halted_step;
     out->unstable_step = (int32_t)h.unstable_step;
     out->launches = c->launches;

@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("energy_tol", C.c_double), ("plane_strain", C.c_int32),
         ("coupled", C.c_int32), ("porosity", C.c_double), ("rho_s", C.c_double),
         ("rho_w", C.c_double), ("wr_a1", C.c_double), ("wr_a2", C.c_double), ("wr_n", C.c_double),
+        ("points_per_block", C.c_int32), ("bond_grid", C.c_int32),
     ]
 
 
@@ -61,7 +62,7 @@ class Counters(C.Structure):
                 ("returns_fp64", C.c_int64), ("bond_tile", C.c_int32), ("halted_step", C.c_int32),
                 ("status", C.c_uint32), ("unstable_step", C.c_int32),
                 ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double),
-                ("W_kin0", C.c_double)]
+                ("W_kin0", C.c_double), ("points_per_block", C.c_int32), ("bond_blocks", C.c_int32)]
 
 
 _lib = None
@@ -118,11 +119,11 @@ def _check(rc: int, what: str):
 
 
 def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_family=0,
-                bond_tile=128) -> Params:
+                bond_tile=32, points_per_block=0, bond_grid=0) -> Params:
     p = Params()
     for name, _ in Params._fields_:
         if name in ("gravity", "precision", "use_graph", "max_family", "model", "pad_",
-                    "bond_tile"):
+                    "bond_tile", "points_per_block", "bond_grid"):
             continue
         if name in cfg:
             setattr(p, name, cfg[name])
@@ -137,6 +138,8 @@ def make_params(cfg: dict, precision=None, model=None, use_graph=True, max_famil
     p.use_graph = int(use_graph)
     p.max_family = int(cfg.get("max_family", max_family))
     p.bond_tile = int(cfg.get("bond_tile", bond_tile))
+    p.points_per_block = int(cfg.get("points_per_block", points_per_block))
+    p.bond_grid = int(cfg.get("bond_grid", bond_grid))
     return p
 
 
@@ -184,14 +187,15 @@ class Simulation:
     when ``columns`` (a list of dicts with nx, ny, nz, suction, M) is given."""
 
     def __init__(self, cfg: dict, columns=None, precision=None, model=None, device=None,
-                 use_graph=True, max_family=0, bond_tile=128):
+                 use_graph=True, max_family=0, bond_tile=32, points_per_block=0, bond_grid=0):
         import torch
 
         if not torch.cuda.is_available():
             raise PPMError("no CUDA device available")
         self._torch = torch
         L = library()
-        self.params = make_params(cfg, precision, model, use_graph, max_family, bond_tile)
+        self.params = make_params(cfg, precision, model, use_graph, max_family, bond_tile,
+                                  points_per_block, bond_grid)
         self.fp64 = self.params.precision == FP64
         self.dtype = np.float64 if self.fp64 else np.float32
         self.tdtype = torch.float64 if self.fp64 else torch.float32

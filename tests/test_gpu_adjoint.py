@@ -62,6 +62,25 @@ def test_adjoint_matches_oracle_finite_differences_on_the_10x10x20_column(precis
     assert np.allclose(g, fd, rtol=tol, atol=0), (g, fd)
 
 
+@pytest.mark.slow
+def test_fp64_adjoint_over_200_steps_matches_oracle_finite_differences():
+    # the length of the adjoint workload (200 steps, checkpoints every 20)
+    # on the 10x10x20 column that yields (p_c0 = 5 kPa): the FP64 GPU
+    # gradient against central differences (h = 1e-6 relative) of the FP64
+    # oracle's objective, to 1e-4 relative per parameter
+    cfg = pi.config(0, pc0=5e3)
+    v0 = pi.initial_velocity(cfg)
+    steps = 200
+    _, g = gpu_gradient(cfg, v0, steps, 20, "fp64")
+    fd = np.zeros(4)
+    for k, name in enumerate(NAMES):
+        h = 1e-6 * cfg[name]
+        fd[k] = (oracle.objective(dict(cfg, **{name: cfg[name] + h}), v0, steps) -
+                 oracle.objective(dict(cfg, **{name: cfg[name] - h}), v0, steps)) / (2 * h)
+    assert np.all(fd != 0.0)
+    assert np.allclose(g, fd, rtol=1e-4, atol=0), (g, fd)
+
+
 def test_adjoint_leaves_the_final_state():
     from paper_2203_05562_gb300 import Simulation
     cfg = pi.small_config(5, 5, 6, suction=50e3)

@@ -36,6 +36,50 @@ def test_family_bit_exact_fp64(amp):
     assert np.array_equal(rev, orev)
 
 
+def _pairs(rp, col):
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return set(zip(rows.tolist(), np.asarray(col).tolist()))
+
+
+@pytest.mark.parametrize("amp", [0.0, 0.3])
+def test_mixed_family_against_oracle_within_fp32_rounding_of_the_horizon(amp):
+    # The mixed path tests membership (Eq. 1) in FP32 lattice units,
+    # (I_j - I_i) + (u_j - u_i) / dx, against (delta / dx)^2 rounded to
+    # FP32.  On the same positions (the FP32 displacement, widened) the
+    # oracle decides in FP64.  The families must agree except for pairs
+    # whose FP64 distance lies within the FP32 rounding of that test of
+    # the horizon: each component carries at most about 3e-7 (its rounded
+    # difference and offset), the squared sum a few ulps of 9; 2e-5 of
+    # delta^2 / dx^2 bounds it.  Pairs planted at the horizon itself
+    # exercise the bound; the reverse index must be valid throughout.
+    from paper_2203_05562_gb300 import Simulation
+    cfg = pi.small_config(9, 8, 11)
+    dx, hf = cfg["dx"], cfg["horizon_factor"]
+    u = pi.perturbation(cfg, amp * dx, seed=7)
+    n = pi.num_points(cfg)
+    ijk = np.stack([np.arange(n) % 9, (np.arange(n) // 9) % 8, np.arange(n) // 72])
+    # plant pairs at |x_j - x_i| = delta along x (lattice offset 3) in a few rows
+    for (iy, iz) in ((2, 3), (5, 6), (4, 8)):
+        row = np.where((ijk[1] == iy) & (ijk[2] == iz))[0]
+        u[:, row] = 0.0
+        u[0, row[3:]] = (hf - 3.0) * dx           # points ix >= 3 shifted by delta - 3 dx
+    u32 = u.astype(np.float32)
+    sim = Simulation(cfg, precision="mixed")
+    sim.write("u", u32.astype(np.float64))
+    sim.build_families()
+    rp, col, rev = sim.read("row_ptr"), sim.read("col"), sim.read("rev")
+    sim.close()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    assert np.array_equal(rev[rev], np.arange(len(col)))
+    assert np.array_equal(col[rev], rows)
+    X = oracle.reference_positions(cfg) + u32.astype(np.float64)
+    orp, ocol, _ = oracle.family(X, hf * dx)
+    diff = _pairs(rp, col) ^ _pairs(orp, ocol)
+    r2 = np.array([((X[:, j] - X[:, i]) ** 2).sum() / dx ** 2 for (i, j) in diff])
+    assert np.all(np.abs(r2 - hf * hf) <= 2e-5 * hf * hf), (len(diff), r2)
+    assert len(diff) <= 2 * 3 * 6
+
+
 def test_family_config0_counts():
     cfg = pi.config(0)
     rp, col, rev = _family_gpu(cfg, np.zeros((3, pi.num_points(cfg))))
@@ -200,6 +244,27 @@ def test_bond_tiles_match_oracle(tile):
         assert sim.status()["bond_tile"] == tile
         err = state_errors(sim, run, norm=norm)
         assert err["u"] <= tol and err["sigma"] <= tol, (precision, err)
+
+
+@pytest.mark.parametrize("model", [0, 2])
+@pytest.mark.parametrize("ppb,grid", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_tensor_core_launch_shapes_match_oracle(model, ppb, grid):
+    # the mixed path's tensor-core bond kernel (32 threads per point) with
+    # one or two points per block, a grid over every point or a persistent
+    # resident wave; plastic bonds (suction 50 kPa) and rebuilds every 3 steps
+    from paper_2203_05562_gb300 import Simulation
+    cfg = pi.small_config(7, 6, 9, suction=50e3, rebuild_every=3, model=model)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=13)
+    run = oracle_run(cfg, 6, v0)
+    sim = Simulation(cfg, precision="mixed", bond_tile=32, points_per_block=ppb, bond_grid=grid)
+    sim.write("v", v0)
+    sim.step(6)
+    st = sim.status()
+    assert st["bond_tile"] == 32 and st["points_per_block"] == ppb
+    assert (st["bond_blocks"] > 0) == (grid == 2)
+    assert st["plastic"] > 0
+    err = state_errors(sim, run, norm=rel_l2)
+    assert err["u"] <= MIXED_TOL and err["sigma"] <= MIXED_TOL, err
 
 
 def test_autotuner_picks_a_tile_and_stays_correct():
