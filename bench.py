@@ -514,6 +514,7 @@ def main():
     # over the same warm-up and steps as the headline, on a fresh column ----
     st = sim.status()
     u_timed = sim.read("u")                       # the precision report compares it with FP64
+    steps_timed_run = int(st["steps"])            # warm-up, alignment to a rebuild, timed steps
     # Eq. 65 (reading R30) on the column at the end of the run, beside the step used
     critical = {"eq65_s": sim.critical_time_step(), "dt_used_s": sim.dt,
                 "note": "micro-modulus over bond length; stable for models 1 and 2 up to at least 2x"}
@@ -723,7 +724,7 @@ def main():
     # ---- the mixed path's error against FP64, per result ----
     precision = None
     if rank == 0 and not args.no_precision:
-        precision = precision_report(cfg, tile, u_timed, args.warmup + args.steps, oracle_state)
+        precision = precision_report(cfg, tile, u_timed, steps_timed_run, oracle_state)
 
     # HBM GB/s of both paths: algorithmic bytes per step x steps per second,
     # and the bond kernel's profiled DRAM bytes over its event-timed launch

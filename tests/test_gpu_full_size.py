@@ -93,3 +93,52 @@ def test_full_size_properties_of_the_1m_point_column():
     f = sim.read("fint").astype(np.float64)
     scale = np.abs(f).sum(axis=1)
     assert np.all(np.abs(f.sum(axis=1)) <= 1e-5 * scale)
+
+
+@pytest.mark.parametrize("shape", [dict(bond_tile=0), dict(bond_tile=32, bond_grid=2)])
+def test_ensemble_with_a_60000_point_column_after_one_step(shape):
+    # a batched ensemble (the workload's material and spacing) with a column
+    # at the upper end of the ensemble's sizes (30 x 30 x 66 = 59,400 points)
+    # and two small ones of other suctions and slopes, in the autotuned launch
+    # shape and in a persistent wave over all columns: the small columns
+    # against full oracle runs, the large one at sampled points against
+    # oracle patches, after one step (mixed path, 1e-4)
+    from paper_2203_05562_gb300 import Simulation
+    base = pi.config("ensemble_64_columns_mixed")
+    cols = [dict(nx=30, ny=30, nz=66, suction=35e3, M=1.3),
+            dict(nx=10, ny=12, nz=20, suction=5e3, M=1.05),
+            dict(nx=14, ny=14, nz=15, suction=48e3, M=1.38)]
+    ccfg = [dict(base, nx=c["nx"], ny=c["ny"], nz=c["nz"], suction=c["suction"], M=c["M"]) for c in cols]
+    v0s = [pi.initial_velocity(c, std=1e-4, seed=40 + q) for q, c in enumerate(ccfg)]
+    sim = Simulation(base, columns=cols, precision="mixed", **shape)
+    sim.write("v", np.concatenate(v0s, axis=1))
+    sim.step(1)
+    st = sim.status()
+    if shape.get("bond_grid") == 2:
+        assert st["bond_blocks"] > 0
+    got = {f: sim.read(f).astype(np.float64) for f in ("u", "v", "a", "sigma", "pc")}
+    offsets = np.cumsum([0] + [pi.num_points(c) for c in ccfg])
+    tol = 1e-4
+    for q, c in enumerate(ccfg):
+        sl = slice(offsets[q], offsets[q + 1])
+        sig0 = oracle.initial_stress(c)
+        if q > 0:                                     # the small columns, whole
+            run = oracle.Run(c, v0s[q], sig0=sig0)
+            run.step(1)
+            want = {"u": run.u, "v": run.v, "a": run.a, "sigma": run.sig, "pc": run.pc[None]}
+            for f, arr in want.items():
+                g = np.atleast_2d(got[f])[:, sl]
+                err = np.abs(g - arr).max() / (np.abs(arr).max() + 1e-300)
+                assert err <= tol, (q, f, err)
+            continue
+        for ijk in _samples(c, 5, seed=17):               # the 59,400-point column, sampled
+            dims, ids, ctr = _patch(c, ijk)
+            pcfg = dict(c, nx=dims[0], ny=dims[1], nz=dims[2])
+            run = oracle.Run(pcfg, v0s[q][:, ids], sig0=sig0[:, ids])
+            run.step(1)
+            want = {"u": run.u, "v": run.v, "a": run.a, "sigma": run.sig, "pc": run.pc[None]}
+            for f, arr in want.items():
+                arr = np.atleast_2d(arr)
+                g = np.atleast_2d(got[f])[:, offsets[q] + ids[ctr]]
+                err = np.abs(g - arr[:, ctr]).max() / (np.abs(arr).max() + 1e-300)
+                assert err <= tol, (ijk, f, err)
