@@ -585,6 +585,24 @@ def main():
                "rebuilds_timed": e1["rebuilds"] - e0["rebuilds"],
                "graph": "one CUDA graph per 50-step rebuild period; the bond pass one launch over all columns"}
         del esim0
+        # the cost of the kernel boundaries inside a step: a 64-point column run
+        # through the same graphs, whose kernels do almost no work
+        tcfg = pi.small_config(4, 4, 4, precision="mixed", rebuild_every=ecfg["rebuild_every"])
+        tsim0 = Simulation(tcfg, precision="mixed")
+        tsim0.step(ecfg["rebuild_every"])
+        torch.cuda.synchronize()
+        tsteps = 10 * ecfg["rebuild_every"]
+        eva.record(tsim0.stream)
+        tsim0.step(tsteps)
+        evb.record(tsim0.stream)
+        torch.cuda.synchronize()
+        floor_ms = eva.elapsed_time(evb) / tsteps
+        ens["step_floor_us"] = 1e3 * floor_ms
+        ens["step_floor_share"] = floor_ms / ens["ms_per_step"]
+        ens["step_floor_note"] = ("ms per step of a 64-point column through the same per-step graph "
+                                  "(predictor, bond, gather, energy launches; the family search every "
+                                  "rebuild period): the kernel boundaries one persistent launch would remove")
+        del tsim0
 
     # ---- large column (64x64x256, 1,048,576 points), mixed ----
     large = None

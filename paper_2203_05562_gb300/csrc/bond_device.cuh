@@ -41,67 +41,104 @@ __device__ __forceinline__ bool inverse_sym_fp64(const double k[6], double inv[6
     return true;
 }
 
-// Exact IEEE 754 re-encodings between binary32 and binary64 in integer
-// operations.  On GB300 the hardware conversions issue on the FP64 pipe at
-// the FP64 rate (about 1/64 of FP32); these take the integer and FP32 pipes.
-// binary32 -> binary64 is exact: the exponent is re-biased by 1023 - 127 =
-// 896 and the 23-bit fraction moves to the top of the 52-bit one; zero keeps
-// its sign; subnormal, infinite and NaN inputs (rare here) take the
-// hardware conversion.
-__device__ __forceinline__ double f32_to_f64_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned sign = u & 0x80000000u, mag = u & 0x7fffffffu;
-    if (mag - 0x00800000u < 0x7f000000u || mag == 0u) {
-        const unsigned hi = mag ? (sign | ((mag >> 3) + 0x38000000u)) : sign;
-        return __hiloint2double((int)hi, (int)(mag << 29));
-    }
-    return (double)f;
-}
-
-// binary64 -> binary32, round to nearest even: for results in the normal
-// binary32 range the top 23 fraction bits are kept and the 29 dropped bits
-// decide the rounding (above half: up; exactly half: up when the kept lsb
-// is odd); a carry out of the fraction moves into the exponent, and out of
-// the largest exponent into infinity, as the rounding rule requires.
-// Zero and binary64 subnormals give a signed zero; results that are
-// binary32 subnormal, and infinities and NaN, take the hardware conversion.
-__device__ __forceinline__ float f64_to_f32_rn(double d) {
-    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    const unsigned sign = hi & 0x80000000u, E = (hi >> 20) & 0x7ffu;
-    if (E - 897u < 254u) {
-        unsigned f = ((E - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-        const unsigned rem = lo & 0x1fffffffu;
-        f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
-        return __uint_as_float(sign | f);
-    }
-    if (E == 0u) return __uint_as_float(sign);
-    return (float)d;
-}
-
 // Mixed path: the cancellation-prone steps -- cofactors and determinant --
 // in FP64 from the FP32 sums; the degeneracy test, the reciprocal of the
-// determinant and the final scaling in FP32 (the result is FP32 either
-// way, so a full FP64 division would change it by at most an ulp).  The
-// conversions between the formats are the exact re-encodings above (the
-// same bits as the hardware's), so that only the 15 FP64 operations of the
-// cofactors and the determinant use the FP64 pipe.
-__device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K22, float K12,
-                                                  float K02, float K01, float inv[6]) {
-    const double k00 = f32_to_f64_exact(K00), k11 = f32_to_f64_exact(K11);
-    const double k22 = f32_to_f64_exact(K22), k12 = f32_to_f64_exact(K12);
-    const double k02 = f32_to_f64_exact(K02), k01 = f32_to_f64_exact(K01);
+// determinant and the final scaling in FP32 (the result is FP32 either way,
+// so a full FP64 division would change it by at most an ulp).
+//
+// On GB300 the hardware conversions between binary32 and binary64 issue on
+// the FP64 pipe at the FP64 rate (about 1/64 of FP32), so the tensor is first
+// brought to a range where both conversions are short integer re-encodings:
+// it is multiplied by the power of two that puts its largest |entry| in
+// [1, 2), and entries below 2^-40 of that are taken as zero (far below the
+// rounding of the FP32 sums they come from).  Every entry is then zero or a
+// normal binary32 number of at least 2^-40, exact in binary64; the product
+// of two entries is exact in binary64 with an ulp of at least 2^-126, so
+// every nonzero cofactor lies in [2^-126, 8], the normal binary32 range, and
+// a determinant below that range fails the degeneracy test (whose bound is
+// at least 1e-12 / 27 on the scaled tensor).  The re-encodings give the
+// hardware's bits (binary32 -> binary64 exact, binary64 -> binary32 round to
+// nearest even) and every scaling is by a power of two without overflow, so
+// the inverse is the one the unscaled steps give.  Tensors whose largest
+// |entry| lies outside [2^-30, 2^31) (or is not finite) take the unscaled
+// steps with the hardware conversions, out of line.
+
+// binary32 -> binary64 for |f| >= 2^-40 (a normal number: the exponent is
+// re-biased by 1023 - 127 = 896 and the 23-bit fraction moves to the top of
+// the 52-bit one), and a zero of the same sign for smaller |f|
+__device__ __forceinline__ double f32_to_f64_flushed(float f) {
+    const unsigned u = __float_as_uint(f);
+    const bool keep = (u & 0x7fffffffu) >= 0x2B800000u;          // |f| >= 2^-40
+    const unsigned hi = (u & 0x80000000u) | (keep ? ((u & 0x7fffffffu) >> 3) + 0x38000000u : 0u);
+    return __hiloint2double((int)hi, keep ? (int)(u << 29) : 0);
+}
+
+// binary64 -> binary32, round to nearest even, for zero and for |d| in the
+// normal binary32 range: a funnel shift keeps the top 23 fraction bits below
+// the exponent's low 9 bits, adding 2^30 re-biases that exponent (896 = 1024
+// - 128, modulo 2^9), the 29 dropped bits decide the rounding (above half:
+// up; exactly half: up when the kept lsb is odd), and a carry out of the
+// fraction moves into the exponent, as the rounding rule requires
+__device__ __forceinline__ float f64_to_f32_regular(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    unsigned f = __funnelshift_l(lo, hi, 3) + 0x40000000u;
+    const unsigned rem = lo & 0x1fffffffu;
+    f += (rem + (f & 1u)) > 0x10000000u ? 1u : 0u;
+    f = (hi & 0x7fffffffu) ? f : 0u;
+    return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// the unscaled steps with the hardware conversions (tensors outside the
+// range of the re-encodings: zero, non-finite, tiny or huge entries)
+__device__ __noinline__ bool inverse_sym_mixed_slow(float K00, float K11, float K22, float K12,
+                                                    float K02, float K01, float inv[6]) {
+    const double k00 = K00, k11 = K11, k22 = K22, k12 = K12, k02 = K02, k01 = K01;
     const double c00 = k11 * k22 - k12 * k12;
     const double c11 = k00 * k22 - k02 * k02;
     const double c22 = k00 * k11 - k01 * k01;
     const double c12 = k01 * k02 - k00 * k12;
     const double c02 = k01 * k12 - k02 * k11;
     const double c01 = k02 * k12 - k01 * k22;
-    const float det = f64_to_f32_rn(k00 * c00 + k01 * c01 + k02 * c02);
+    const float det = (float)(k00 * c00 + k01 * c01 + k02 * c02);
     const float t = (K00 + K11 + K22) * (1.0f / 3.0f);
     if (!(det > 1e-12f * t * t * t) || det == 0.0f) return false;
     const float r = __frcp_rn(det);                     // = 1 / det, correctly rounded
-    inv[0] = f64_to_f32_rn(c00) * r; inv[1] = f64_to_f32_rn(c11) * r; inv[2] = f64_to_f32_rn(c22) * r;
-    inv[3] = f64_to_f32_rn(c12) * r; inv[4] = f64_to_f32_rn(c02) * r; inv[5] = f64_to_f32_rn(c01) * r;
+    inv[0] = (float)c00 * r; inv[1] = (float)c11 * r; inv[2] = (float)c22 * r;
+    inv[3] = (float)c12 * r; inv[4] = (float)c02 * r; inv[5] = (float)c01 * r;
+    return true;
+}
+
+__device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K22, float K12,
+                                                  float K02, float K01, float inv[6]) {
+    // the largest |entry| by its bit pattern (NaN and infinity order above
+    // every finite value); the scaled path needs it in [2^-30, 2^31)
+    const unsigned m = max(max(max(__float_as_uint(K00) & 0x7fffffffu, __float_as_uint(K11) & 0x7fffffffu),
+                               max(__float_as_uint(K22) & 0x7fffffffu, __float_as_uint(K12) & 0x7fffffffu)),
+                           max(__float_as_uint(K02) & 0x7fffffffu, __float_as_uint(K01) & 0x7fffffffu));
+    if (m - 0x30800000u >= 0x1E800000u) return inverse_sym_mixed_slow(K00, K11, K22, K12, K02, K01, inv);
+    // 2^(127 - e) for 2^e <= max |entry| < 2^(e+1): the scaled maximum is in [1, 2)
+    const float sc = __uint_as_float((254u - (m >> 23)) << 23);
+    const float s00 = K00 * sc, s11 = K11 * sc, s22 = K22 * sc;
+    const float s12 = K12 * sc, s02 = K02 * sc, s01 = K01 * sc;
+    const double k00 = f32_to_f64_flushed(s00), k11 = f32_to_f64_flushed(s11);
+    const double k22 = f32_to_f64_flushed(s22), k12 = f32_to_f64_flushed(s12);
+    const double k02 = f32_to_f64_flushed(s02), k01 = f32_to_f64_flushed(s01);
+    const double c00 = k11 * k22 - k12 * k12;
+    const double c11 = k00 * k22 - k02 * k02;
+    const double c22 = k00 * k11 - k01 * k01;
+    const double c12 = k01 * k02 - k00 * k12;
+    const double c02 = k01 * k12 - k02 * k11;
+    const double c01 = k02 * k12 - k01 * k22;
+    const double det64 = k00 * c00 + k01 * c01 + k02 * c02;
+    // below the normal binary32 range, zero or negative: degenerate
+    if ((int)__double2hiint(det64) <= 0x38100000) return false;
+    const float det = f64_to_f32_regular(det64);
+    const float t = (s00 + s11 + s22) * (1.0f / 3.0f);
+    if (!(det > 1e-12f * t * t * t)) return false;
+    const float r = __frcp_rn(det) * sc;                // sc / det of the scaled tensor = 1 / det
+    inv[0] = f64_to_f32_regular(c00) * r; inv[1] = f64_to_f32_regular(c11) * r;
+    inv[2] = f64_to_f32_regular(c22) * r; inv[3] = f64_to_f32_regular(c12) * r;
+    inv[4] = f64_to_f32_regular(c02) * r; inv[5] = f64_to_f32_regular(c01) * r;
     return true;
 }
 
