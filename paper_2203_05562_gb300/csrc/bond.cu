@@ -620,7 +620,8 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
     // rows where plastic bonds park during their returns)
     __shared__ alignas(16) unsigned char s_yFs[PPB][kTcYF];
     __shared__ float s_Jms[PPB][CPL ? kTcRows : 1];   // coupled mode: the members' volume ratios
-    __shared__ alignas(16) unsigned s_phis[PPB][32][kTcPhiStride / 2];
+    __shared__ alignas(16) unsigned s_phis[PPB][kTcPhiWords];
+    __shared__ alignas(16) unsigned s_tws[PPB][4 * kTcRows];   // the test's member words
     // model 2: each sender's matrix M = varpi sigma K^-1 (and its park row)
     __shared__ alignas(16) float s_Ms[PPB][MODEL == 2 ? kTcRows : 1][16];
     R4<float>* s_z = s_zs[w];
@@ -628,7 +629,8 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
     R4<float>* s_y = reinterpret_cast<R4<float>*>(s_yFs[w]);
     float(*F)[kTcF] = reinterpret_cast<float(*)[kTcF]>(s_yFs[w]);
     float* s_Jm = s_Jms[w];
-    unsigned(*s_phi)[kTcPhiStride / 2] = s_phis[w];
+    unsigned* s_phi = s_phis[w];
+    unsigned* s_tw = s_tws[w];
 
     for (int i = blockIdx.x * PPB + w; i < k.npoints; i += gridDim.x * PPB) {
         const int r0 = s.row_ptr[i];
@@ -669,10 +671,9 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
             if constexpr (CPL) s_Jm[t] = s.J[j];
         }
         __syncwarp();
-        float uK, uA;
-        tc_build_features(s_z, s_y, nb, s_phi, uK, uA);   // s_y is free afterwards
-
-        const Real hf2 = k.hf2f;
+        float uK, uA, sT;
+        tc_build_features(s_z, s_y, nb, s_phi, s_tw, uK, uA, sT);   // s_y is free afterwards
+        const float sT2 = sT * sT, hf2s = k.hf2f * sT2;        // the test's scaled radius
         const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
         Real red[NRED];
 #pragma unroll
@@ -685,7 +686,7 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
             // the bond's reverse slot, issued before the sums so that its latency hides
             const int rb = (MODEL == 0 && t < nb) ? s.rev[r0 + t] : -1;
             __syncwarp();                             // the previous pass's rows are free
-            tc_pass_sums(s_z, nb, p, hf2, s_phi, F, uK, uA);
+            tc_pass_sums(s_z, s_tw, nb, p, sT2, hf2s, s_phi, F, uK, uA);
             if (t < nb) {
                 const float* Fr = F[lane];
                 const Real K00 = Fr[0], K11 = Fr[1], K22 = Fr[2], K12 = Fr[3], K02 = Fr[4], K01 = Fr[5];
@@ -716,7 +717,7 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
                 const int t = 32 * p + lane;
                 const int rb = t < nb ? s.rev[r0 + t] : -1;
                 __syncwarp();
-                tc_pass_receiver(s_z, nb, p, hf2, s_phi, F, uM);
+                tc_pass_receiver(s_z, s_tw, nb, p, sT2, hf2s, s_phi, F, uM);
                 if (t < nb) {
                     const float* Nr = F[lane];
                     const R4<Real> zt = s_z[t];

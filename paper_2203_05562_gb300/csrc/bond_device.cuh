@@ -719,7 +719,8 @@ __device__ __forceinline__ float small_float(int x) {
 // for bond j, with m_j = (-2 zeta~_j, hf^2 - |zeta~_j|^2):
 // |z_k|^2 - 2 z_k.z_j <= hf^2 - |z_j|^2, i.e. |zeta~_k - zeta~_j|^2 <= hf^2
 // (the sub-horizon test of Alg. 1), always with this rounding sequence, so
-// that every kernel that tests a pair takes the same decision.
+// that every scalar kernel that tests a pair takes the same decision (the
+// tensor-core kernel below has its own test, shared by its two passes).
 __device__ __forceinline__ float member_test_lhs(float zx, float zy, float zz, float zw, float mx,
                                                  float my, float mz) {
     return __fmaf_rn(zx, mx, __fmaf_rn(zy, my, __fmaf_rn(zz, mz, zw)));
@@ -730,31 +731,55 @@ __device__ __forceinline__ float member_test_lhs(float zx, float zy, float zz, f
 // ---------------------------------------------------------------------------
 // For one point with nb <= kTcRows bonds, the sums of every bond t over its
 // sub-horizon (Eq. 23-25, 55) form a product: F = Mask * Phi, where
-// Mask[t][k] = 1 if family member k lies in the sub-horizon of bond t (the
-// FP32 test above, the same decision as the scalar loop) and Phi[k] holds
-// the member's features zeta~ zeta~^T (6), Ydot zeta~^T (9) and 1 (count).
-// Mask is exact in fp16.  Each feature is scaled by a power of two into
-// [-1, 1] and split (Veltkamp, in FP32) into a part of 11 significant bits
-// and the remainder; both are fp16 terms, together within 2^-24 of the
-// largest scaled feature.  The products are exact and accumulate in FP32
-// (mma.sync m16n8k16; each lane builds its 16x16 mask fragment with the FP32
-// tests), so the sums have the accuracy of the FP32 sums they replace, with
-// another rounding order.  One warp does a point: the features once, then
-// 32 bonds (two 16-row tiles) per pass, just before their updates.
+// Mask[t][k] = 1 if family member k lies in the sub-horizon of bond t and
+// Phi[k] holds the member's features zeta~ zeta~^T (6), Ydot zeta~^T (9) and
+// 1 (count).  Mask is exact in fp16.  Each feature is scaled by a power of
+// two into [-1, 1] and split (Veltkamp, in FP32) into a part of 11
+// significant bits and the remainder; both are fp16 terms, together within
+// 2^-24 of the largest scaled feature.  The products are exact and
+// accumulate in FP32 (mma.sync m16n8k16), so the sums have the accuracy of
+// the FP32 sums they replace, with another rounding order.  One warp does a
+// point: the features once, then 32 bonds (two 16-row tiles) per pass, just
+// before their updates.
+//
+// The membership test itself is a tensor-core product too.  With zeta~
+// scaled by sT (a power of two that brings the point's largest |component|
+// into [1/2, 1)), d(t, k) = sT^2 (|zeta~_k - zeta~_t|^2 - hf^2)
+//   = sum_c (-2 c_t)(c_k) + w_k + e_t,  w = sT^2 |zeta~|^2, e_t = w_t - sT^2 hf^2,
+// and member k lies in the sub-horizon of bond t when d(t, k) < 0.  Each
+// scaled component is split c = c^h + c^l (c^h exact in fp16, c^l rounded
+// to fp16) and so is w; a bond row carries (-2c^h, -2c^h, -2c^l, -2c^l) per
+// component and (1, 1) against the member column's (c^h, c^l, c^h, c^l)
+// and (w^h, w^l): 14 of the 16 terms of one m16n8k16 product, whose
+// accumulator starts at e_t (FP32).  The split keeps each component to
+// 2^-24 and w to 2^-22 of the scaled range, so the decision carries about
+// the rounding of the FP32 test (member_test_lhs), from another sequence;
+// pairs within ~1e-6 of the sub-horizon radius may be decided differently
+// from the FP64 oracle, as with the FP32 test.  The signs of a 16 x 16 tile
+// of d become the mask fragment directly (the accumulator layout of the
+// product is the operand layout of the next one).  Both passes of the
+// power-conjugate force state take the same products (same operands, same
+// instruction), so every decision is taken once, bit for bit.
 constexpr int kTcRows = 128;        // bonds (and members) of a point summed this way
-constexpr int kTcPhiStride = 136;   // halfs per feature row: 16-byte rows, conflict-free ldmatrix
+constexpr int kTcPhiWords = 32 * 64;   // feature rows x member pairs (fp16 pairs)
 constexpr int kTcF = 17;            // floats per bond row of a pass's sums (odd: conflict-free)
 constexpr int kTcYF = (kTcRows * 16 > 32 * kTcF * 4) ? kTcRows * 16 : 32 * kTcF * 4;
+constexpr unsigned kTcOnes = 0x3C003C00u;   // the fp16 pair (1, 1)
+constexpr unsigned kTcFarWord = 0x7753u;    // the fp16 pair (30000, 0): a member in no sub-horizon
+constexpr float kTcFar = 30000.0f;          // and the accumulator start of a bond with no members
+
+// Word index of member pair kp (fp16 pair) in feature row f of phi.  Rows
+// are 256 bytes apart; the 16-byte chunk c of row f is stored at c ^ (f & 7),
+// so that the eight rows of one ldmatrix fall in eight different bank groups.
+__device__ __forceinline__ int tc_phi_word(int f, int kp) {
+    return f * 64 + ((((kp >> 2) ^ (f & 7)) << 2) | (kp & 3));
+}
 
 // 2^-(e+1) for 2^e <= m < 2^(e+1): m times it lies in [1/2, 1)
 __device__ __forceinline__ float tc_scale(float m) {
     const int e = (int)((__float_as_uint(m) >> 23) & 0xffu);
     if (e == 0 || e >= 253) return 1.0f;
     return __uint_as_float((unsigned)(253 - e) << 23);
-}
-
-__device__ __forceinline__ unsigned tc_mask_pair(bool lo, bool hi) {
-    return (lo ? 0x3C00u : 0u) | (hi ? 0x3C000000u : 0u);     // fp16 1.0 in each half
 }
 
 // two FP32 values as an fp16 pair (lo in the low half), one packed conversion
@@ -771,6 +796,12 @@ __device__ __forceinline__ void tc_split(float f, float& hi, float& lo) {
     lo = __fsub_rn(f, hi);
 }
 
+__device__ __forceinline__ unsigned tc_split_pack(float f) {
+    float h, l;
+    tc_split(f, h, l);
+    return tc_pack(h, l);
+}
+
 __device__ __forceinline__ void tc_mma(float (&c)[4], unsigned a0, unsigned a1, unsigned a2,
                                        unsigned a3, unsigned b0, unsigned b1) {
     asm volatile(
@@ -785,6 +816,43 @@ __device__ __forceinline__ void tc_ldmatrix_x4(unsigned addr, unsigned& r0, unsi
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(addr));
+}
+
+// the 8 x 8 matrix of fp16 pairs held as one mma fragment, transposed
+__device__ __forceinline__ unsigned tc_transpose8(unsigned a) {
+    unsigned d;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
+}
+
+// The mask pair of two test values: fp16 1.0 in the low half when lo < 0
+// (its sign bit set), in the high half when hi < 0.  The permute replicates
+// each sign bit over two bytes; the mask keeps the bits of 1.0.
+__device__ __forceinline__ unsigned tc_sign_pair(float lo, float hi) {
+    unsigned r;
+    asm("prmt.b32 %0, %1, %2, 0xFFBB;" : "=r"(r) : "r"(__float_as_uint(lo)), "r"(__float_as_uint(hi)));
+    return r & kTcOnes;
+}
+
+// The bond-side terms of row r of the test for this lane's column group tq
+// (rows of the product: tq < 3 component tq, tq == 3 the |zeta~|^2 terms):
+// first = the terms against the member's (c^h, c^l) in k-columns 2tq, 2tq + 1,
+// second = those in k-columns 2tq + 8, 2tq + 9, and the accumulator start e.
+// tw holds the member words (tc_build_features); a row without a finite,
+// representable bond vector (or a padding row) gets e = kTcFar: no members.
+__device__ __forceinline__ void tc_bond_terms(const unsigned* tw, const R4<float>* s_z, int r, int tq,
+                                              float sT2, float hf2s, unsigned& first,
+                                              unsigned& second, float& e) {
+    const unsigned wq = tw[4 * r + tq], ww = tw[4 * r + 3];
+    unsigned dh, dl;
+    asm("prmt.b32 %0, %1, %1, 0x1010;" : "=r"(dh) : "r"(wq));   // (c^h, c^h)
+    asm("prmt.b32 %0, %1, %1, 0x3232;" : "=r"(dl) : "r"(wq));   // (c^l, c^l)
+    const __half2 m2 = __float2half2_rn(-2.0f);                  // exact products
+    const __half2 ph = __hmul2(*reinterpret_cast<const __half2*>(&dh), m2);
+    const __half2 pl = __hmul2(*reinterpret_cast<const __half2*>(&dl), m2);
+    first = tq < 3 ? *reinterpret_cast<const unsigned*>(&ph) : kTcOnes;
+    second = tq < 3 ? *reinterpret_cast<const unsigned*>(&pl) : 0u;
+    e = ww == kTcFarWord ? kTcFar : __fmaf_rn(s_z[r].w, sT2, -hf2s);
 }
 
 // The 15 scaled features and the count of member k (all zero for a padding
@@ -815,11 +883,15 @@ __device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R
 
 // One warp: the member features of a point into phi (row 2f: the high part
 // of feature f, row 2f + 1: the low part, 32 rows of fp16 pairs along the
-// members), and the factors uK, uA that undo the scaling of the K~ and A~
-// sums.  Members [nb, 16 ceil(nb/16)) of s_z are zeroed (tile padding).
+// members), the factors uK, uA that undo the scaling of the K~ and A~ sums,
+// the member words of the test into tw (4 per member: (c^h, c^l) of the
+// three scaled components and of w; kTcFarWord in the last for a member in
+// no sub-horizon, zeros before it) and the test's scale sT.  Members
+// [nb, 16 ceil(nb/16)) are padding: zero features, far words, and zeroed
+// in s_z.
 __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float>* s_y, int nb,
-                                                  unsigned (*phi)[kTcPhiStride / 2], float& uK,
-                                                  float& uA) {
+                                                  unsigned* phi, unsigned* tw, float& uK,
+                                                  float& uA, float& sT) {
     const int lane = threadIdx.x & 31;
     const int KT = (nb + 15) >> 4;
     // largest |component| of zeta~ and of Ydot over the members with finite values
@@ -837,6 +909,8 @@ __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float
     const float sK = tc_scale(mz * mz), sA = tc_scale(mz * my);
     uK = 1.0f / sK;                                      // powers of two: exact
     uA = 1.0f / sA;
+    sT = tc_scale(mz);
+    const float sT2 = sT * sT;
     for (int kp = lane; kp < KT * 8; kp += 32) {
         float f0[16], f1[16];
         tc_member_features(s_z, s_y, 2 * kp, nb, sK, sA, f0);
@@ -846,11 +920,22 @@ __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float
             float h0, l0, h1, l1;
             tc_split(f0[e], h0, l0);
             tc_split(f1[e], h1, l1);
-            phi[2 * e][kp] = tc_pack(h0, h1);      // exact: 11 significant bits
-            phi[2 * e + 1][kp] = tc_pack(l0, l1);
+            phi[tc_phi_word(2 * e, kp)] = tc_pack(h0, h1);      // exact: 11 significant bits
+            phi[tc_phi_word(2 * e + 1, kp)] = tc_pack(l0, l1);
         }
-        phi[30][kp] = tc_pack(f0[15], f1[15]);
-        phi[31][kp] = 0u;
+        phi[tc_phi_word(30, kp)] = tc_pack(f0[15], f1[15]);
+        phi[tc_phi_word(31, kp)] = 0u;
+    }
+    for (int k = lane; k < KT * 16; k += 32) {
+        uint4 W = make_uint4(0u, 0u, 0u, kTcFarWord);
+        if (k < nb) {
+            const R4<float> z = s_z[k];
+            const float cx = z.x * sT, cy = z.y * sT, cz = z.z * sT, cw = z.w * sT2;
+            // comparisons with NaN are false: such a member stays far
+            if (fabsf(cx) < 2.0f && fabsf(cy) < 2.0f && fabsf(cz) < 2.0f && cw < 16.0f)
+                W = make_uint4(tc_split_pack(cx), tc_split_pack(cy), tc_split_pack(cz), tc_split_pack(cw));
+        }
+        reinterpret_cast<uint4*>(tw)[k] = W;
     }
     __syncwarp();
     for (int k = nb + lane; k < KT * 16; k += 32) {
@@ -864,26 +949,26 @@ __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float
 // One warp, pass p: the sums of bonds 32p .. 32p + 31 (row tiles 2p, 2p + 1)
 // into F[0..31][0..15]: F[r][0..5] = K~ (xx yy zz yz xz xy), F[r][6..14] = A~
 // (row-major, A_rc = sum Ydot_r zeta~_c), F[r][15] = |S| of bond 32p + r.
-__device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, int nb, int p, float hf2,
-                                             const unsigned (*phi)[kTcPhiStride / 2],
+// hf2s = sT^2 hf^2.
+__device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, const unsigned* tw, int nb, int p,
+                                             float sT2, float hf2s, const unsigned* phi,
                                              float (*F)[kTcF], float uK, float uA) {
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     const int KT = (nb + 15) >> 4;
     const int nm = KT - 2 * p >= 2 ? 2 : 1;              // row tiles with bonds in this pass
-    // bond-side terms of the test for this lane's rows 32p + 16m + g (+ 8)
-    float mj[2][2][4];
+    // the test's bond-side terms of this lane's rows 32p + 16m + g (+ 8):
+    // ta[m] = (a0, a1, a2, a3) of the product, te[m] = accumulator starts
+    unsigned ta[2][4];
+    float te[2][2];
 #pragma unroll
     for (int m = 0; m < 2; m++)
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            const int r = 32 * p + 16 * m + g + 8 * h;
-            R4<float> z;
-            z.x = z.y = z.z = z.w = 0.0f;
-            if (r < nb) z = s_z[r];
-            mj[m][h][0] = -2.0f * z.x;
-            mj[m][h][1] = -2.0f * z.y;
-            mj[m][h][2] = -2.0f * z.z;
-            mj[m][h][3] = hf2 - z.w;
+            ta[m][h] = ta[m][2 + h] = 0u;
+            te[m][h] = kTcFar;
+            if (m < nm)
+                tc_bond_terms(tw, s_z, 32 * p + 16 * m + g + 8 * h, tq, sT2, hf2s, ta[m][h],
+                              ta[m][2 + h], te[m][h]);
         }
     float acc[2][4][4];
 #pragma unroll
@@ -894,32 +979,29 @@ __device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, int nb, int p
             for (int e = 0; e < 4; e++) acc[m][nt][e] = 0.0f;
     // ldmatrix rows: lanes 8q .. 8q + 7 address matrix q = (n-tile q/2, k half q%2)
     const int lm = lane >> 3, lr = lane & 7;
-    const unsigned phi_base = (unsigned)__cvta_generic_to_shared(&phi[0][0]);
+    const unsigned phi_base = (unsigned)__cvta_generic_to_shared(phi);
     for (int kt = 0; kt < KT; kt++) {
-        const int c0 = 16 * kt + 2 * tq;
-        const R4<float> z0 = s_z[c0], z1 = s_z[c0 + 1], z2 = s_z[c0 + 8], z3 = s_z[c0 + 9];
+        // the test's member-side terms of members 16kt + g and 16kt + 8 + g
+        const unsigned w0 = tw[4 * (16 * kt + g) + tq], w1 = tw[4 * (16 * kt + 8 + g) + tq];
+        const unsigned v0 = tq < 3 ? w0 : 0u, v1 = tq < 3 ? w1 : 0u;
         unsigned b[4][2];
 #pragma unroll
         for (int np = 0; np < 2; np++) {
             const int row = 8 * (2 * np + (lm >> 1)) + lr;
-            const unsigned addr = phi_base + (unsigned)(row * kTcPhiStride + 16 * kt + 8 * (lm & 1)) * 2u;
+            const unsigned addr = phi_base + 4u * (unsigned)tc_phi_word(row, 8 * kt + 4 * (lm & 1));
             tc_ldmatrix_x4(addr, b[2 * np][0], b[2 * np][1], b[2 * np + 1][0], b[2 * np + 1][1]);
         }
 #pragma unroll
         for (int m = 0; m < 2; m++) {
             if (m >= nm) continue;                       // warp-uniform
-            bool q[2][4];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                q[h][0] = member_test_lhs(z0.x, z0.y, z0.z, z0.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
-                q[h][1] = member_test_lhs(z1.x, z1.y, z1.z, z1.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
-                q[h][2] = member_test_lhs(z2.x, z2.y, z2.z, z2.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
-                q[h][3] = member_test_lhs(z3.x, z3.y, z3.z, z3.w, mj[m][h][0], mj[m][h][1], mj[m][h][2]) <= mj[m][h][3];
-            }
-            const unsigned a0 = tc_mask_pair(q[0][0], q[0][1]);   // row g, columns 2tq, 2tq + 1
-            const unsigned a1 = tc_mask_pair(q[1][0], q[1][1]);   // row g + 8
-            const unsigned a2 = tc_mask_pair(q[0][2], q[0][3]);   // row g, columns 2tq + 8, 2tq + 9
-            const unsigned a3 = tc_mask_pair(q[1][2], q[1][3]);   // row g + 8
+            float d0[4] = {te[m][0], te[m][0], te[m][1], te[m][1]};
+            float d1[4] = {te[m][0], te[m][0], te[m][1], te[m][1]};
+            tc_mma(d0, ta[m][0], ta[m][1], ta[m][2], ta[m][3], w0, v0);   // members 16kt + 0..7
+            tc_mma(d1, ta[m][0], ta[m][1], ta[m][2], ta[m][3], w1, v1);   // members 16kt + 8..15
+            const unsigned a0 = tc_sign_pair(d0[0], d0[1]);   // row g, columns 2tq, 2tq + 1
+            const unsigned a1 = tc_sign_pair(d0[2], d0[3]);   // row g + 8
+            const unsigned a2 = tc_sign_pair(d1[0], d1[1]);   // row g, columns 2tq + 8, 2tq + 9
+            const unsigned a3 = tc_sign_pair(d1[2], d1[3]);   // row g + 8
 #pragma unroll
             for (int nt = 0; nt < 4; nt++) tc_mma(acc[m][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
         }
@@ -941,26 +1023,27 @@ __device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, int nb, int p
 // One warp, pass p of the receiver sums of the power-conjugate force state
 // (model 2): for receivers t = 32p .. 32p + 31, N_t = sum over senders q of
 // [t in S_q] M_q, with M_q = varpi sigma K^-1 of sender bond q (9 values,
-// row-major).  The mask element (t, q) is the sender's own FP32 test of
-// member t (member_test_lhs with q's bond terms), so it is the decision
-// the sender pass took.  phi holds M split into fp16 pairs (row 2f: high,
-// 2f + 1: low part of entry f, rows 18..23 zero) scaled by a power of two;
-// uM undoes it.  Writes F[r][0..8] = N of receiver 32p + r.
-__device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, int nb, int p, float hf2,
-                                                 const unsigned (*phi)[kTcPhiStride / 2],
+// row-major).  The mask element (t, q) is the sender pass's own decision:
+// the test tile is taken with the senders as rows and the receivers as
+// columns, exactly as tc_pass_sums took it (same operands, same product),
+// and its mask fragments are transposed (movmatrix).  phi holds M split into
+// fp16 pairs (row 2f: high, 2f + 1: low part of entry f, rows 18..23 zero)
+// scaled by a power of two; uM undoes it.  Writes F[r][0..8] = N of
+// receiver 32p + r.
+__device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, const unsigned* tw, int nb,
+                                                 int p, float sT2, float hf2s, const unsigned* phi,
                                                  float (*F)[kTcF], float uM) {
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     const int KT = (nb + 15) >> 4;
     const int nm = KT - 2 * p >= 2 ? 2 : 1;
-    // member-side terms of this lane's receivers 32p + 16m + g (+ 8)
-    R4<float> zr[2][2];
+    // the test's member-side terms of this lane's receivers 32p + 16m + 8n + g
+    unsigned rw[2][2], rv[2][2];
 #pragma unroll
     for (int m = 0; m < 2; m++)
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int r = 32 * p + 16 * m + g + 8 * h;
-            zr[m][h].x = zr[m][h].y = zr[m][h].z = zr[m][h].w = 0.0f;
-            if (r < nb) zr[m][h] = s_z[r];
+        for (int n = 0; n < 2; n++) {
+            rw[m][n] = m < nm ? tw[4 * (32 * p + 16 * m + 8 * n + g) + tq] : 0u;
+            rv[m][n] = tq < 3 ? rw[m][n] : 0u;
         }
     float acc[2][3][4];
 #pragma unroll
@@ -970,40 +1053,33 @@ __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, int nb, i
 #pragma unroll
             for (int e = 0; e < 4; e++) acc[m][nt][e] = 0.0f;
     const int lm = lane >> 3, lr = lane & 7;
-    const unsigned phi_base = (unsigned)__cvta_generic_to_shared(&phi[0][0]);
+    const unsigned phi_base = (unsigned)__cvta_generic_to_shared(phi);
     for (int kt = 0; kt < KT; kt++) {
-        const int c0 = 16 * kt + 2 * tq;
-        float mq[4][4];                                   // senders' bond terms
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const R4<float> z = s_z[c0 + (c & 1) + 8 * (c >> 1)];
-            mq[c][0] = -2.0f * z.x;
-            mq[c][1] = -2.0f * z.y;
-            mq[c][2] = -2.0f * z.z;
-            mq[c][3] = hf2 - z.w;
-        }
+        // the test's bond-side terms of senders 16kt + g and 16kt + 8 + g
+        unsigned sa[4];
+        float se[2];
+        tc_bond_terms(tw, s_z, 16 * kt + g, tq, sT2, hf2s, sa[0], sa[2], se[0]);
+        tc_bond_terms(tw, s_z, 16 * kt + 8 + g, tq, sT2, hf2s, sa[1], sa[3], se[1]);
         unsigned b[3][2], bx, by;
         {
             const int row = 8 * (lm >> 1) + lr;
-            const unsigned addr = phi_base + (unsigned)(row * kTcPhiStride + 16 * kt + 8 * (lm & 1)) * 2u;
+            const unsigned addr = phi_base + 4u * (unsigned)tc_phi_word(row, 8 * kt + 4 * (lm & 1));
             tc_ldmatrix_x4(addr, b[0][0], b[0][1], b[1][0], b[1][1]);
-            const unsigned addr2 = phi_base + (unsigned)((16 + row) * kTcPhiStride + 16 * kt + 8 * (lm & 1)) * 2u;
+            const unsigned addr2 = phi_base + 4u * (unsigned)tc_phi_word(16 + row, 8 * kt + 4 * (lm & 1));
             tc_ldmatrix_x4(addr2, b[2][0], b[2][1], bx, by);   // rows 24..31 are not used
         }
 #pragma unroll
         for (int m = 0; m < 2; m++) {
             if (m >= nm) continue;
-            bool q[2][4];
-#pragma unroll
-            for (int h = 0; h < 2; h++)
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    q[h][c] = member_test_lhs(zr[m][h].x, zr[m][h].y, zr[m][h].z, zr[m][h].w, mq[c][0],
-                                              mq[c][1], mq[c][2]) <= mq[c][3];
-            const unsigned a0 = tc_mask_pair(q[0][0], q[0][1]);
-            const unsigned a1 = tc_mask_pair(q[1][0], q[1][1]);
-            const unsigned a2 = tc_mask_pair(q[0][2], q[0][3]);
-            const unsigned a3 = tc_mask_pair(q[1][2], q[1][3]);
+            float d0[4] = {se[0], se[0], se[1], se[1]};
+            float d1[4] = {se[0], se[0], se[1], se[1]};
+            tc_mma(d0, sa[0], sa[1], sa[2], sa[3], rw[m][0], rv[m][0]);   // receivers 0..7 of the tile
+            tc_mma(d1, sa[0], sa[1], sa[2], sa[3], rw[m][1], rv[m][1]);   // receivers 8..15
+            // the senders' mask (rows q, columns t) in four 8 x 8 blocks, transposed
+            const unsigned f0 = tc_sign_pair(d0[0], d0[1]), f1 = tc_sign_pair(d0[2], d0[3]);
+            const unsigned f2 = tc_sign_pair(d1[0], d1[1]), f3 = tc_sign_pair(d1[2], d1[3]);
+            const unsigned a0 = tc_transpose8(f0), a1 = tc_transpose8(f2);
+            const unsigned a2 = tc_transpose8(f1), a3 = tc_transpose8(f3);
 #pragma unroll
             for (int nt = 0; nt < 3; nt++) tc_mma(acc[m][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
         }
@@ -1028,7 +1104,7 @@ __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, int nb, i
 // returns the factor that undoes the scaling.  Rows 18..31 are zero, and so
 // are members [nb, 16 ceil(nb/16)).
 __device__ __forceinline__ float tc_build_sender_features(const float (*sM)[16], int nb,
-                                                          unsigned (*phi)[kTcPhiStride / 2]) {
+                                                          unsigned* phi) {
     const int lane = threadIdx.x & 31;
     const int KT = (nb + 15) >> 4;
     float mx = 0.0f;
@@ -1049,11 +1125,11 @@ __device__ __forceinline__ float tc_build_sender_features(const float (*sM)[16],
             float h0, l0, h1, l1;
             tc_split(v0, h0, l0);
             tc_split(v1, h1, l1);
-            phi[2 * e][kp] = tc_pack(h0, h1);
-            phi[2 * e + 1][kp] = tc_pack(l0, l1);
+            phi[tc_phi_word(2 * e, kp)] = tc_pack(h0, h1);
+            phi[tc_phi_word(2 * e + 1, kp)] = tc_pack(l0, l1);
         }
 #pragma unroll
-        for (int r = 18; r < 32; r++) phi[r][kp] = 0u;
+        for (int r = 18; r < 32; r++) phi[tc_phi_word(r, kp)] = 0u;
     }
     __syncwarp();
     return 1.0f / sc;
