@@ -469,6 +469,8 @@ def main():
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + steps of the mixed path only (for ncu captures)")
+    ap.add_argument("--profile-model", type=int, default=0, choices=[0, 1, 2],
+                    help="the force state --profile-only runs (0: Eq. 51, 1: standard, 2: power-conjugate)")
     ap.add_argument("--profile-workload", default=WORKLOAD,
                     choices=[WORKLOAD, "large_64x64x256_mixed"],
                     help="the column --profile-only runs")
@@ -495,7 +497,8 @@ def main():
     if args.profile_only:
         from paper_2203_05562_gb300 import Simulation
         pcfg = pi.config(args.profile_workload)
-        sim = Simulation(pcfg, precision="mixed", use_graph=False, bond_tile=args.tile)
+        sim = Simulation(pcfg, precision="mixed", model=args.profile_model, use_graph=False,
+                         bond_tile=args.tile)
         sim.write("v", pi.initial_velocity(pcfg))
         sim.step(args.warmup + args.steps)
         torch.cuda.synchronize()
@@ -538,6 +541,18 @@ def main():
     rp = tsim.read("row_ptr")
     fam_sq = float(np.sum(np.diff(rp).astype(np.float64) ** 2))
     del tsim
+    # every launch shape of the bond pass on the same steps (the autotuner's
+    # candidates for this workload): event-timed mean ms per bond launch
+    shape_ms = {}
+    for name, kw in (("warp_tensor_core_32", dict(bond_tile=32, points_per_block=1, bond_grid=1)),
+                     ("warp_tensor_core_32_persistent", dict(bond_tile=32, points_per_block=1, bond_grid=2)),
+                     ("tensor_memory_tcgen05_128", dict(bond_tile=128)),
+                     ("scalar_64", dict(bond_tile=64))):
+        ssim = Simulation(cfg, precision="mixed", **kw)
+        ssim.write("v", pi.initial_velocity(cfg))
+        ssim.step(args.warmup + align_to_rebuild(args.warmup, cfg["rebuild_every"]))
+        shape_ms[name] = ssim.step_timed(args.steps)[1] / args.steps
+        del ssim
     flops = FLOPS_TEST * fam_sq + FLOPS_PAIR * pairs_per_step
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -556,7 +571,8 @@ def main():
                 "peak_nominal": nominal_tflops, "frac_of_nominal": achieved / nominal_tflops,
                 "nominal_kind": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max SM clock)",
                 "flops_per_launch": flops,
-                "bond_kernel_ms": bond_ms, "gather_ms": phase[2] / nph,
+                "bond_kernel_ms": bond_ms, "bond_kernel_ms_by_launch_shape": shape_ms,
+                "gather_ms": phase[2] / nph,
                 "predictor_family_ms": phase[0] / nph}
 
     # ---- batched ensemble: 64 columns in one context, whole rebuild periods as graphs ----

@@ -55,6 +55,9 @@ extern "C" {
 #define PPM_STATUS_UNSTABLE      32u  /* energy balance of Eq. 69 above 1e-2        */
 #define PPM_STATUS_HALTED        64u  /* halt_on_unstable: the steps after the one
                                          whose Eq. 69 check failed did nothing   */
+#define PPM_STATUS_TC_TIMEOUT   128u  /* a tensor-memory bond pass stopped waiting
+                                         for its products: points it had not
+                                         reached kept their state                */
 
 /* precision of the path */
 #define PPM_FP64  0   /* everything in FP64                                     */
@@ -107,7 +110,11 @@ typedef struct {
     int32_t bond_tile;           /* bond-kernel threads per point: 32, 64, 128,
                                     256, or 0 to time each on the first call's
                                     bond pass and keep the fastest (results
-                                    are bitwise reproducible for a fixed tile) */
+                                    are bitwise reproducible for a fixed tile).
+                                    PPM_MIXED with model 0 outside the coupled
+                                    mode: 32 is the warp tensor-core kernel
+                                    and 128 the tensor-memory (tcgen05) one,
+                                    one thread per bond                       */
     int32_t bc;                  /* boundary conditions: 0 = base layer iz = 0
                                     fixed (the column collapse); 1 = uniaxial
                                     compression along x (Sec. 4.1): the

@@ -74,7 +74,7 @@ __global__ void k_predictor(DevState<Real> s, StepConst k) {
 // the member's volume ratio (coupled mode), K (xx yy zz yz xz xy), A (row-
 // major) and cntr = |S_b| its sums, (mjx, mjy, mjz, thj): the terms of its
 // membership test, park: a 16-entry row the thread owns (FP32 path).
-template <typename Real, int MODEL, bool CPL, int NRED>
+template <typename Real, int MODEL, bool CPL, int NRED, int SMW = 16>
 __device__ __forceinline__ void bond_epilogue(
     const DevState<Real>& s, const StepConst& k, int i, int r0, int t, int rb, const R4<Real>& zj,
     Real Jj, Real K00, Real K11, Real K22, Real K12, Real K02, Real K01, Real A00, Real A01,
@@ -104,7 +104,7 @@ __device__ __forceinline__ void bond_epilogue(
         } else {
 #pragma unroll
             for (int e = 0; e < 9; e++) sM[e] = (Real)0;
-            if constexpr (!F64) {
+            if constexpr (!F64 && SMW >= 13) {
                 sM[9] = mjx; sM[10] = mjy; sM[11] = mjz; sM[12] = thj;
             }
         }
@@ -132,7 +132,7 @@ __device__ __forceinline__ void bond_epilogue(
                 // the bond waits in shared memory while the return runs, so
                 // that none of it is held in registers across the return's
                 // calls (the compiler barriers keep it from being forwarded)
-                Real* pk = (MODEL == 2) ? sM : park;
+                Real* pk = (MODEL == 2 && SMW >= 14) ? sM : park;
 #pragma unroll
                 for (int c = 0; c < 6; c++) pk[c] = st[c];
 #pragma unroll
@@ -145,7 +145,7 @@ __device__ __forceinline__ void bond_epilogue(
                 for (int c = 0; c < 6; c++) stp[c] = pk[c];
                 material_return<Real>(stp, pc_i, k, cc.M, cc.Mf, bs);
                 asm volatile("" ::: "memory");
-                const Real* q = (MODEL == 2) ? sM : park;
+                const Real* q = (MODEL == 2 && SMW >= 14) ? sM : park;
                 Ki[0] = q[6]; Ki[1] = q[11]; Ki[2] = q[10];
                 Ki[3] = q[11]; Ki[4] = q[7]; Ki[5] = q[9];
                 Ki[6] = q[10]; Ki[7] = q[9]; Ki[8] = q[8];
@@ -174,25 +174,38 @@ __device__ __forceinline__ void bond_epilogue(
     const Real S[9] = {bs.sig[0] + Srs, bs.sig[5], bs.sig[4],
                        bs.sig[5], bs.sig[1] + Srs, bs.sig[3],
                        bs.sig[4], bs.sig[3], bs.sig[2] + Srs};
-    Real SK[9];
+    Real SK[9];          // varpi S K^-1 (the FP64 path's force state; model 2's sender matrix)
+    if constexpr (MODEL == 2 || sizeof(Real) == 8) {
 #pragma unroll
-    for (int r = 0; r < 3; r++)
+        for (int r = 0; r < 3; r++)
 #pragma unroll
-        for (int c = 0; c < 3; c++)
-            SK[r * 3 + c] = varpi * (S[r * 3 + 0] * Ki[0 * 3 + c] + S[r * 3 + 1] * Ki[1 * 3 + c] +
-                                     S[r * 3 + 2] * Ki[2 * 3 + c]);
+            for (int c = 0; c < 3; c++)
+                SK[r * 3 + c] = varpi * (S[r * 3 + 0] * Ki[0 * 3 + c] + S[r * 3 + 1] * Ki[1 * 3 + c] +
+                                         S[r * 3 + 2] * Ki[2 * 3 + c]);
+    }
     if constexpr (MODEL != 2) {
         // force state on the bond itself (Eq. 31-32, 51)
-        const Real T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
-        const Real T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
-        const Real T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+        Real T0, T1, T2;
+        if constexpr (sizeof(Real) == 8) {
+            T0 = SK[0] * zj.x + SK[1] * zj.y + SK[2] * zj.z;
+            T1 = SK[3] * zj.x + SK[4] * zj.y + SK[5] * zj.z;
+            T2 = SK[6] * zj.x + SK[7] * zj.y + SK[8] * zj.z;
+        } else {
+            // mixed path: T = varpi S (K^-1 zeta~), 18 products instead of 36
+            const Real y0 = Ki[0] * zj.x + Ki[1] * zj.y + Ki[2] * zj.z;
+            const Real y1 = Ki[3] * zj.x + Ki[4] * zj.y + Ki[5] * zj.z;
+            const Real y2 = Ki[6] * zj.x + Ki[7] * zj.y + Ki[8] * zj.z;
+            T0 = varpi * (S[0] * y0 + S[1] * y1 + S[2] * y2);
+            T1 = varpi * (S[3] * y0 + S[4] * y1 + S[5] * y2);
+            T2 = varpi * (S[6] * y0 + S[7] * y1 + S[8] * y2);
+        }
         Real o[3];
         store_force_state<CPL>(s, k, (size_t)r0 + t, rb, T0, T1, T2, zj, Jj, CPL ? s.J[i] : (Real)1, o);
         red[9] += o[0]; red[10] += o[1]; red[11] += o[2];
     } else {
 #pragma unroll
         for (int e = 0; e < 9; e++) sM[e] = SK[e];
-        if constexpr (!F64) {
+        if constexpr (!F64 && SMW >= 13) {
             sM[9] = mjx; sM[10] = mjy; sM[11] = mjz; sM[12] = thj;
         }
     }
@@ -622,10 +635,10 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
     __shared__ float s_Jms[PPB][CPL ? kTcRows : 1];   // coupled mode: the members' volume ratios
     __shared__ alignas(16) unsigned s_phis[PPB][kTcPhiWords];
     __shared__ alignas(16) unsigned s_tws[PPB][4 * kTcRows];   // the test's member words
-    // model 2: each sender's matrix M = varpi sigma K^-1 (and its park row)
-    __shared__ alignas(16) float s_Ms[PPB][MODEL == 2 ? kTcRows : 1][16];
+    // model 2: each sender's matrix M = varpi sigma K^-1
+    __shared__ float s_Ms[PPB][MODEL == 2 ? kTcRows : 1][9];
     R4<float>* s_z = s_zs[w];
-    float(*s_M)[16] = s_Ms[w];
+    float(*s_M)[9] = s_Ms[w];
     R4<float>* s_y = reinterpret_cast<R4<float>*>(s_yFs[w]);
     float(*F)[kTcF] = reinterpret_cast<float(*)[kTcF]>(s_yFs[w]);
     float* s_Jm = s_Jms[w];
@@ -695,8 +708,7 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
                 const Real cntr = Fr[15];
                 const R4<Real> zj = s_z[t];
                 // the row is this lane's until the next pass: it parks there
-                // (model 2 parks in the sender's row of s_M)
-                bond_epilogue<Real, MODEL, CPL, NRED>(
+                bond_epilogue<Real, MODEL, CPL, NRED, 9>(
                     s, k, i, r0, t, rb, zj, CPL ? s_Jm[t] : (Real)1, K00, K11, K22, K12, K02, K01,
                     A00, A01, A02, A10, A11, A12, A20, A21, A22, cntr, small_count(cntr), (Real)0,
                     (Real)0, (Real)0, (Real)0, sig_i, pc_i, cc, Srs, inv_nb, inv_dx, with_dt, F[lane],
@@ -739,11 +751,313 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
     }
 }
 
+// Fused bond kernel with the sub-horizon tests and sums in tensor memory
+// (tcgen05): the mixed path, the force state of Eq. 51, not the coupled
+// mode, points with at most kTcRows bonds (k_bond_big takes the others).
+// One CTA of kT5Threads threads per point, thread t its bond t and its
+// member t; a persistent wave of CTAs loops over the points, each holding
+// kT5Cols columns of tensor memory for its whole life.  Per point: the
+// staging, the member features (Phi) and the test terms of thread t's bond
+// and member in shared memory; the distance product and, from its signs,
+// the mask; the sums product; then each thread updates its bond
+// (bond_epilogue) and the CTA commits the point.  The next point's
+// neighbour data is fetched by cp.async while the current point's bonds
+// are updated, so that its staging finds it in shared memory.  A wait that
+// runs out sets PPM_STATUS_TC_TIMEOUT and stops the CTA (its remaining
+// points keep their state); the CTA still waits for its product in flight
+// (bounded) and frees its tensor memory.
+
+// words of the prefetched staging data: per bond (lat, u xyz, vh xyz, rev
+// of the neighbour) and per point (lat, u xyz, vh xyz, sigma, pc, eps, column)
+constexpr int kT5StageWords = 8;
+constexpr int kT5PointWords = 16;
+
+__device__ __forceinline__ void t5_cp4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+// Issue the copies of point i's staging data (thread t: its bond's
+// neighbour; threads below kT5PointWords: one word of the point's own
+// data).  r0, nb: the point's row; j: its t-th neighbour (t < nb).
+__device__ __forceinline__ void t5_prefetch(const DevState<float>& s, size_t n, int i, int r0, int nb,
+                                            int j, int t, unsigned* stage, unsigned* pt) {
+    if (nb <= kTcRows && t < nb) {
+        unsigned* d = stage + kT5StageWords * t;
+        t5_cp4(d + 0, s.lat + j);
+        t5_cp4(d + 1, s.u + j);
+        t5_cp4(d + 2, s.u + n + j);
+        t5_cp4(d + 3, s.u + 2 * n + j);
+        t5_cp4(d + 4, s.vh + j);
+        t5_cp4(d + 5, s.vh + n + j);
+        t5_cp4(d + 6, s.vh + 2 * n + j);
+        t5_cp4(d + 7, s.rev + r0 + t);
+    }
+    if (t < kT5PointWords) {
+        const void* src = t == 0 ? (const void*)(s.lat + i)
+                        : t < 4 ? (const void*)(s.u + (size_t)(t - 1) * n + i)
+                        : t < 7 ? (const void*)(s.vh + (size_t)(t - 4) * n + i)
+                        : t < 13 ? (const void*)(s.sig + (size_t)(t - 7) * n + i)
+                        : t == 13 ? (const void*)(s.pc + i)
+                        : t == 14 ? (const void*)(s.eps + i) : (const void*)(s.colid + i);
+        t5_cp4(pt + t, src);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kT5Threads, 4)
+k_bond_t5(DevState<float> s, StepConst k, int with_dt, int update) {
+    using Real = float;
+    constexpr int NRED = 12;
+    if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;   // the whole CTA, before any allocation
+    extern __shared__ __align__(128) unsigned char t5s[];
+    __shared__ alignas(8) uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_max[2][kT5Threads / 32];
+    __shared__ float s_red[2][kT5Threads / 32][NRED];             // by point parity
+    __shared__ unsigned s_cnt[2][kT5Threads / 32][5];
+    __shared__ unsigned s_pt[kT5PointWords];
+    // the staging buffer shares the test-term region, free between the
+    // distance product of one point and the term writes of the next
+    unsigned* stage = reinterpret_cast<unsigned*>(t5s + kT5Bond);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const size_t n = (size_t)k.npoints;
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"((uint32_t)__cvta_generic_to_shared(&s_tmem)), "r"(kT5Cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
+    }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the first point's staging data
+    int i = blockIdx.x;
+    int r0 = 0, nb = 0;
+    if (i < k.npoints) {
+        r0 = s.row_ptr[i];
+        nb = s.row_ptr[i + 1] - r0;
+        t5_prefetch(s, n, i, r0, nb, (nb <= kTcRows && t < nb) ? s.col[r0 + t] : 0, t, stage, s_pt);
+    }
+    t5_fence_before();
+    __syncthreads();
+    t5_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);        // this warp's 32 lanes
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(t5s);
+    uint32_t phase = 0;
+    int parity = 0;
+    bool ok = true;
+    for (; i < k.npoints; i += gridDim.x) {
+        const int in = i + gridDim.x;                               // this CTA's next point
+        // this point's staging data has landed (every thread's copies)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (nb > kTcRows) {                                         // CTA-uniform: k_bond_big's point
+            if (in < k.npoints) {
+                const int r0n = s.row_ptr[in], nbn = s.row_ptr[in + 1] - r0n;
+                t5_prefetch(s, n, in, r0n, nbn, (nbn <= kTcRows && t < nbn) ? s.col[r0n + t] : 0, t, stage, s_pt);
+                r0 = r0n;
+                nb = nbn;
+            }
+            continue;
+        }
+        const bool in_row = t < nb;
+        const int li = (int)s_pt[0];
+        const int ix = lat_x(li), iy = lat_y(li), iz = lat_z(li);
+        const Real inv_dx = k.inv_dxf;
+        Real sig_i[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) sig_i[c] = __uint_as_float(s_pt[7 + c]);
+        const Real pc_i = __uint_as_float(s_pt[13]);
+        const Real eps_i = __uint_as_float(s_pt[14]);
+        const ColumnConst cc = s.cols[(int)s_pt[15]];
+        const Real Srs = cc.Srsf;
+        // staging of bond / member t (the FP32 staging of bond_point)
+        R4<Real> z, y;
+        z.x = z.y = z.z = z.w = (Real)0;
+        y = z;
+        int rb = -1;
+        if (in_row) {
+            const unsigned* sg = stage + kT5StageWords * t;
+            const int lj = (int)sg[0];
+            rb = (int)sg[7];
+            z.x = small_float(lat_x(lj) - ix) + (__uint_as_float(sg[1]) - __uint_as_float(s_pt[1])) * inv_dx;
+            z.y = small_float(lat_y(lj) - iy + image_shift(k, lj, li) * k.pbc_ny) +
+                  (__uint_as_float(sg[2]) - __uint_as_float(s_pt[2])) * inv_dx;
+            z.z = small_float(lat_z(lj) - iz) + (__uint_as_float(sg[3]) - __uint_as_float(s_pt[3])) * inv_dx;
+            z.w = z.x * z.x + z.y * z.y + z.z * z.z;
+            y.x = __uint_as_float(sg[4]) - __uint_as_float(s_pt[4]);
+            y.y = __uint_as_float(sg[5]) - __uint_as_float(s_pt[5]);
+            y.z = __uint_as_float(sg[6]) - __uint_as_float(s_pt[6]);
+        }
+        // largest |component| of zeta~ and of Ydot over the members with finite values
+        const float az = fmaxf(fabsf(z.x), fmaxf(fabsf(z.y), fabsf(z.z)));
+        const float ay = fmaxf(fabsf(y.x), fmaxf(fabsf(y.y), fabsf(y.z)));
+        const bool zfin = in_row && az <= FLT_MAX;
+        float mz = zfin ? az : 0.0f, my = (zfin && ay <= FLT_MAX) ? ay : 0.0f;
+        mz = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mz)));
+        my = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(my)));
+        if (lane == 0) { s_max[0][w] = mz; s_max[1][w] = my; }
+        __syncthreads();                                            // the staging buffer is read
+#pragma unroll
+        for (int q = 0; q < kT5Threads / 32; q++) { mz = fmaxf(mz, s_max[0][q]); my = fmaxf(my, s_max[1][q]); }
+        const float sK = tc_scale(mz * mz), sA = tc_scale(mz * my), sT = tc_scale(mz);
+        const float uK = 1.0f / sK, uA = 1.0f / sA, sT2 = sT * sT, hf2s = k.hf2f * sT2;
+        // member features of member t into Phi (rows 2f / 2f + 1: high / low part of
+        // feature f, row 30 the count, row 31 zero): neighbouring threads pair up so
+        // that each writes one fp16 pair
+        {
+            float f[16];
+            tc_member_features_of(z, y, zfin, sK, sA, f);
+            const bool odd = t & 1;
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                float h, l;
+                if (e < 15) tc_split(f[e], h, l);
+                else { h = f[15]; l = 0.0f; }
+                const float x = __shfl_xor_sync(0xffffffffu, odd ? h : l, 1);
+                const int row = 2 * e + (odd ? 1 : 0);
+                const unsigned word = odd ? tc_pack(x, l) : tc_pack(h, x);
+                *reinterpret_cast<unsigned*>(t5s + kT5Phi + t5_off(row, t & ~1, 128)) = word;
+            }
+        }
+        // test terms of bond t (a row of the distance product) and of member t (a column)
+        {
+            const float cx = z.x * sT, cy = z.y * sT, cz = z.z * sT, cw = z.w * sT2;
+            const bool tok = in_row && fabsf(cx) < 2.0f && fabsf(cy) < 2.0f && fabsf(cz) < 2.0f && cw < 16.0f;
+            uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = make_uint4(0u, 0u, kTcOnes, kTcFarWord);
+            uint4 b0 = make_uint4(0u, 0u, 0u, 0u), b1 = make_uint4(0u, 0u, kTcFarWord, kTcOnes);
+            if (tok) {
+                float xh, xl, yh, yl, zh, zl;
+                tc_split(cx, xh, xl);
+                tc_split(cy, yh, yl);
+                tc_split(cz, zh, zl);
+                a0 = make_uint4(tc_pack(-2.0f * xh, -2.0f * xh), tc_pack(-2.0f * xl, -2.0f * xl),
+                                tc_pack(-2.0f * yh, -2.0f * yh), tc_pack(-2.0f * yl, -2.0f * yl));
+                a1 = make_uint4(tc_pack(-2.0f * zh, -2.0f * zh), tc_pack(-2.0f * zl, -2.0f * zl), kTcOnes,
+                                tc_split_pack(__fmaf_rn(z.w, sT2, -hf2s)));
+                b0 = make_uint4(tc_pack(xh, xl), tc_pack(xh, xl), tc_pack(yh, yl), tc_pack(yh, yl));
+                b1 = make_uint4(tc_pack(zh, zl), tc_pack(zh, zl), tc_split_pack(cw), kTcOnes);
+            }
+            *reinterpret_cast<uint4*>(t5s + kT5Bond + t5_off(t, 0, 16)) = a0;
+            *reinterpret_cast<uint4*>(t5s + kT5Bond + t5_off(t, 8, 16)) = a1;
+            *reinterpret_cast<uint4*>(t5s + kT5Memb + t5_off(t, 0, 16)) = b0;
+            *reinterpret_cast<uint4*>(t5s + kT5Memb + t5_off(t, 8, 16)) = b1;
+        }
+        t5_fence_proxy();
+        t5_fence_before();
+        __syncthreads();
+        t5_fence_after();
+        if (t == 0) {
+            t5_mma(tmem, t5_desc(sbase + kT5Bond, 256), t5_desc(sbase + kT5Memb, 256), kT5IdescDist, 0);
+            t5_commit(mb);
+        }
+        // the next point's row, while the product runs
+        int r0n = 0, nbn = 0;
+        if (in < k.npoints) {
+            r0n = s.row_ptr[in];
+            nbn = s.row_ptr[in + 1] - r0n;
+        }
+        ok = __syncthreads_and(t5_wait(mb, phase));
+        phase ^= 1u;
+        if (!ok) break;
+        t5_fence_after();
+        // the next point's t-th neighbour, for its copies
+        const int jn = (in < k.npoints && nbn <= kTcRows && t < nbn) ? s.col[r0n + t] : 0;
+        // the mask row of bond t from the signs of its distances
+#pragma unroll 1
+        for (int c = 0; c < 4; c++) {
+            float v[32];
+            t5_ld32(tl + 32u * c, v);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint4 m = make_uint4(tc_sign_pair(v[8 * q], v[8 * q + 1]), tc_sign_pair(v[8 * q + 2], v[8 * q + 3]),
+                                           tc_sign_pair(v[8 * q + 4], v[8 * q + 5]), tc_sign_pair(v[8 * q + 6], v[8 * q + 7]));
+                *reinterpret_cast<uint4*>(t5s + kT5Mask + t5_off(t, 32 * c + 8 * q, 128)) = m;
+            }
+        }
+        t5_fence_proxy();
+        t5_fence_before();
+        __syncthreads();
+        t5_fence_after();
+        if (t == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 8; kk++)
+                t5_mma(tmem, t5_desc(sbase + kT5Mask + 256u * kk, 2048), t5_desc(sbase + kT5Phi + 256u * kk, 2048),
+                       kT5IdescSums, kk > 0);
+            t5_commit(mb);
+        }
+        ok = __syncthreads_and(t5_wait(mb, phase));
+        phase ^= 1u;
+        if (!ok) break;
+        t5_fence_after();
+        Real F[16];
+        {
+            float v[32];
+            t5_ld32(tl, v);
+#pragma unroll
+            for (int f = 0; f < 16; f++) F[f] = (v[2 * f] + v[2 * f + 1]) * (f < 6 ? uK : (f < 15 ? uA : 1.0f));
+        }
+        // the test terms are consumed: the next point's copies land there during the updates
+        if (in < k.npoints) t5_prefetch(s, n, in, r0n, nbn, jn, t, stage, s_pt);
+        Real red[NRED];
+#pragma unroll
+        for (int e = 0; e < NRED; e++) red[e] = (Real)0;
+        unsigned n_plastic = 0, n_nonconv = 0, n_singular = 0, n_pairs = 0, n_ret64 = 0;
+        if (in_row) {
+            // the mask has been read: its rows park the plastic bonds
+            float* park = reinterpret_cast<float*>(t5s + kT5Mask) + 16 * t;
+            bond_epilogue<Real, 0, false, NRED>(
+                s, k, i, r0, t, rb, z, (Real)1, F[0], F[1], F[2], F[3], F[4], F[5], F[6], F[7], F[8],
+                F[9], F[10], F[11], F[12], F[13], F[14], F[15], small_count(F[15]), (Real)0, (Real)0,
+                (Real)0, (Real)0, sig_i, pc_i, cc, Srs, nb > 0 ? (Real)1 / (Real)nb : (Real)0, inv_dx,
+                with_dt, park, park, red, n_pairs, n_plastic, n_nonconv, n_singular, n_ret64);
+        }
+        unsigned cnts[5] = {n_plastic, n_nonconv, n_singular, n_pairs, n_ret64};
+        warp_sum<NRED, Real>(red);
+#pragma unroll
+        for (int e = 0; e < 5; e++) cnts[e] = __reduce_add_sync(0xffffffffu, cnts[e]);
+        if (lane == 0) {
+#pragma unroll
+            for (int e = 0; e < NRED; e++) s_red[parity][w][e] = red[e];
+#pragma unroll
+            for (int e = 0; e < 5; e++) s_cnt[parity][w][e] = cnts[e];
+        }
+        __syncthreads();
+        if (t == 0) {
+#pragma unroll
+            for (int q = 1; q < kT5Threads / 32; q++) {
+#pragma unroll
+                for (int e = 0; e < NRED; e++) red[e] += s_red[parity][q][e];
+#pragma unroll
+                for (int e = 0; e < 5; e++) cnts[e] += s_cnt[parity][q][e];
+            }
+            point_commit<Real, false, NRED>(s, i, n, red, red[0], eps_i, cnts, update);
+        }
+        // the next point's sums go to the other half of s_red / s_cnt, so the
+        // CTA moves on without waiting for the commit
+        parity ^= 1;
+        r0 = r0n;
+        nb = nbn;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok) {
+        if (t == 0) atomicOr(&s.ctr->status, PPM_STATUS_TC_TIMEOUT);
+        // the product in flight completes the phase the failed wait was on
+        (void)__syncthreads_and(t5_wait(mb, phase ^ 1u));
+    }
+    t5_fence_before();
+    __syncthreads();
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kT5Cols));
+}
+
 // ---------------------------------------------------------------------------
 // gather: f_i = dx^2 (sum_own T^ - sum T^[rev]); acceleration, corrector
 // ---------------------------------------------------------------------------
 
-// kGatherLanes lanes per point (four points per warp): each lane sums every
+// kGatherLanes lanes per point (eight points per warp): each lane sums every
 // kGatherLanes-th entry of the point's row with a compensated running sum,
 // then the group combines its lanes in a fixed butterfly; lanes 0..2 of the
 // group finish the point's three components
@@ -1067,6 +1381,14 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
     else if (tpp == 256) PPM_BOND(M, 256);          \
     else PPM_BOND(M, 128);
     if constexpr (sizeof(Real) == 4) {
+        if (k.model == 0 && !k.coupled && tpp == 128 && k.t5_blocks > 0) {
+            // tensor-memory tests and sums, one CTA per point; then the points
+            // with more than kTcRows bonds with the scalar sums
+            const int grid = k.t5_blocks < k.npoints ? k.t5_blocks : k.npoints;
+            k_bond_t5<<<grid, kT5Threads, kT5Smem, st>>>(s, k, with_dt, update);
+            k_bond_big<0, false><<<big_blocks(k.npoints), 32, 0, st>>>(s, k, with_dt, update);
+            return cudaGetLastError();
+        }
         if ((k.model == 0 || k.model == 2) && tpp == 32) {
             // tensor-core sums, one warp per point; then the points with more
             // than kTcRows bonds (normally none) with the scalar sums
@@ -1129,6 +1451,35 @@ cudaError_t bond_tc_resident_blocks(int model, int ppb, int coupled, int* blocks
 #undef PPM_OCC
     *blocks = sms * (per_sm > 0 ? per_sm : 1);
     return e;
+}
+
+cudaError_t bond_t5_prepare(int* blocks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bond_t5, cudaFuncAttributeMaxDynamicSharedMemorySize, kT5Smem);
+    // the whole unified L1 / shared array as shared memory, so that four CTAs fit
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bond_t5, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    // resident CTAs per SM from the kernel's registers and shared memory (the
+    // occupancy query answers one for this kernel, while four run side by
+    // side), and at most four: each holds kT5Cols of the SM's 512 columns
+    cudaFuncAttributes fa;
+    int smem_sm = 0, regs_sm = 0, reserved = 0;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_bond_t5);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess) return e;
+    const int by_smem = smem_sm / (kT5Smem + (int)fa.sharedSizeBytes + reserved);
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;     // allocated per warp in 256s
+    const int by_regs = regs_sm / (regs_warp * (kT5Threads / 32));
+    per_sm = 512 / (int)kT5Cols;
+    if (by_smem < per_sm) per_sm = by_smem;
+    if (by_regs < per_sm) per_sm = by_regs;
+    *blocks = sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
 }
 
 cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, int initial,

@@ -859,16 +859,9 @@ __device__ __forceinline__ void tc_bond_terms(const unsigned* tw, const R4<float
 // member or one without a finite position: it is in no sub-horizon; a
 // non-finite velocity stays in its features and makes the point's velocity
 // gradients NaN, as in the scalar sums)
-__device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R4<float>* s_y, int k,
-                                                   int nb, float sK, float sA, float (&f)[16]) {
-    R4<float> z, y;
-    z.x = z.y = z.z = z.w = 0.0f;
-    y = z;
-    if (k < nb) {
-        z = s_z[k];
-        y = s_y[k];
-    }
-    const bool ok = k < nb && fmaxf(fabsf(z.x), fmaxf(fabsf(z.y), fabsf(z.z))) <= FLT_MAX;
+// (the same from the member's values and its validity ok)
+__device__ __forceinline__ void tc_member_features_of(R4<float> z, R4<float> y, bool ok, float sK,
+                                                      float sA, float (&f)[16]) {
     if (!ok) {
         z.x = z.y = z.z = 0.0f;
         y.x = y.y = y.z = 0.0f;
@@ -879,6 +872,19 @@ __device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R
     f[9] = y.y * z.x * sA; f[10] = y.y * z.y * sA; f[11] = y.y * z.z * sA;
     f[12] = y.z * z.x * sA; f[13] = y.z * z.y * sA; f[14] = y.z * z.z * sA;
     f[15] = ok ? 1.0f : 0.0f;
+}
+
+__device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R4<float>* s_y, int k,
+                                                   int nb, float sK, float sA, float (&f)[16]) {
+    R4<float> z, y;
+    z.x = z.y = z.z = z.w = 0.0f;
+    y = z;
+    if (k < nb) {
+        z = s_z[k];
+        y = s_y[k];
+    }
+    const bool ok = k < nb && fmaxf(fabsf(z.x), fmaxf(fabsf(z.y), fabsf(z.z))) <= FLT_MAX;
+    tc_member_features_of(z, y, ok, sK, sA, f);
 }
 
 // One warp: the member features of a point into phi (row 2f: the high part
@@ -1103,7 +1109,8 @@ __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, const uns
 // tc_pass_receiver, scaled by a power of two below the largest |entry|;
 // returns the factor that undoes the scaling.  Rows 18..31 are zero, and so
 // are members [nb, 16 ceil(nb/16)).
-__device__ __forceinline__ float tc_build_sender_features(const float (*sM)[16], int nb,
+template <int W>
+__device__ __forceinline__ float tc_build_sender_features(const float (*sM)[W], int nb,
                                                           unsigned* phi) {
     const int lane = threadIdx.x & 31;
     const int KT = (nb + 15) >> 4;
@@ -1133,6 +1140,97 @@ __device__ __forceinline__ float tc_build_sender_features(const float (*sM)[16],
     }
     __syncwarp();
     return 1.0f / sc;
+}
+
+// ---------------------------------------------------------------------------
+// Sub-horizon tests and sums in tensor memory (tcgen05, mixed path, Eq. 51)
+// ---------------------------------------------------------------------------
+// One CTA of 128 threads does a point, thread t its bond t and its member t.
+// Operands sit in shared memory in the no-swizzle K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix; 128 bytes between core matrices along
+// K, 128 * K / 8 bytes between groups of 8 rows), accumulators in 128 columns
+// of tensor memory (row t = lane t).  Per point two products, each issued by
+// one thread and awaited on an mbarrier:
+//   d (128 x 128, f32) = bond terms (128 x 16) * member terms (128 x 16)^T:
+//       the squared distances of the sub-horizon test, as in the warp kernel
+//       (slots per component c: bond (-2c^h, -2c^h, -2c^l, -2c^l) against
+//       member (c^h, c^l, c^h, c^l); then (1, 1) against (w^h, w^l) and
+//       (e^h, e^l) against (1, 1), e = sT^2 (|zeta~_t|^2 - hf^2));
+//   F (128 x 32, f32) = Mask (128 x 128) * Phi (32 x 128)^T in eight steps of
+//       K = 16, Mask[t][k] = [d(t, k) < 0] written by thread t from its row.
+constexpr int kT5Threads = 128;
+constexpr unsigned kT5Cols = 128;                 // tensor-memory columns per CTA
+constexpr int kT5Mask = 0;                        // Mask: 128 x 128 fp16 (32 KB); later the park rows
+constexpr int kT5Phi = 32768;                     // Phi: 32 x 128 fp16 (8 KB)
+constexpr int kT5Bond = 40960;                    // bond terms: 128 x 16 fp16 (4 KB)
+constexpr int kT5Memb = 45056;                    // member terms: 128 x 16 fp16 (4 KB)
+constexpr int kT5Smem = 49152;                    // dynamic shared memory per CTA
+// instruction descriptors (kind::f16): f32 accumulator (bits 4-5 = 1), f16 A
+// and B (0), both K-major (0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
+constexpr uint32_t kT5IdescDist = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kT5IdescSums = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr int kT5WaitLimit = 1 << 22;             // mbarrier polls before a wait is given up
+
+// byte offset of element (r, k) in a K-major matrix with K columns
+__device__ __forceinline__ uint32_t t5_off(int r, int k, int K) {
+    return (uint32_t)(r >> 3) * (uint32_t)(16 * K) + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride
+// (8-row) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void t5_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void t5_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(mbar) : "memory");
+}
+
+// bounded wait for the completion of phase `parity` of the mbarrier
+__device__ __forceinline__ bool t5_wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < kT5WaitLimit; it++) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void t5_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void t5_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory writes of the threads become visible to the tensor cores
+__device__ __forceinline__ void t5_fence_proxy() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 consecutive columns of this thread's lane (32x32b shape, 32 repetitions)
+__device__ __forceinline__ void t5_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                 "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
 }
 
 }  // namespace

@@ -11,8 +11,8 @@ namespace ppm {
 constexpr int kMaxRow = 256;          // hard cap of bonds per point (smem staging)
 constexpr int kDefaultMaxFamily = 192;
 constexpr int kWarpPointsPerBlock = 8;  // family kernels: one warp per point
-constexpr int kGatherLanes = 8;         // force gather: lanes per point ...
-constexpr int kGatherPointsPerBlock = 32;   // ... and points per block (256 threads)
+constexpr int kGatherLanes = 4;         // force gather: lanes per point ...
+constexpr int kGatherPointsPerBlock = 32;   // ... and points per block (128 threads)
 constexpr int kAdjAccDoubles = 32;     // adjoint accumulators (gradient, state sums) ...
 constexpr int kAdjRedBlocks = 152;     // ... followed by 5 partial sums per reduction block
 constexpr int kLatBits = 10;          // packed lattice index: ix | iy << 10 | iz << 20
@@ -77,6 +77,7 @@ struct StepConst {
     int npoints, ncols, max_family, tile;   // tile: bond-kernel threads per point
     int tc_ppb, tc_blocks;       // tensor-core bond kernel: points per block; grid (0: one
                                  // point per warp, else a persistent grid of that many blocks)
+    int t5_blocks;               // tensor-memory bond kernel: its persistent grid
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;
@@ -284,6 +285,9 @@ cudaError_t launch_energy_reduce(double* epart, int nblocks, DevCounters* ctr, i
 // blocks of one resident wave of the tensor-core bond kernel (force state
 // model 0 or 2, points per block ppb = 1 or 2) on the current device
 cudaError_t bond_tc_resident_blocks(int model, int ppb, int coupled, int* blocks);
+// the tensor-memory bond kernel on the current device: sets its dynamic
+// shared memory limit and returns the blocks of one resident wave
+cudaError_t bond_t5_prepare(int* blocks);
 
 // ---- launchers (adjoint.cu) ----
 // one reverse step from the restored start state (predictor already

@@ -371,7 +371,8 @@ int capture_segment(ppm_ctx* c, const DevState<Real>& s, int len, cudaGraphExec_
 // (Eq. 51 or the power-conjugate one), 32 means the tensor-core kernel,
 // tried with one and two points per block, each with a grid that covers
 // every point once and with a persistent resident wave that loops over
-// the points.
+// the points; for the mixed path with Eq. 51 outside the coupled mode, 128
+// means the tensor-memory (tcgen05) kernel, one CTA per point.
 struct LaunchShape {
     int tile, ppb, blocks;
 };
@@ -847,6 +848,13 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
         }
         k.tc_blocks = resident;
     }
+    k.t5_blocks = 0;
+    if (p->precision == PPM_MIXED && p->model == 0 && !p->coupled) {
+        if (bond_t5_prepare(&k.t5_blocks) != cudaSuccess) {
+            delete c;
+            return PPM_ECUDA;
+        }
+    }
     k.cap = c->cap;
     k.dxf = (float)k.dx;
     k.inv_dxf = (float)k.inv_dx;
@@ -1008,7 +1016,9 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     out->returns_fp64 = (int64_t)h.ret64;
     out->bond_tile = c->k.tile;
     out->points_per_block = c->k.tc_ppb;
-    out->bond_blocks = c->k.tc_blocks;
+    // the persistent grid in use: the tensor-memory kernel's, or the warp kernel's
+    const bool t5 = c->k.tile == 128 && c->k.t5_blocks > 0 && c->k.model == 0 && !c->k.coupled;
+    out->bond_blocks = t5 ? c->k.t5_blocks : c->k.tc_blocks;
     out->halted_step = (int32_t)h.halted_step;
     out->unstable_step = (int32_t)h.unstable_step;
     out->launches = c->launches;

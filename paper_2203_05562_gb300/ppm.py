@@ -20,7 +20,7 @@ SUBHORIZON, STANDARD, SUBHORIZON_CONJUGATE = 0, 1, 2
 FIELD = dict(u=0, v=1, a=2, sigma=3, pc=4, eps_s=5, fint=6, row_ptr=7, col=8, rev=9, tforce=10, J=11)
 _NCOMP = dict(u=3, v=3, a=3, sigma=6, pc=1, eps_s=1, fint=3, J=1)
 STATUS_BITS = dict(nonconv=1, singular=2, nonfinite=4, family_full=8, row_full=16, unstable=32,
-                   halted=64)
+                   halted=64, tc_timeout=128)
 
 
 class PPMError(RuntimeError):
