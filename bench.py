@@ -469,6 +469,9 @@ def main():
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + steps of the mixed path only (for ncu captures)")
+    ap.add_argument("--profile-adjoint", type=int, default=0,
+                    help="with --profile-only: an adjoint of this many steps (checkpoints every "
+                         "half of them) instead of plain steps")
     ap.add_argument("--profile-model", type=int, default=0, choices=[0, 1, 2],
                     help="the force state --profile-only runs (0: Eq. 51, 1: standard, 2: power-conjugate)")
     ap.add_argument("--profile-workload", default=WORKLOAD,
@@ -500,7 +503,15 @@ def main():
         sim = Simulation(pcfg, precision="mixed", model=args.profile_model, use_graph=False,
                          bond_tile=args.tile)
         sim.write("v", pi.initial_velocity(pcfg))
-        sim.step(args.warmup + args.steps)
+        if args.profile_adjoint > 0:
+            sim.adjoint_forward(args.profile_adjoint, max(1, args.profile_adjoint // 2))
+            u = sim.read("u", device=True).double()
+            nxy = pcfg["nx"] * pcfg["ny"]
+            dJ = torch.zeros_like(u)
+            dJ[0:2, -nxy:] = 2.0 * u[0:2, -nxy:]
+            sim.adjoint_reverse(dJ)
+        else:
+            sim.step(args.warmup + args.steps)
         torch.cuda.synchronize()
         print(json.dumps({"profile_only": True, "status": sim.status()["flags"]}))
         return 0

@@ -231,6 +231,14 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
     Real* s_b = reinterpret_cast<Real*>(s_p + (F64 ? 3 * kMaxRow : 0));   // [kMaxRow][kAdjSlots]
     __shared__ Real s_red[NW][16];
     __shared__ double s_redd[NW][4];
+    __shared__ float s_tcs[kAdjThreads / 32];                     // block maxima
+    // the tensor-core sums (mixed path, Eq. 51, at most kTcRows bonds) keep
+    // their feature rows and test words in the upper half of the bond slots,
+    // which only points with more bonds use
+    static_assert((kMaxRow - kTcRows) * kAdjSlots >= kTcPhiWords + 4 * kTcRows, "tensor-core scratch");
+    unsigned* tc_phi = reinterpret_cast<unsigned*>(s_b + (size_t)kTcRows * kAdjSlots);
+    unsigned* tc_tw = tc_phi + kTcPhiWords;
+    const int wid = threadIdx.x >> 5;
 
     const int i = blockIdx.x;
     const size_t n = (size_t)k.npoints;
@@ -293,6 +301,24 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
     const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
     const Real fbi[3] = {a.fb[i], a.fb[n + i], a.fb[2 * n + i]};
 
+    // the forward's tensor-core tests and sums (the same operands and
+    // products as k_bond_tcw, so the same bits): warp w sums bonds 32w ..
+    // 32w + 31 straight into their slots (K~ at kSlG, A~ at kSlAb, |S| at kSlCnt)
+    bool use_tc = false;
+    float tc_sT2 = 0.0f, tc_hf2s = 0.0f;
+    if constexpr (!F64 && MODEL == 0) {
+        use_tc = nb <= kTcRows;                                     // block-uniform
+        if (use_tc) {
+            float uK, uA, sT;
+            tc_build_features<kAdjThreads>(s_z, s_y, nb, tc_phi, tc_tw, uK, uA, sT, s_tcs);
+            tc_sT2 = sT * sT;
+            tc_hf2s = k.hf2f * tc_sT2;
+            if (32 * wid < nb)
+                tc_pass_sums<kAdjSlots>(s_z, tc_tw, nb, wid, tc_sT2, tc_hf2s, tc_phi,
+                                        s_b + (size_t)32 * wid * kAdjSlots + kSlG, uK, uA);
+        }
+    }
+
     // pass 1: sub-horizon sums, kept per bond
     Real wpart[1] = {(Real)0};
     for (int t = threadIdx.x; t < nb; t += kAdjThreads) {
@@ -325,6 +351,14 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
                     cnt++;
                 }
             }
+        } else if (use_tc) {
+            const Real* sbt = s_b + (size_t)t * kAdjSlots;          // this warp's rows
+            K00 = sbt[kSlG + 0]; K11 = sbt[kSlG + 1]; K22 = sbt[kSlG + 2];
+            K12 = sbt[kSlG + 3]; K02 = sbt[kSlG + 4]; K01 = sbt[kSlG + 5];
+            A00 = sbt[kSlAb + 0]; A01 = sbt[kSlAb + 1]; A02 = sbt[kSlAb + 2];
+            A10 = sbt[kSlAb + 3]; A11 = sbt[kSlAb + 4]; A12 = sbt[kSlAb + 5];
+            A20 = sbt[kSlAb + 6]; A21 = sbt[kSlAb + 7]; A22 = sbt[kSlAb + 8];
+            cnt = small_count(sbt[kSlCnt]);
         } else {
             float Kf[6] = {0, 0, 0, 0, 0, 0}, Af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             float cntf = 0.0f;
@@ -490,6 +524,18 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
 
     Real zs[6] = {0, 0, 0, 0, 0, 0};   // sums over the row of the position / velocity adjoints
     if constexpr (!INITIAL) {
+        // the tensor-core receiver sums: the senders' terms G, Ab (in their
+        // slots after pass 2) as features, the forward's mask tiles transposed;
+        // warp w writes the sums of receivers 32w .. 32w + 31 into their slots
+        if constexpr (!F64 && MODEL == 0) {
+            if (use_tc) {
+                float uG, uAb;
+                tc_build_adj_sender_features<kAdjThreads>(s_b + kSlG, kAdjSlots, nb, tc_phi, uG, uAb, s_tcs);
+                if (32 * wid < nb)
+                    tc_pass_receiver<4, kAdjSlots>(s_z, tc_tw, nb, wid, tc_sT2, tc_hf2s, tc_phi,
+                                                   s_b + (size_t)32 * wid * kAdjSlots + kSlG, uG, uAb, 6, 15);
+            }
+        }
         // pass 3: receiver t gathers from every sender q whose sub-horizon holds
         // it: zeta~-bar += G zeta~_t + Ab^T Ydot_t and Ydot-bar += Ab zeta~_t,
         // with G and Ab first summed over those senders
@@ -498,7 +544,12 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
             const R4<Real> yt = s_y[t];
             const Real* sbt = s_b + (size_t)t * kAdjSlots;
             Real Gs[6] = {0, 0, 0, 0, 0, 0}, As[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if constexpr (!F64 && MODEL != 1) {
+            if (use_tc) {
+#pragma unroll
+                for (int e = 0; e < 6; e++) Gs[e] = sbt[kSlG + e];
+#pragma unroll
+                for (int e = 0; e < 9; e++) As[e] = sbt[kSlAb + e];
+            } else if constexpr (!F64 && MODEL != 1) {
                 // the sender's own membership test, same operands and rounding
                 float Gf[6] = {0, 0, 0, 0, 0, 0}, Af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 2

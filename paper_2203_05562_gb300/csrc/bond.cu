@@ -685,7 +685,7 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
         }
         __syncwarp();
         float uK, uA, sT;
-        tc_build_features(s_z, s_y, nb, s_phi, s_tw, uK, uA, sT);   // s_y is free afterwards
+        tc_build_features<32>(s_z, s_y, nb, s_phi, s_tw, uK, uA, sT);   // s_y is free afterwards
         const float sT2 = sT * sT, hf2s = k.hf2f * sT2;        // the test's scaled radius
         const Real inv_nb = nb > 0 ? (Real)1 / (Real)nb : (Real)0;
         Real red[NRED];
@@ -699,7 +699,7 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
             // the bond's reverse slot, issued before the sums so that its latency hides
             const int rb = (MODEL == 0 && t < nb) ? s.rev[r0 + t] : -1;
             __syncwarp();                             // the previous pass's rows are free
-            tc_pass_sums(s_z, s_tw, nb, p, sT2, hf2s, s_phi, F, uK, uA);
+            tc_pass_sums<kTcF>(s_z, s_tw, nb, p, sT2, hf2s, s_phi, &F[0][0], uK, uA);
             if (t < nb) {
                 const float* Fr = F[lane];
                 const Real K00 = Fr[0], K11 = Fr[1], K22 = Fr[2], K12 = Fr[3], K02 = Fr[4], K01 = Fr[5];
@@ -729,7 +729,7 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
                 const int t = 32 * p + lane;
                 const int rb = t < nb ? s.rev[r0 + t] : -1;
                 __syncwarp();
-                tc_pass_receiver(s_z, s_tw, nb, p, sT2, hf2s, s_phi, F, uM);
+                tc_pass_receiver<3, kTcF>(s_z, s_tw, nb, p, sT2, hf2s, s_phi, &F[0][0], uM, uM, 9, 9);
                 if (t < nb) {
                     const float* Nr = F[lane];
                     const R4<Real> zt = s_z[t];

@@ -887,7 +887,7 @@ __device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R
     tc_member_features_of(z, y, ok, sK, sA, f);
 }
 
-// One warp: the member features of a point into phi (row 2f: the high part
+// The member features of a point into phi (row 2f: the high part
 // of feature f, row 2f + 1: the low part, 32 rows of fp16 pairs along the
 // members), the factors uK, uA that undo the scaling of the K~ and A~ sums,
 // the member words of the test into tw (4 per member: (c^h, c^l) of the
@@ -895,29 +895,53 @@ __device__ __forceinline__ void tc_member_features(const R4<float>* s_z, const R
 // no sub-horizon, zeros before it) and the test's scale sT.  Members
 // [nb, 16 ceil(nb/16)) are padding: zero features, far words, and zeroed
 // in s_z.
+// NTH threads build them together: one warp (NTH = 32), or a whole block of
+// NTH threads, which then needs 2 NTH / 32 floats of shared scratch for the
+// maxima and synchronises the block.
+template <int NTH>
+__device__ __forceinline__ void tc_sync() {
+    if constexpr (NTH == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// the largest of v over the NTH threads (non-negative floats order as
+// their bit patterns)
+template <int NTH>
+__device__ __forceinline__ float tc_group_max(float v, float* scratch) {
+    v = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+    if constexpr (NTH > 32) {
+        if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NTH / 32; q++) v = fmaxf(v, scratch[q]);
+        __syncthreads();
+    }
+    return v;
+}
+
+template <int NTH>
 __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float>* s_y, int nb,
                                                   unsigned* phi, unsigned* tw, float& uK,
-                                                  float& uA, float& sT) {
-    const int lane = threadIdx.x & 31;
+                                                  float& uA, float& sT, float* scratch = nullptr) {
+    const int lane = NTH == 32 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
     const int KT = (nb + 15) >> 4;
     // largest |component| of zeta~ and of Ydot over the members with finite values
     float mz = 0.0f, my = 0.0f;
-    for (int k = lane; k < nb; k += 32) {
+    for (int k = lane; k < nb; k += NTH) {
         const R4<float> z = s_z[k], y = s_y[k];
         const float az = fmaxf(fabsf(z.x), fmaxf(fabsf(z.y), fabsf(z.z)));
         const float ay = fmaxf(fabsf(y.x), fmaxf(fabsf(y.y), fabsf(y.z)));
         if (az <= FLT_MAX) mz = fmaxf(mz, az);
         if (az <= FLT_MAX && ay <= FLT_MAX) my = fmaxf(my, ay);
     }
-    // non-negative floats order as their bit patterns
-    mz = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mz)));
-    my = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(my)));
+    mz = tc_group_max<NTH>(mz, scratch);
+    my = tc_group_max<NTH>(my, scratch);
     const float sK = tc_scale(mz * mz), sA = tc_scale(mz * my);
     uK = 1.0f / sK;                                      // powers of two: exact
     uA = 1.0f / sA;
     sT = tc_scale(mz);
     const float sT2 = sT * sT;
-    for (int kp = lane; kp < KT * 8; kp += 32) {
+    for (int kp = lane; kp < KT * 8; kp += NTH) {
         float f0[16], f1[16];
         tc_member_features(s_z, s_y, 2 * kp, nb, sK, sA, f0);
         tc_member_features(s_z, s_y, 2 * kp + 1, nb, sK, sA, f1);
@@ -932,7 +956,7 @@ __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float
         phi[tc_phi_word(30, kp)] = tc_pack(f0[15], f1[15]);
         phi[tc_phi_word(31, kp)] = 0u;
     }
-    for (int k = lane; k < KT * 16; k += 32) {
+    for (int k = lane; k < KT * 16; k += NTH) {
         uint4 W = make_uint4(0u, 0u, 0u, kTcFarWord);
         if (k < nb) {
             const R4<float> z = s_z[k];
@@ -943,22 +967,23 @@ __device__ __forceinline__ void tc_build_features(R4<float>* s_z, const R4<float
         }
         reinterpret_cast<uint4*>(tw)[k] = W;
     }
-    __syncwarp();
-    for (int k = nb + lane; k < KT * 16; k += 32) {
+    tc_sync<NTH>();
+    for (int k = nb + lane; k < KT * 16; k += NTH) {
         R4<float> zero;
         zero.x = zero.y = zero.z = zero.w = 0.0f;
         s_z[k] = zero;
     }
-    __syncwarp();
+    tc_sync<NTH>();
 }
 
 // One warp, pass p: the sums of bonds 32p .. 32p + 31 (row tiles 2p, 2p + 1)
-// into F[0..31][0..15]: F[r][0..5] = K~ (xx yy zz yz xz xy), F[r][6..14] = A~
-// (row-major, A_rc = sum Ydot_r zeta~_c), F[r][15] = |S| of bond 32p + r.
+// into rows of FS floats, F[r FS + 0..15]: 0..5 = K~ (xx yy zz yz xz xy),
+// 6..14 = A~ (row-major, A_rc = sum Ydot_r zeta~_c), 15 = |S| of bond 32p + r.
 // hf2s = sT^2 hf^2.
+template <int FS>
 __device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, const unsigned* tw, int nb, int p,
-                                             float sT2, float hf2s, const unsigned* phi,
-                                             float (*F)[kTcF], float uK, float uA) {
+                                             float sT2, float hf2s, const unsigned* phi, float* F,
+                                             float uK, float uA) {
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     const int KT = (nb + 15) >> 4;
     const int nm = KT - 2 * p >= 2 ? 2 : 1;              // row tiles with bonds in this pass
@@ -1019,26 +1044,30 @@ __device__ __forceinline__ void tc_pass_sums(const R4<float>* s_z, const unsigne
         for (int nt = 0; nt < 4; nt++) {
             const int f = 4 * nt + tq;                   // columns 2f (high part) and 2f + 1 (low)
             const float u = f < 6 ? uK : (f < 15 ? uA : 1.0f);
-            F[16 * m + g][f] = (acc[m][nt][0] + acc[m][nt][1]) * u;
-            F[16 * m + g + 8][f] = (acc[m][nt][2] + acc[m][nt][3]) * u;
+            F[(16 * m + g) * FS + f] = (acc[m][nt][0] + acc[m][nt][1]) * u;
+            F[(16 * m + g + 8) * FS + f] = (acc[m][nt][2] + acc[m][nt][3]) * u;
         }
     }
     __syncwarp();
 }
 
-// One warp, pass p of the receiver sums of the power-conjugate force state
-// (model 2): for receivers t = 32p .. 32p + 31, N_t = sum over senders q of
-// [t in S_q] M_q, with M_q = varpi sigma K^-1 of sender bond q (9 values,
-// row-major).  The mask element (t, q) is the sender pass's own decision:
-// the test tile is taken with the senders as rows and the receivers as
-// columns, exactly as tc_pass_sums took it (same operands, same product),
-// and its mask fragments are transposed (movmatrix).  phi holds M split into
-// fp16 pairs (row 2f: high, 2f + 1: low part of entry f, rows 18..23 zero)
-// scaled by a power of two; uM undoes it.  Writes F[r][0..8] = N of
-// receiver 32p + r.
+// One warp, pass p of receiver sums: for receivers t = 32p .. 32p + 31,
+// N_t = sum over senders q of [t in S_q] V_q, where V_q holds nf < 16 values
+// of sender bond q (the power-conjugate force state: M_q = varpi sigma K^-1,
+// 9 values; the adjoint: its 6 + 9 sender terms).  The mask element (t, q)
+// is the sender pass's own decision: the test tile is taken with the
+// senders as rows and the receivers as columns, exactly as tc_pass_sums took
+// it (same operands, same product), and its mask fragments are transposed
+// (movmatrix).  phi holds V split into fp16 pairs (row 2f: high, 2f + 1: low
+// part of value f; the other rows zero) scaled by powers of two: u_lo undoes
+// the scaling of values f < f_split, u_hi that of the others.  Writes
+// F[r FS + f], f < nf, for receiver 32p + r; NT n-tiles of 8 rows of phi
+// (3 for 9 values, 4 for 15).
+template <int NT, int FS>
 __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, const unsigned* tw, int nb,
                                                  int p, float sT2, float hf2s, const unsigned* phi,
-                                                 float (*F)[kTcF], float uM) {
+                                                 float* F, float u_lo, float u_hi, int f_split,
+                                                 int nf) {
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     const int KT = (nb + 15) >> 4;
     const int nm = KT - 2 * p >= 2 ? 2 : 1;
@@ -1051,11 +1080,12 @@ __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, const uns
             rw[m][n] = m < nm ? tw[4 * (32 * p + 16 * m + 8 * n + g) + tq] : 0u;
             rv[m][n] = tq < 3 ? rw[m][n] : 0u;
         }
-    float acc[2][3][4];
+    static_assert(NT == 3 || NT == 4, "three or four n-tiles of values");
+    float acc[2][NT][4];
 #pragma unroll
     for (int m = 0; m < 2; m++)
 #pragma unroll
-        for (int nt = 0; nt < 3; nt++)
+        for (int nt = 0; nt < NT; nt++)
 #pragma unroll
             for (int e = 0; e < 4; e++) acc[m][nt][e] = 0.0f;
     const int lm = lane >> 3, lr = lane & 7;
@@ -1066,13 +1096,13 @@ __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, const uns
         float se[2];
         tc_bond_terms(tw, s_z, 16 * kt + g, tq, sT2, hf2s, sa[0], sa[2], se[0]);
         tc_bond_terms(tw, s_z, 16 * kt + 8 + g, tq, sT2, hf2s, sa[1], sa[3], se[1]);
-        unsigned b[3][2], bx, by;
+        unsigned b[4][2];
         {
             const int row = 8 * (lm >> 1) + lr;
             const unsigned addr = phi_base + 4u * (unsigned)tc_phi_word(row, 8 * kt + 4 * (lm & 1));
             tc_ldmatrix_x4(addr, b[0][0], b[0][1], b[1][0], b[1][1]);
             const unsigned addr2 = phi_base + 4u * (unsigned)tc_phi_word(16 + row, 8 * kt + 4 * (lm & 1));
-            tc_ldmatrix_x4(addr2, b[2][0], b[2][1], bx, by);   // rows 24..31 are not used
+            tc_ldmatrix_x4(addr2, b[2][0], b[2][1], b[3][0], b[3][1]);   // rows 24..31: used with NT = 4
         }
 #pragma unroll
         for (int m = 0; m < 2; m++) {
@@ -1087,18 +1117,19 @@ __device__ __forceinline__ void tc_pass_receiver(const R4<float>* s_z, const uns
             const unsigned a0 = tc_transpose8(f0), a1 = tc_transpose8(f2);
             const unsigned a2 = tc_transpose8(f1), a3 = tc_transpose8(f3);
 #pragma unroll
-            for (int nt = 0; nt < 3; nt++) tc_mma(acc[m][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
+            for (int nt = 0; nt < NT; nt++) tc_mma(acc[m][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
         }
     }
 #pragma unroll
     for (int m = 0; m < 2; m++) {
         if (m >= nm) continue;
 #pragma unroll
-        for (int nt = 0; nt < 3; nt++) {
+        for (int nt = 0; nt < NT; nt++) {
             const int f = 4 * nt + tq;
-            if (f < 9) {
-                F[16 * m + g][f] = (acc[m][nt][0] + acc[m][nt][1]) * uM;
-                F[16 * m + g + 8][f] = (acc[m][nt][2] + acc[m][nt][3]) * uM;
+            if (f < nf) {
+                const float u = f < f_split ? u_lo : u_hi;
+                F[(16 * m + g) * FS + f] = (acc[m][nt][0] + acc[m][nt][1]) * u;
+                F[(16 * m + g + 8) * FS + f] = (acc[m][nt][2] + acc[m][nt][3]) * u;
             }
         }
     }
@@ -1140,6 +1171,53 @@ __device__ __forceinline__ float tc_build_sender_features(const float (*sM)[W], 
     }
     __syncwarp();
     return 1.0f / sc;
+}
+
+// NTH threads (tc_build_features): the adjoint's sender terms of bonds q < nb (rows of stride
+// floats: G at row[0..5], Ab at row[6..14]) into phi for tc_pass_receiver
+// (row 2f: high, 2f + 1: low part of value f; rows 30, 31 and members
+// [nb, 16 ceil(nb/16)) zero), G and Ab each scaled by a power of two below
+// its largest |entry|; uG, uAb undo the scalings.
+template <int NTH>
+__device__ __forceinline__ void tc_build_adj_sender_features(const float* rows, int stride, int nb,
+                                                             unsigned* phi, float& uG, float& uAb,
+                                                             float* scratch) {
+    const int lane = NTH == 32 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int KT = (nb + 15) >> 4;
+    // maxima: consecutive threads take consecutive values of a row (few bank conflicts)
+    float mg = 0.0f, ma = 0.0f;
+    for (int idx = lane; idx < 15 * nb; idx += NTH) {
+        const int q = idx / 15, e = idx - 15 * q;
+        const float a = fabsf(rows[q * stride + e]);
+        if (a <= FLT_MAX) {
+            if (e < 6) mg = fmaxf(mg, a);
+            else ma = fmaxf(ma, a);
+        }
+    }
+    mg = tc_group_max<NTH>(mg, scratch);
+    ma = tc_group_max<NTH>(ma, scratch);
+    const float sg = tc_scale(mg), sa = tc_scale(ma);
+    // value e (e < 15; 15: the zero rows 30, 31) of member pair kp
+    for (int idx = lane; idx < 16 * KT * 8; idx += NTH) {
+        const int kp = idx >> 4, e = idx & 15;
+        const int q0 = 2 * kp, q1 = 2 * kp + 1;
+        unsigned hi = 0u, lo = 0u;
+        if (e < 15) {
+            const float sc = e < 6 ? sg : sa;
+            const float v0 = q0 < nb ? rows[q0 * stride + e] * sc : 0.0f;
+            const float v1 = q1 < nb ? rows[q1 * stride + e] * sc : 0.0f;
+            float h0, l0, h1, l1;
+            tc_split(v0, h0, l0);
+            tc_split(v1, h1, l1);
+            hi = tc_pack(h0, h1);
+            lo = tc_pack(l0, l1);
+        }
+        phi[tc_phi_word(2 * e, kp)] = hi;
+        phi[tc_phi_word(2 * e + 1, kp)] = lo;
+    }
+    tc_sync<NTH>();
+    uG = 1.0f / sg;
+    uAb = 1.0f / sa;
 }
 
 // ---------------------------------------------------------------------------
