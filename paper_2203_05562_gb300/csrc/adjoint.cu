@@ -321,6 +321,7 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
 
     // pass 1: sub-horizon sums, kept per bond
     Real wpart[1] = {(Real)0};
+    Real kid1[6] = {0, 0, 0, 0, 0, 0};     // the thread's bond inverse, kept for pass 2 (use_tc)
     for (int t = threadIdx.x; t < nb; t += kAdjThreads) {
         const R4<Real> zj = s_z[t];
         const Real mjx = (Real)-2 * zj.x, mjy = (Real)-2 * zj.y, mjz = (Real)-2 * zj.z;
@@ -392,6 +393,10 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
         sb[kSlAct] = active ? (Real)1 : (Real)0;
         sb[kSlTest + 0] = mjx; sb[kSlTest + 1] = mjy; sb[kSlTest + 2] = mjz; sb[kSlTest + 3] = thj;
         if (active) wpart[0] += (Real)cnt * inv_nb;
+        if (use_tc) {                       // at most one bond per thread
+#pragma unroll
+            for (int c = 0; c < 6; c++) kid1[c] = Kid[c];
+        }
     }
     block_sum<1, Real>(wpart, reinterpret_cast<Real(*)[1]>(&s_red[0][0]));
     const Real w = wpart[0];
@@ -413,7 +418,10 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
         const R4<Real> zj = s_z[t];
         Real Kid[6];
         if (active) {
-            if constexpr (F64) {
+            if (use_tc) {
+#pragma unroll
+                for (int c = 0; c < 6; c++) Kid[c] = kid1[c];
+            } else if constexpr (F64) {
                 const double Kd[6] = {sb[kSlG + 0], sb[kSlG + 1], sb[kSlG + 2],
                                       sb[kSlG + 3], sb[kSlG + 4], sb[kSlG + 5]};
                 inverse_sym_fp64(Kd, Kid);
