@@ -10,7 +10,9 @@ terms.  The FP64 path is timed on the same column for comparison.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--runout]
 
 Besides the headline, the JSON line carries:
-- the roofline of the bond kernel, the HBM figures and the clocks;
+- the roofline of the bond kernel, the HBM figures and the clocks, and the
+  bond pass's time in every launch shape (warp tensor-core kernel, its
+  persistent wave, the tensor-memory kernel, a scalar tile);
 - the end-to-end rate through the API with host buffers;
 - the mixed path's error against FP64 (precision);
 - the FP64 path, the other force states and the coupled mode;

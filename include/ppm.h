@@ -208,7 +208,9 @@ typedef struct {
     double W_int, W_ext, W_kin, W_kin0;   /* Eq. 66-68 (summed over points)   */
     int32_t points_per_block;    /* tensor-core bond kernel: points per block   */
     int32_t bond_blocks;         /* its grid: 0 one warp per point, else the
-                                    blocks of the persistent wave              */
+                                    blocks of the persistent wave (the
+                                    tensor-memory kernel, bond_tile 128, always
+                                    runs one: its CTAs in flight)              */
 } ppm_counters;
 
 typedef struct ppm_ctx ppm_ctx;

@@ -347,7 +347,7 @@ class Simulation:
     def status(self) -> dict:
         """Counters and energies of ``ppm_status`` with the status bits as
         names in ``flags`` (nonconv, singular, nonfinite, family_full,
-        row_full, unstable, halted)."""
+        row_full, unstable, halted, tc_timeout)."""
         c = Counters()
         _check(library().ppm_status(self._ctx, C.byref(c)), "ppm_status")
         out = {name: getattr(c, name) for name, _ in Counters._fields_ if "pad" not in name}
