@@ -177,6 +177,9 @@ typedef struct {
                                     point; 2 a persistent resident wave of
                                     blocks looping over the points; with
                                     bond_tile = 0 the autotuner chooses        */
+    int32_t gather_lanes;        /* force gather: lanes per point, 4 or 8, or 0
+                                    for 4 (with bond_tile = 0 the first call
+                                    times both and keeps the faster)           */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */
@@ -211,6 +214,7 @@ typedef struct {
                                     blocks of the persistent wave (the
                                     tensor-memory kernel, bond_tile 128, always
                                     runs one: its CTAs in flight)              */
+    int32_t gather_lanes;        /* force gather: lanes per point in use        */
 } ppm_counters;
 
 typedef struct ppm_ctx ppm_ctx;

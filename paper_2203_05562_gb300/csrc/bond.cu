@@ -1057,15 +1057,16 @@ k_bond_t5(DevState<float> s, StepConst k, int with_dt, int update) {
 // gather: f_i = dx^2 (sum_own T^ - sum T^[rev]); acceleration, corrector
 // ---------------------------------------------------------------------------
 
-// kGatherLanes lanes per point (eight points per warp): each lane sums every
-// kGatherLanes-th entry of the point's row with a compensated running sum,
+// G lanes per point (4: eight points per warp, or 8: four; the autotuner
+// times both): each lane sums every G-th entry of the point's row with a
+// compensated running sum,
 // then the group combines its lanes in a fixed butterfly; lanes 0..2 of the
 // group finish the point's three components
-template <typename Real>
-__global__ void __launch_bounds__(kGatherPointsPerBlock * kGatherLanes)
+template <typename Real, int G>
+__global__ void __launch_bounds__(kGatherPointsPerBlock * G)
 k_gather(DevState<Real> s, StepConst k, double dt, int initial) {
     constexpr bool F64 = sizeof(Real) == 8;
-    constexpr int G = kGatherLanes;
+    static_assert(G == 4 || G == 8, "four or eight lanes per point");
     if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;   // the run has stopped
     __shared__ Real s_e[kGatherPointsPerBlock][3];
     const int lane = threadIdx.x & 31, sub = threadIdx.x & (G - 1), grp = threadIdx.x / G;
@@ -1423,7 +1424,8 @@ cudaError_t launch_bond(const DevState<Real>& s, const StepConst& k, double dt, 
 template <typename Real>
 cudaError_t launch_gather(const DevState<Real>& s, const StepConst& k, double dt, int initial,
                           int gather_blocks, cudaStream_t st) {
-    k_gather<Real><<<gather_blocks, kGatherPointsPerBlock * kGatherLanes, 0, st>>>(s, k, dt, initial);
+    if (k.gather_lanes == 8) k_gather<Real, 8><<<gather_blocks, kGatherPointsPerBlock * 8, 0, st>>>(s, k, dt, initial);
+    else k_gather<Real, 4><<<gather_blocks, kGatherPointsPerBlock * 4, 0, st>>>(s, k, dt, initial);
     return cudaGetLastError();
 }
 

@@ -11,8 +11,7 @@ namespace ppm {
 constexpr int kMaxRow = 256;          // hard cap of bonds per point (smem staging)
 constexpr int kDefaultMaxFamily = 192;
 constexpr int kWarpPointsPerBlock = 8;  // family kernels: one warp per point
-constexpr int kGatherLanes = 4;         // force gather: lanes per point ...
-constexpr int kGatherPointsPerBlock = 32;   // ... and points per block (128 threads)
+constexpr int kGatherPointsPerBlock = 32;   // force gather: points per block (4 or 8 lanes each)
 constexpr int kAdjAccDoubles = 32;     // adjoint accumulators (gradient, state sums) ...
 constexpr int kAdjRedBlocks = 152;     // ... followed by 5 partial sums per reduction block
 constexpr int kLatBits = 10;          // packed lattice index: ix | iy << 10 | iz << 20
@@ -78,6 +77,7 @@ struct StepConst {
     int tc_ppb, tc_blocks;       // tensor-core bond kernel: points per block; grid (0: one
                                  // point per warp, else a persistent grid of that many blocks)
     int t5_blocks;               // tensor-memory bond kernel: its persistent grid
+    int gather_lanes;            // force gather: lanes per point, 4 or 8
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;

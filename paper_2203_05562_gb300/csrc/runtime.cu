@@ -106,6 +106,7 @@ int check_params(const ppm_params* p) {
         return PPM_EINVAL;
     if (p->points_per_block < 0 || p->points_per_block > 2 || p->bond_grid < 0 || p->bond_grid > 2)
         return PPM_EINVAL;
+    if (p->gather_lanes != 0 && p->gather_lanes != 4 && p->gather_lanes != 8) return PPM_EINVAL;
     if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
         return PPM_EINVAL;
     if ((p->bc != 0 && p->bc != 1) || !(p->load_rate >= 0) || !std::isfinite(p->load_rate))
@@ -288,6 +289,26 @@ int issue_initial(ppm_ctx* c, const DevState<Real>& s) {
         if (rc) return rc;
     }
     CU(launch_bond<Real>(s, c->k, 0.0, 0, c->stream));
+    if (c->p.bond_tile == 0 && c->p.gather_lanes == 0) {
+        // the gather's lanes per point, timed on the initial gather (which
+        // only recomputes the initial forces and accelerations: repeating it
+        // leaves the same state)
+        float best = 1e30f;
+        int pick = 4;
+        for (int lanes : {4, 8}) {
+            c->k.gather_lanes = lanes;
+            CU(launch_gather<Real>(s, c->k, 0.0, 1, c->gather_blocks, c->stream));      // warm
+            CU(cudaEventRecord(c->ev[4], c->stream));
+            for (int r = 0; r < 3; r++) CU(launch_gather<Real>(s, c->k, 0.0, 1, c->gather_blocks, c->stream));
+            CU(cudaEventRecord(c->ev[5], c->stream));
+            CU(cudaEventSynchronize(c->ev[5]));
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
+            c->launches += 4;
+            if (ms < best) { best = ms; pick = lanes; }
+        }
+        c->k.gather_lanes = pick;
+    }
     CU(launch_gather<Real>(s, c->k, 0.0, 1, c->gather_blocks, c->stream));
     CU(launch_energy_reduce(s.epart, c->gather_blocks, s.ctr, 1, s.row_ptr, c->k.npoints, c->k.halt,
                             c->k.energy_tol, c->stream));
@@ -848,6 +869,7 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
         }
         k.tc_blocks = resident;
     }
+    k.gather_lanes = p->gather_lanes == 8 ? 8 : 4;
     k.t5_blocks = 0;
     if (p->precision == PPM_MIXED && p->model == 0 && !p->coupled) {
         if (bond_t5_prepare(&k.t5_blocks) != cudaSuccess) {
@@ -1019,6 +1041,7 @@ int ppm_status(ppm_ctx* c, ppm_counters* out) {
     // the persistent grid in use: the tensor-memory kernel's, or the warp kernel's
     const bool t5 = c->k.tile == 128 && c->k.t5_blocks > 0 && c->k.model == 0 && !c->k.coupled;
     out->bond_blocks = t5 ? c->k.t5_blocks : c->k.tc_blocks;
+    out->gather_lanes = c->k.gather_lanes;
     out->halted_step = (int32_t)h.halted_step;
     out->unstable_step = (int32_t)h.unstable_step;
     out->launches = c->launches;

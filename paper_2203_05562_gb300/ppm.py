@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("energy_tol", C.c_double), ("plane_strain", C.c_int32),
         ("coupled", C.c_int32), ("porosity", C.c_double), ("rho_s", C.c_double),
         ("rho_w", C.c_double), ("wr_a1", C.c_double), ("wr_a2", C.c_double), ("wr_n", C.c_double),
-        ("points_per_block", C.c_int32), ("bond_grid", C.c_int32),
+        ("points_per_block", C.c_int32), ("bond_grid", C.c_int32), ("gather_lanes", C.c_int32),
     ]
 
 
@@ -62,7 +62,8 @@ class Counters(C.Structure):
                 ("returns_fp64", C.c_int64), ("bond_tile", C.c_int32), ("halted_step", C.c_int32),
                 ("status", C.c_uint32), ("unstable_step", C.c_int32),
                 ("W_int", C.c_double), ("W_ext", C.c_double), ("W_kin", C.c_double),
-                ("W_kin0", C.c_double), ("points_per_block", C.c_int32), ("bond_blocks", C.c_int32)]
+                ("W_kin0", C.c_double), ("points_per_block", C.c_int32), ("bond_blocks", C.c_int32),
+                ("gather_lanes", C.c_int32)]
 
 
 _lib = None

@@ -246,6 +246,20 @@ def test_bond_tiles_match_oracle(tile):
         assert err["u"] <= tol and err["sigma"] <= tol, (precision, err)
 
 
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_gather_lanes_match_oracle(lanes):
+    # the force gather with four or eight lanes per point (the autotuner's two
+    # candidates), both precisions, plastic bonds and rebuilds every 3 steps
+    cfg = pi.small_config(7, 6, 9, suction=50e3, rebuild_every=3, gather_lanes=lanes)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=13)
+    run = oracle_run(cfg, 6, v0)
+    for precision, tol, norm in (("fp64", FP64_TOL, rel_inf), ("mixed", MIXED_TOL, rel_l2)):
+        sim = gpu_run(cfg, 6, precision, v0=v0)
+        assert sim.status()["gather_lanes"] == lanes
+        err = state_errors(sim, run, norm=norm)
+        assert err["u"] <= tol and err["a"] <= 10 * tol, (precision, err)
+
+
 @pytest.mark.parametrize("model", [0, 2])
 @pytest.mark.parametrize("ppb,grid", [(1, 1), (1, 2), (2, 1), (2, 2)])
 def test_tensor_core_launch_shapes_match_oracle(model, ppb, grid):
@@ -276,6 +290,7 @@ def test_autotuner_picks_a_tile_and_stays_correct():
     sim.write("v", v0)
     sim.step(10)
     assert sim.status()["bond_tile"] in (32, 64, 128, 256)
+    assert sim.status()["gather_lanes"] in (4, 8)
     assert rel_l2(sim.read("u"), run.u) <= MIXED_TOL
 
 
