@@ -108,3 +108,26 @@ def test_agrees_with_the_warp_tensor_core_kernel():
     b = run_t5(cfg, 9, v0, tile=32)
     assert rel_l2(a.read("u"), b.read("u")) <= 1e-5
     assert rel_l2(a.read("sigma"), b.read("sigma")) <= 1e-5
+
+
+def test_ensemble_of_uneven_columns_matches_per_column_oracle():
+    # the persistent CTAs run across column boundaries; each column against
+    # its own oracle run
+    from paper_2203_05562_gb300 import Simulation
+    cols = pi.ensemble_columns(count=4, seed=5, n_min=200, n_max=700)
+    cfg = pi.config("ensemble_64_columns_mixed", rebuild_every=5)
+    n = sum(c["nx"] * c["ny"] * c["nz"] for c in cols)
+    v0 = np.random.default_rng(8).normal(0, 1e-6, size=(3, n))
+    sim = Simulation(cfg, columns=cols, precision="mixed", bond_tile=128)
+    sim.write("v", v0)
+    sim.step(12)
+    st = sim.status()
+    assert st["bond_tile"] == 128 and "tc_timeout" not in st["flags"]
+    u = sim.read("u")
+    off = 0
+    for c in cols:
+        cc = dict(cfg, **c)
+        m = pi.num_points(cc)
+        run = oracle_run(cc, 12, v0[:, off:off + m])
+        assert rel_l2(u[:, off:off + m], run.u) <= MIXED_TOL
+        off += m
