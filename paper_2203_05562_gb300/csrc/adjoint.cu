@@ -204,7 +204,8 @@ __global__ void k_adj_pre(DevState<Real> s, AdjState<Real> a, StepConst k, int i
 }
 
 constexpr int kAdjThreads = 128;
-constexpr int kAdjSlots = 24;   // per-bond shared slots:
+constexpr int kAdjSlots = 25;   // per-bond shared slots (an odd row stride: each thread walks its
+                                //   own row without bank conflicts):
 constexpr int kSlTest = 0;      //   -2 zeta~_j (3) and hf^2 - |zeta~_j|^2: the membership test
 constexpr int kSlG = 4;         //   K~ sums (pass 1), then G = K~-bar + K~-bar^T (pass 2): 6
 constexpr int kSlAb = 10;       //   A~ sums (pass 1), then A~-bar (pass 2): 9
@@ -563,11 +564,12 @@ k_adj_bond(DevState<Real> s, AdjState<Real> a, StepConst k) {
 #pragma unroll 2
                 for (int q = 0; q < nb; q++) {
                     const float* sq = s_b + (size_t)q * kAdjSlots;
-                    const float4 m = *reinterpret_cast<const float4*>(sq + kSlTest);
-                    const float4 g0 = *reinterpret_cast<const float4*>(sq + 4);
-                    const float4 g1 = *reinterpret_cast<const float4*>(sq + 8);
-                    const float4 g2 = *reinterpret_cast<const float4*>(sq + 12);
-                    const float4 g3 = *reinterpret_cast<const float4*>(sq + 16);
+                    // rows are 25 floats apart: scalar loads (every thread reads the same row)
+                    const float4 m = make_float4(sq[kSlTest], sq[kSlTest + 1], sq[kSlTest + 2], sq[kSlTest + 3]);
+                    const float4 g0 = make_float4(sq[4], sq[5], sq[6], sq[7]);
+                    const float4 g1 = make_float4(sq[8], sq[9], sq[10], sq[11]);
+                    const float4 g2 = make_float4(sq[12], sq[13], sq[14], sq[15]);
+                    const float4 g3 = make_float4(sq[16], sq[17], sq[18], sq[19]);
                     const float tst = member_test_lhs(zt.x, zt.y, zt.z, zt.w, m.x, m.y, m.z);
                     masked_add15(tst, m.w, g0, g1, g2, g3, Gf, Af);
                 }
