@@ -180,6 +180,16 @@ typedef struct {
     int32_t gather_lanes;        /* force gather: lanes per point, 4 or 8, or 0
                                     for 4 (with bond_tile = 0 the first call
                                     times both and keeps the faster)           */
+    int32_t withhold_tc_product; /* fault injection for tests, normally 0.  1:
+                                    in every pass of the tensor-memory bond
+                                    kernel (bond_tile 128) each CTA's first
+                                    product signals a spare mbarrier instead
+                                    of the one awaited, so that the wait runs
+                                    out after about a second: the pass sets
+                                    PPM_STATUS_TC_TIMEOUT and the points it
+                                    had not reached keep their state.  The
+                                    product still completes (on the spare
+                                    barrier), and the context stays usable  */
 } ppm_params;
 
 /* one column of a batched ensemble; other parameters come from ppm_params */

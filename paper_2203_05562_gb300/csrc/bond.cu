@@ -763,9 +763,9 @@ k_bond_tcw(DevState<float> s, StepConst k, int with_dt, int update) {
 // (bond_epilogue) and the CTA commits the point.  The next point's
 // neighbour data is fetched by cp.async while the current point's bonds
 // are updated, so that its staging finds it in shared memory.  A wait that
-// runs out sets PPM_STATUS_TC_TIMEOUT and stops the CTA (its remaining
-// points keep their state); the CTA still waits for its product in flight
-// (bounded) and frees its tensor memory.
+// runs out (about a second) sets PPM_STATUS_TC_TIMEOUT and stops the CTA
+// (its remaining points keep their state); the CTA still waits for its
+// product in flight (bounded) and frees its tensor memory.
 
 // words of the prefetched staging data: per bond (lat, u xyz, vh xyz, rev
 // of the neighbour) and per point (lat, u xyz, vh xyz, sigma, pc, eps, column)
@@ -812,6 +812,7 @@ k_bond_t5(DevState<float> s, StepConst k, int with_dt, int update) {
     if (k.halt && (s.ctr->status & PPM_STATUS_HALTED)) return;   // the whole CTA, before any allocation
     extern __shared__ __align__(128) unsigned char t5s[];
     __shared__ alignas(8) uint64_t s_mbar;
+    __shared__ alignas(8) uint64_t s_spare;                        // fault injection (t5_withhold)
     __shared__ uint32_t s_tmem;
     __shared__ float s_max[2][kT5Threads / 32];
     __shared__ float s_red[2][kT5Threads / 32][NRED];             // by point parity
@@ -828,8 +829,13 @@ k_bond_t5(DevState<float> s, StepConst k, int with_dt, int update) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
     }
     const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+    const uint32_t mb_spare = (uint32_t)__cvta_generic_to_shared(&s_spare);
+    // with t5_withhold the CTA's first product signals the spare barrier, so
+    // that the wait on mb runs out; the drain below then waits on the spare
+    const bool withhold = k.t5_withhold != 0;
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb_spare) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // the first point's staging data
@@ -952,7 +958,7 @@ k_bond_t5(DevState<float> s, StepConst k, int with_dt, int update) {
         t5_fence_after();
         if (t == 0) {
             t5_mma(tmem, t5_desc(sbase + kT5Bond, 256), t5_desc(sbase + kT5Memb, 256), kT5IdescDist, 0);
-            t5_commit(mb);
+            t5_commit(withhold ? mb_spare : mb);
         }
         // the next point's row, while the product runs
         int r0n = 0, nbn = 0;
@@ -1046,7 +1052,8 @@ k_bond_t5(DevState<float> s, StepConst k, int with_dt, int update) {
     if (!ok) {
         if (t == 0) atomicOr(&s.ctr->status, PPM_STATUS_TC_TIMEOUT);
         // the product in flight completes the phase the failed wait was on
-        (void)__syncthreads_and(t5_wait(mb, phase ^ 1u));
+        // (with t5_withhold: the spare barrier's first phase)
+        (void)__syncthreads_and(withhold ? t5_wait(mb_spare, 0u) : t5_wait(mb, phase ^ 1u));
     }
     t5_fence_before();
     __syncthreads();

@@ -1247,7 +1247,10 @@ constexpr int kT5Smem = 49152;                    // dynamic shared memory per C
 // and B (0), both K-major (0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
 constexpr uint32_t kT5IdescDist = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr uint32_t kT5IdescSums = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr int kT5WaitLimit = 1 << 22;             // mbarrier polls before a wait is given up
+// a wait is given up after about a second (global timer), or after 2^24
+// polls should the timer not advance
+constexpr unsigned long long kT5WaitNs = 1000000000ull;
+constexpr int kT5WaitPolls = 1 << 24;
 
 // byte offset of element (r, k) in a K-major matrix with K columns
 __device__ __forceinline__ uint32_t t5_off(int r, int k, int K) {
@@ -1273,13 +1276,24 @@ __device__ __forceinline__ void t5_commit(uint32_t mbar) {
                  :: "r"(mbar) : "memory");
 }
 
-// bounded wait for the completion of phase `parity` of the mbarrier
+__device__ __forceinline__ unsigned long long t5_now() {
+    unsigned long long ns;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+    return ns;
+}
+
+// bounded wait for the completion of phase `parity` of the mbarrier: true
+// once it completes, false when the time or poll bound runs out first
 __device__ __forceinline__ bool t5_wait(uint32_t mbar, uint32_t parity) {
-    for (int it = 0; it < kT5WaitLimit; it++) {
+    unsigned long long t0 = 0;
+    for (int it = 0; it < kT5WaitPolls; it++) {
         uint32_t ok;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
         if (ok) return true;
+        const unsigned long long now = t5_now();
+        if (it == 0) t0 = now;
+        else if (now - t0 > kT5WaitNs) return false;
     }
     return false;
 }

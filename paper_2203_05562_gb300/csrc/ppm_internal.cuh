@@ -78,6 +78,7 @@ struct StepConst {
                                  // point per warp, else a persistent grid of that many blocks)
     int t5_blocks;               // tensor-memory bond kernel: its persistent grid
     int gather_lanes;            // force gather: lanes per point, 4 or 8
+    int t5_withhold;             // fault injection: tensor-memory products signal a spare barrier
     long long cap;               // bond capacity
     // FP32 copies used by the mixed path (no FP64 conversions in its loops)
     float dxf, inv_dxf, dtf, hdtf, Kf, muf, rhof, inv_rho_dxf, dx2f, massf, etaf;

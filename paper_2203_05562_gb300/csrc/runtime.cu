@@ -107,6 +107,7 @@ int check_params(const ppm_params* p) {
     if (p->points_per_block < 0 || p->points_per_block > 2 || p->bond_grid < 0 || p->bond_grid > 2)
         return PPM_EINVAL;
     if (p->gather_lanes != 0 && p->gather_lanes != 4 && p->gather_lanes != 8) return PPM_EINVAL;
+    if (p->withhold_tc_product != 0 && p->withhold_tc_product != 1) return PPM_EINVAL;
     if (p->rebuild_every < 0 || p->suction < 0 || !(p->vg_n > 1.0) || !(p->vg_alpha >= 0))
         return PPM_EINVAL;
     if ((p->bc != 0 && p->bc != 1) || !(p->load_rate >= 0) || !std::isfinite(p->load_rate))
@@ -870,6 +871,7 @@ int ppm_init(const ppm_params* p, int n_columns, const ppm_column* cols, void* d
         k.tc_blocks = resident;
     }
     k.gather_lanes = p->gather_lanes == 8 ? 8 : 4;
+    k.t5_withhold = p->withhold_tc_product;
     k.t5_blocks = 0;
     if (p->precision == PPM_MIXED && p->model == 0 && !p->coupled) {
         if (bond_t5_prepare(&k.t5_blocks) != cudaSuccess) {

@@ -47,6 +47,7 @@ class Params(C.Structure):
         ("coupled", C.c_int32), ("porosity", C.c_double), ("rho_s", C.c_double),
         ("rho_w", C.c_double), ("wr_a1", C.c_double), ("wr_a2", C.c_double), ("wr_n", C.c_double),
         ("points_per_block", C.c_int32), ("bond_grid", C.c_int32), ("gather_lanes", C.c_int32),
+        ("withhold_tc_product", C.c_int32),
     ]
 
 

@@ -4,7 +4,10 @@ sub-horizon tests and sums, one CTA per point) against the FP64 oracle on
 identical seeded inputs, within the mixed tolerance (1e-3 relative L2), and
 its launch properties: bitwise reproducible, graph replay equal to direct
 launches, no wait given up, and the points with more than 128 bonds handed
-to the scalar kernel in the same pass."""
+to the scalar kernel in the same pass.  One test makes the bounded wait run
+out through a host-set switch (no GPU fault) and checks the status word."""
+import time
+
 import numpy as np
 import pytest
 
@@ -131,3 +134,32 @@ def test_ensemble_of_uneven_columns_matches_per_column_oracle():
         run = oracle_run(cc, 12, v0[:, off:off + m])
         assert rel_l2(u[:, off:off + m], run.u) <= MIXED_TOL
         off += m
+
+
+def test_a_withheld_product_ends_the_wait_with_a_status_and_the_context_stays_usable():
+    # withhold_tc_product: each CTA's first product signals a spare barrier,
+    # so the wait on the awaited one runs out (about a second).  The pass sets
+    # tc_timeout and stops: every point here has at most 128 bonds, so no
+    # point's stress moves.  The product still completes on the spare
+    # barrier, the CTA frees its tensor memory, and the process goes on to a
+    # parity case on the same device.
+    from paper_2203_05562_gb300 import Simulation
+    cfg = pi.small_config(7, 6, 9, suction=30e3, rebuild_every=100)
+    v0 = pi.initial_velocity(cfg, std=1e-3, seed=2)
+    sim = Simulation(dict(cfg, withhold_tc_product=1), precision="mixed", bond_tile=128,
+                     use_graph=False)
+    assert np.diff(sim.read("row_ptr")).max() <= 128
+    sim.write("v", v0)
+    sig0 = sim.read("sigma")
+    t0 = time.perf_counter()
+    sim.step(1)
+    st = sim.status()
+    elapsed = time.perf_counter() - t0
+    assert "tc_timeout" in st["flags"], st["flags"]
+    assert 0.5 < elapsed < 60.0, elapsed
+    assert np.array_equal(sim.read("sigma"), sig0)
+    sim.close()
+    run = oracle_run(cfg, 4, v0)
+    ok = run_t5(cfg, 4, v0, use_graph=True)
+    err = state_errors(ok, run, norm=rel_l2)
+    assert err["u"] <= MIXED_TOL and err["sigma"] <= MIXED_TOL, err
