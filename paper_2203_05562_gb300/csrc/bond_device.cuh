@@ -41,10 +41,15 @@ __device__ __forceinline__ bool inverse_sym_fp64(const double k[6], double inv[6
     return true;
 }
 
-// Mixed path: the cancellation-prone steps -- cofactors and determinant --
-// in FP64 from the FP32 sums; the degeneracy test, the reciprocal of the
-// determinant and the final scaling in FP32 (the result is FP32 either way,
-// so a full FP64 division would change it by at most an ulp).
+// Mixed path: the determinant -- the step where cancellation decides the
+// degeneracy test and the scale of every entry -- in FP64 from the FP32
+// sums (its three first-row cofactors too); the six cofactors of the
+// inverse's entries in FP32, each a 2 x 2 minor a b - c d by Kahan's FMA
+// algorithm (minor2_f32: relative error at most 2u, so each entry is within
+// a few ulp of the one full FP64 cofactors give); the degeneracy test, the
+// reciprocal of the determinant and the final scaling in FP32 (the result is
+// FP32 either way, so a full FP64 division would change it by at most an
+// ulp).
 //
 // On GB300 the hardware conversions between binary32 and binary64 issue on
 // the FP64 pipe at the FP64 rate (about 1/64 of FP32), so the tensor is first
@@ -88,6 +93,17 @@ __device__ __forceinline__ float f64_to_f32_regular(double d) {
     return __uint_as_float(f | (hi & 0x80000000u));
 }
 
+// a b - c d of binary32 numbers by Kahan's algorithm: w = RN(c d), its
+// rounding error w - c d recovered exactly by an FMA, and RN(a b - w) plus
+// that error; relative error at most 2u (Jeannerod, Louvet and Muller, Math.
+// Comp. 82, 2013), barring underflow of the error term
+__device__ __forceinline__ float minor2_f32(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
 // the unscaled steps with the hardware conversions (tensors outside the
 // range of the re-encodings: zero, non-finite, tiny or huge entries)
 __device__ __noinline__ bool inverse_sym_mixed_slow(float K00, float K11, float K22, float K12,
@@ -124,9 +140,6 @@ __device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K2
     const double k22 = f32_to_f64_flushed(s22), k12 = f32_to_f64_flushed(s12);
     const double k02 = f32_to_f64_flushed(s02), k01 = f32_to_f64_flushed(s01);
     const double c00 = k11 * k22 - k12 * k12;
-    const double c11 = k00 * k22 - k02 * k02;
-    const double c22 = k00 * k11 - k01 * k01;
-    const double c12 = k01 * k02 - k00 * k12;
     const double c02 = k01 * k12 - k02 * k11;
     const double c01 = k02 * k12 - k01 * k22;
     const double det64 = k00 * c00 + k01 * c01 + k02 * c02;
@@ -136,9 +149,12 @@ __device__ __forceinline__ bool inverse_sym_mixed(float K00, float K11, float K2
     const float t = (s00 + s11 + s22) * (1.0f / 3.0f);
     if (!(det > 1e-12f * t * t * t)) return false;
     const float r = __frcp_rn(det) * sc;                // sc / det of the scaled tensor = 1 / det
-    inv[0] = f64_to_f32_regular(c00) * r; inv[1] = f64_to_f32_regular(c11) * r;
-    inv[2] = f64_to_f32_regular(c22) * r; inv[3] = f64_to_f32_regular(c12) * r;
-    inv[4] = f64_to_f32_regular(c02) * r; inv[5] = f64_to_f32_regular(c01) * r;
+    inv[0] = minor2_f32(s11, s22, s12, s12) * r;        // c00
+    inv[1] = minor2_f32(s00, s22, s02, s02) * r;        // c11
+    inv[2] = minor2_f32(s00, s11, s01, s01) * r;        // c22
+    inv[3] = minor2_f32(s01, s02, s00, s12) * r;        // c12
+    inv[4] = minor2_f32(s01, s12, s02, s11) * r;        // c02
+    inv[5] = minor2_f32(s02, s12, s01, s22) * r;        // c01
     return true;
 }
 
