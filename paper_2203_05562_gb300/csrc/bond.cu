@@ -85,7 +85,8 @@ __device__ __forceinline__ void bond_epilogue(
     unsigned& n_singular, unsigned& n_ret64) {
     constexpr bool F64 = sizeof(Real) == 8;
     n_pairs += (unsigned)cnt;
-    // shape-tensor inverse with FP64 cofactors and determinant (Eq. 23, 25)
+    // shape-tensor inverse (Eq. 23, 25): FP64 on the FP64 path; the mixed
+    // path keeps FP64 for the determinant (inverse_sym_mixed)
     Real Kid[6];
     bool active = cntr >= (Real)3;
     if constexpr (F64) {
