@@ -84,12 +84,14 @@ def _ws_cols(cfg, columns):
 
 
 def test_the_later_parameters_are_validated():
-    # the energy tolerance, the substrate, plane strain (y period > 4 delta) and
-    # the coupled mode (material ranges), without a GPU
+    # the energy tolerance, the substrate, plane strain (y period > 4 delta),
+    # the coupled mode (material ranges) and the launch-shape switches, without a GPU
     cfg = pi.small_config(6, 13, 5)
     assert _ws(cfg)[0] == 0
     good = [dict(energy_tol=5e-2), dict(contact=1), dict(plane_strain=1), dict(coupled=1),
-            dict(plane_strain=1, contact=1, coupled=1, halt_on_unstable=1)]
+            dict(plane_strain=1, contact=1, coupled=1, halt_on_unstable=1),
+            dict(bond_tile=128), dict(points_per_block=2, bond_grid=2), dict(gather_lanes=8),
+            dict(withhold_tc_product=1)]
     for kw in good:
         assert _ws(dict(cfg, **kw))[0] == 0, kw
     bad = [dict(energy_tol=-1e-2), dict(energy_tol=float("inf")), dict(contact=2),
@@ -97,7 +99,9 @@ def test_the_later_parameters_are_validated():
            dict(plane_strain=2), dict(plane_strain=1, ny=12), dict(coupled=2),
            dict(coupled=1, porosity=0.0), dict(coupled=1, porosity=1.0),
            dict(coupled=1, rho_s=0.0), dict(coupled=1, wr_a1=0.0), dict(coupled=1, wr_n=1.0),
-           dict(coupled=1, wr_a2=-1.0), dict(halt_on_unstable=2)]
+           dict(coupled=1, wr_a2=-1.0), dict(halt_on_unstable=2), dict(bond_tile=96),
+           dict(points_per_block=3), dict(bond_grid=3), dict(gather_lanes=5),
+           dict(withhold_tc_product=2)]
     for kw in bad:
         assert _ws(dict(cfg, **kw))[0] == -1, kw
     # plane strain and the coupled mode take one column
